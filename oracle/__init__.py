@@ -103,7 +103,7 @@ def _load():
                                       P, P, P, P, P, P, P, P, P, C.c_int]
     lib.oracle_shade.restype = C.c_int
     lib.oracle_shade.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P, P, P, P, P, C.c_int64,
-                                 P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
+                                 P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P,
                                  P, P, P, P, P, P, C.c_int]
     lib.oracle_splitmix64.restype = C.c_uint64
     lib.oracle_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
@@ -196,9 +196,11 @@ def trace_grad(scene, ray_o, ray_d, g_feat, g_depth, g_opacity, params: Params =
 
 
 def shade(scene, x, nrm, albedo, rough, wo, env, n_diffuse: int, n_spec: int, seed: int,
-          params: Params, margins: Margins | None = Margins(), n_threads: int = 0):
+          params: Params, margins: Margins | None = Margins(), n_threads: int = 0,
+          point_ids=None):
     """Monte Carlo rendering equation per point (Eq. 13-15). Returns a dict
-    with rgb [P,3], vis [P], ind [P,3] and flags [P]."""
+    with rgb [P,3], vis [P], ind [P,3] and flags [P]. `point_ids` gives the
+    point number that keys each point's random stream (default 0..P-1)."""
     lib = _load()
     means, quats, scales, opacity, feats = _surfel_arrays(scene)
     x, nrm, albedo, wo = (_f32(a).reshape(-1, 3) for a in (x, nrm, albedo, wo))
@@ -210,10 +212,11 @@ def shade(scene, x, nrm, albedo, rough, wo, env, n_diffuse: int, n_spec: int, se
            "flags": np.zeros(Pn, np.uint32)}
     p = params.c()
     m = margins.c() if margins is not None else None
+    pid = None if point_ids is None else np.ascontiguousarray(point_ids, np.int64).reshape(Pn)
     rc = lib.oracle_shade(_ptr(means), _ptr(quats), _ptr(scales), _ptr(opacity), _ptr(feats), n, F,
                           _ptr(x), _ptr(nrm), _ptr(albedo), _ptr(rough), _ptr(wo), Pn, _ptr(env),
                           H, W, int(n_diffuse), int(n_spec), C.c_uint64(seed & (2**64 - 1)),
-                          C.byref(p), C.byref(m) if m is not None else None,
+                          _ptr(pid), C.byref(p), C.byref(m) if m is not None else None,
                           _ptr(out["rgb"]), _ptr(out["vis"]), _ptr(out["ind"]), _ptr(out["flags"]),
                           int(n_threads))
     if rc != 0:

@@ -591,14 +591,16 @@ int oracle_sample_dirs(const float* nrm, const float* wo_in, const float* rough,
  *   specular lobe, GGX samples:   f_s L_i cos / pdf = F G (w_o.h) L_i / ((n.w_o)(n.h));
  *   L_i = V L_dir + L_ind with (L_ind, 1 - V) = Trace(x, w_i) (Eq. 13-14).
  * Outputs rgb [P,3]; vis [P] and ind [P,3] are the means of V and L_ind over
- * the cosine samples (NULL to skip); flags [P] ORs the traced rays' flags. */
+ * the cosine samples (NULL to skip); flags [P] ORs the traced rays' flags.
+ * point_ids [P] (or NULL for 0..P-1) is the point number that keys the
+ * random stream of each point. */
 int oracle_shade(const float* means, const float* quats, const float* scales, const float* opacity,
                  const float* feats, int64_t n, int32_t F_total,
                  const float* x_in, const float* n_in, const float* albedo, const float* rough,
                  const float* wo_in, int64_t Pn, const float* env, int32_t env_h, int32_t env_w,
-                 int32_t n_diffuse, int32_t n_spec, uint64_t seed, const oracle_params* P,
-                 const oracle_margins* M, double* out_rgb, double* out_vis, double* out_ind,
-                 uint32_t* out_flags, int n_threads)
+                 int32_t n_diffuse, int32_t n_spec, uint64_t seed, const int64_t* point_ids,
+                 const oracle_params* P, const oracle_margins* M, double* out_rgb, double* out_vis,
+                 double* out_ind, uint32_t* out_flags, int n_threads)
 {
     if (n < 0 || Pn < 0 || !P || P->feat_count != 3) return -1;
     if (P->feat_offset < 0 || P->feat_offset + 3 > F_total) return -1;
@@ -633,7 +635,8 @@ int oracle_shade(const float* means, const float* quats, const float* scales, co
                 double no = dot3(nn, wo);
                 for (int64_t sI = 0; sI < S; ++sI) {
                     double wi[3], h[3];
-                    if (!sample_direction(seed, p, sI, S, n_diffuse, nn, wo, r, wi, h)) continue;
+                    int64_t key = point_ids ? point_ids[p] : p;
+                    if (!sample_direction(seed, key, sI, S, n_diffuse, nn, wo, r, wi, h)) continue;
                     int64_t nnr = 0;
                     int64_t nh = collect_hits(s, n, x, wi, P, M, hits, nears, &nnr);
                     double C[3], D, Tfin;
