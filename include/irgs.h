@@ -1,0 +1,211 @@
+/*
+ * irgs.h -- C ABI of the GB300 2D Gaussian ray tracer (libirgs.so).
+ *
+ * Differentiable ray tracing of 2D Gaussian surfels as defined by IRGS
+ * (Gu et al., "IRGS: Inter-Reflective Gaussian Splatting with 2D Gaussian Ray
+ * Tracing", CVPR 2025, arXiv 2412.15867): the ray-splat intersection of
+ * Eq. 6, the surfel response of Eq. 7, front-to-back alpha blending (Eq. 2)
+ * into Trace(r_o, r_d) of Eq. 8, its gradient (Sec. 3.3, "our 2D Gaussian ray
+ * tracing approach is fully differentiable"), and the Monte Carlo rendering
+ * equation of Eq. 15 with the light split of Eq. 13-14.
+ *
+ * Conventions shared by every entry point
+ *  - Array arguments are DEVICE pointers to C-contiguous float32 / int32 data
+ *    owned by the caller. The library never frees them and never keeps them
+ *    after the call returns (the scene keeps its own copies).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). All work is
+ *    enqueued asynchronously on it; a call returns once the work is queued.
+ *  - The return status covers argument validation and launch errors. Errors
+ *    that kernels detect (traversal stack overflow) are recorded in the
+ *    scene's status word and reported by irgs_scene_status().
+ *  - No entry point exits or aborts the process. Build/destroy of one scene
+ *    must not race with other calls on that scene; concurrent traces of one
+ *    scene are safe (they only read it).
+ *  - Quaternions are (w, x, y, z) and need not be normalised; the rotation
+ *    columns are the tangents t_u, t_v and the normal n = t_u x t_v (Sec. 3.2).
+ *    Scales (s_u, s_v) > 0 and opacities in [0, 1] are activated values.
+ */
+#ifndef IRGS_H
+#define IRGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IRGS_ABI_VERSION 1
+#define IRGS_MAX_FEATURES 16   /* blended channels per trace call */
+
+typedef enum {
+    IRGS_OK = 0,
+    IRGS_ERR_INVALID_ARG = 1,   /* a pointer, size or parameter is invalid       */
+    IRGS_ERR_OOM = 2,           /* device memory allocation failed               */
+    IRGS_ERR_CUDA = 3,          /* a CUDA runtime call or launch failed          */
+    IRGS_ERR_NONFINITE = 4,     /* reserved: non-finite input detected           */
+    IRGS_ERR_TIMEOUT = 5,       /* reserved: a bounded device wait gave up       */
+    IRGS_ERR_UNSUPPORTED = 6,   /* e.g. a k-buffer size that is not compiled in  */
+    IRGS_ERR_DEVICE = 7         /* a kernel recorded an error (stack overflow)   */
+} irgs_status;
+
+/* Opaque scene: owns a Morton-ordered packed copy of the surfels, their
+ * features, and a linear BVH over the surfels' support-disk bounding boxes. */
+typedef struct irgs_scene_s* irgs_scene;
+
+/* Surfel cloud in user order (device pointers, float32, C-contiguous). */
+typedef struct {
+    const float* means;       /* [n, 3] centres mu                                */
+    const float* quats;       /* [n, 4] rotation quaternions (w, x, y, z)          */
+    const float* scales;      /* [n, 2] (s_u, s_v) > 0                             */
+    const float* opacity;     /* [n] opacity o in [0, 1]                          */
+    const float* features;    /* [n, num_features], NULL iff num_features == 0     */
+    int64_t n;                /* number of surfels, 0 <= n < 2^31 - 1              */
+    int32_t num_features;     /* channels per surfel, 0 .. 64                      */
+} irgs_surfels;
+
+/* Parameters of one trace (Eq. 2, 6-8 and the termination rule of Sec. 4). */
+typedef struct {
+    int32_t k;            /* k-buffer size: 1, 4, 8, 16 or 32 (8 and 16 everywhere) */
+    float alpha_min;      /* hits need alpha >= alpha_min; >= the scene's value     */
+    float alpha_max;      /* alpha = min(alpha_max, o exp(-rho^2/2)), <= 1          */
+    float T_min;          /* stop after the hit that makes T < T_min, in [0, 1)     */
+    float t_min;          /* hits need tau > t_min (>= 0)                           */
+    float t_max;          /* hits need tau < t_max (may be +inf)                    */
+    int32_t feat_offset;  /* first blended feature channel                          */
+    int32_t feat_count;   /* blended channels, 0 .. IRGS_MAX_FEATURES               */
+    uint32_t flags;       /* reserved, must be 0                                    */
+} irgs_trace_params;
+
+/* Human-readable name of a status code (static storage). */
+const char* irgs_status_string(irgs_status status);
+
+/* IRGS_ABI_VERSION of the loaded library. */
+int32_t irgs_abi_version(void);
+
+/*
+ * Build a scene from a surfel cloud (Sec. 3.2, bounding proxies and BVH;
+ * Eq. 5 gives the support radius). Each surfel is bounded by the box of its
+ * support disk rho <= rho_c, rho_c = min(3, sqrt(2 ln(o / alpha_min))),
+ * where rho^2 = u^2 + v^2 of Eq. 7; surfels with o < alpha_min never hit.
+ * The library copies the surfels into Morton order and builds a binary LBVH
+ * (Morton codes, radix sort, Karras hierarchy, bottom-up box refit) on the
+ * device, enqueued on `stream`.
+ *   surfels   : device arrays, read during the call's stream work only.
+ *   alpha_min : the smallest alpha cutoff later traces may use (> 0).
+ *   out       : receives the new scene handle (caller owns it; free it with
+ *               irgs_destroy_scene). Unchanged on error.
+ * The scene allocates device memory (about 200 B per surfel plus features)
+ * with cudaMalloc; IRGS_ERR_OOM if that fails.
+ */
+irgs_status irgs_build_scene(const irgs_surfels* surfels, float alpha_min, void* stream,
+                             irgs_scene* out);
+
+/* Free a scene and all its device memory (synchronises the device first).
+ * NULL is accepted and ignored. */
+irgs_status irgs_destroy_scene(irgs_scene scene);
+
+/* Scene facts: surfel count, feature channels, alpha_min and device bytes.
+ * Any output pointer may be NULL. */
+irgs_status irgs_scene_info(irgs_scene scene, int64_t* n, int32_t* num_features,
+                            float* alpha_min, int64_t* device_bytes);
+
+/* Synchronise `stream`, then read and clear the scene's device error word.
+ * Returns IRGS_OK or IRGS_ERR_DEVICE; *bits (may be NULL) receives the raw
+ * word (bit 0: a traversal stack overflowed and that ray's result is
+ * incomplete). */
+irgs_status irgs_scene_status(irgs_scene scene, void* stream, uint32_t* bits);
+
+/*
+ * Copy the scene's structure to HOST buffers for inspection and tests
+ * (synchronous). Any pointer may be NULL.
+ *   perm      : [n] int32, user index of each Morton-ordered surfel.
+ *   keys      : [n] uint32, sorted 30-bit Morton codes.
+ *   nodes     : [max(n-1,1), 16] float32, internal nodes: child 0 box
+ *               (lo xyz, hi xyz), child 1 box, then the two child ids as
+ *               int32 bits (>= 0 internal node, < 0 leaf ~m, INT32_MIN none),
+ *               then two unused words.
+ *   leaf_boxes: [n, 6] float32, (lo xyz, hi xyz) of each Morton-ordered leaf.
+ */
+irgs_status irgs_scene_export(irgs_scene scene, int32_t* perm, uint32_t* keys, float* nodes,
+                              float* leaf_boxes);
+
+/*
+ * Forward trace, Trace(r_o, r_d) of Eq. 8 for n_rays rays. For each ray
+ * every surfel hit with t_min < tau < t_max is found (Eq. 6-7: tau =
+ * n.(mu - o)/(n.d), u = (p - mu).t_u / s_u, v = (p - mu).t_v / s_v, alpha =
+ * min(alpha_max, o exp(-(u^2+v^2)/2)), kept if rho <= rho_c and alpha >=
+ * alpha_min, no hit if |n.d| < 1e-8 |d|), and hits are blended front to back
+ * in (tau, index) order with a k-buffer (Eq. 2): w = T alpha, T *= 1 - alpha,
+ * stopping after the hit that makes T < T_min.
+ *   ray_o, ray_d  : [n_rays, 3] origins and directions (any non-zero length;
+ *                   tau is in units of |d|).
+ *   out_feat      : [n_rays, feat_count] sum of w f (Eq. 8/9, unnormalised).
+ *   out_depth     : [n_rays] sum of w tau (Eq. 9, unnormalised).
+ *   out_opacity   : [n_rays] 1 - T_final (o_rt of Eq. 8).
+ *   out_nhits     : [n_rays] int32 blended hits, or NULL.
+ *   out_hit_ids   : [n_rays, max_hit_ids] int32 user indices of the first
+ *                   blended hits in order, -1 padded, or NULL (debugging).
+ * Outputs are overwritten. n_rays may be 0.
+ */
+irgs_status irgs_trace_forward(irgs_scene scene, const float* ray_o, const float* ray_d,
+                               int64_t n_rays, const irgs_trace_params* params,
+                               float* out_feat, float* out_depth, float* out_opacity,
+                               int32_t* out_nhits, int32_t* out_hit_ids, int32_t max_hit_ids,
+                               void* stream);
+
+/*
+ * Backward of irgs_trace_forward for the loss
+ *   L = sum_r g_feat[r].feat[r] + g_depth[r] depth[r] + g_opacity[r] opacity[r].
+ * The kernel replays each ray's k-buffer march, recomputing the hits (no hit
+ * list is stored), and ADDS dL/d(parameter) into the user-order gradient
+ * arrays with atomics (the caller zeroes them first).
+ *   out_feat, out_depth, out_opacity, out_nhits: the forward's outputs for
+ *                   the same scene, rays and params (required).
+ *   g_feat [n_rays, feat_count], g_depth [n_rays], g_opacity [n_rays]:
+ *                   upstream gradients; g_depth / g_opacity may be NULL (0).
+ *   g_means [n,3], g_quats [n,4] (w.r.t. the raw, unnormalised quaternion),
+ *   g_scales [n,2], g_opacity_param [n], g_features [n, num_features]
+ *                   (only the traced channel range receives gradient).
+ * The surfel gradient pointers must all be non-NULL.
+ */
+irgs_status irgs_trace_backward(irgs_scene scene, const float* ray_o, const float* ray_d,
+                                int64_t n_rays, const irgs_trace_params* params,
+                                const float* out_feat, const float* out_depth,
+                                const float* out_opacity, const int32_t* out_nhits,
+                                const float* g_feat, const float* g_depth, const float* g_opacity,
+                                float* g_means, float* g_quats, float* g_scales,
+                                float* g_opacity_param, float* g_features, void* stream);
+
+/*
+ * Monte Carlo rendering equation at G-buffer points (Eq. 3, 15), with the
+ * dielectric BRDF of Eq. 4 and incident light L_i = V L_dir + L_ind whose
+ * (L_ind, 1 - V) come from tracing (x, w_i) (Eq. 13-14). Incident directions
+ * are importance sampled per lobe (supplementary "Composited scene details"):
+ * n_diffuse cosine-weighted samples estimate the diffuse term (estimate
+ * a L_i each) and n_spec GGX samples (alpha_g = roughness^2) estimate the
+ * specular term (estimate F G (w_o.h) L_i / ((n.w_o)(n.h)) each; a sample
+ * below the horizon adds 0 but counts). D is GGX, F is Schlick with F0 = 0.04
+ * on (w_o.h), G is separable Schlick-GGX with k = alpha_g / 2. The normal is
+ * flipped when n.w_o <= 0. Random numbers: SplitMix64 stream of `seed`,
+ * output index (p * (n_diffuse + n_spec) + s) * 2 + dim, top 24 bits.
+ *   x, n, albedo, wo : [n_points, 3]; rough : [n_points].
+ *   env   : [env_h, env_w, 3] equirectangular radiance, z up, row = polar
+ *           angle acos(z), column = azimuth atan2(y, x) from -pi; bilinear,
+ *           wrapping in azimuth and clamping in polar angle.
+ *   params: the secondary-ray trace; feat_count must be 3 (radiance c of the
+ *           surfels, Sec. 3.3) and t_min > 0 is the self-hit offset.
+ *   out_rgb [n_points, 3]; out_vis [n_points] and out_ind [n_points, 3]
+ *           (means of V and L_ind over the cosine samples) may be NULL.
+ * Results do not depend on how points are batched into calls.
+ */
+irgs_status irgs_shade_mc(irgs_scene scene, const float* x, const float* n, const float* albedo,
+                          const float* rough, const float* wo, int64_t n_points, const float* env,
+                          int32_t env_h, int32_t env_w, int32_t n_diffuse, int32_t n_spec,
+                          uint64_t seed, const irgs_trace_params* params, float* out_rgb,
+                          float* out_vis, float* out_ind, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IRGS_H */

@@ -1,0 +1,262 @@
+"""GB300 differentiable 2D Gaussian ray tracer (IRGS, arXiv 2412.15867).
+
+Thin Python binding over the C ABI of libirgs.so (include/irgs.h). Every step
+of the path runs in the library's CUDA kernels; this module only marshals
+torch tensors (device memory) and the current CUDA stream into the calls.
+
+    scene = Scene(means, quats, scales, opacity, features, alpha_min=1/255)
+    feat, depth, opac = trace(scene, ray_o, ray_d, TraceParams(k=16, feat_count=10))
+    (feat.sum() + depth.sum()).backward()      # gradients into the surfel tensors
+    rgb = shade_mc(scene, x, n, albedo, rough, wo, env, 32, 32, seed, params)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from dataclasses import dataclass, replace
+
+import torch
+
+from . import _lib
+from ._lib import IrgsError
+
+__all__ = ["TraceParams", "Scene", "trace", "trace_forward", "trace_backward", "shade_mc",
+           "IrgsError", "library_path"]
+
+
+def library_path() -> str:
+    return _lib.LIB_PATH
+
+
+@dataclass(frozen=True)
+class TraceParams:
+    """Parameters of a trace (irgs_trace_params)."""
+    k: int = 16
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    T_min: float = 1e-4
+    t_min: float = 0.0
+    t_max: float = math.inf
+    feat_offset: int = 0
+    feat_count: int = 3
+
+    def c(self) -> _lib.TraceParamsC:
+        return _lib.TraceParamsC(int(self.k), float(self.alpha_min), float(self.alpha_max),
+                                 float(self.T_min), float(self.t_min), float(self.t_max),
+                                 int(self.feat_offset), int(self.feat_count), 0)
+
+    def with_(self, **kw) -> "TraceParams":
+        return replace(self, **kw)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(device) -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev_f32(t: torch.Tensor, name: str, shape_last=None) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32, got {t.dtype}")
+    if shape_last is not None and (t.dim() < 1 or t.shape[-1] != shape_last):
+        raise ValueError(f"{name} must have last dimension {shape_last}, got {tuple(t.shape)}")
+    return t.contiguous()
+
+
+class Scene:
+    """A resident scene: Morton-ordered surfel copy + LBVH built on the GPU.
+
+    The tensors it was built from are kept so that `trace` can route
+    gradients to them; the library itself only keeps its own copies."""
+
+    def __init__(self, means, quats, scales, opacity, features=None, alpha_min: float = 1.0 / 255.0):
+        self.means = _dev_f32(means, "means", 3)
+        n = self.means.shape[0]
+        self.quats = _dev_f32(quats, "quats", 4)
+        self.scales = _dev_f32(scales, "scales", 2)
+        self.opacity = _dev_f32(opacity, "opacity").reshape(n)
+        if features is None:
+            features = torch.zeros((n, 0), device=self.means.device, dtype=torch.float32)
+        self.features = _dev_f32(features, "features")
+        if self.features.dim() == 1:
+            self.features = self.features.reshape(n, 1)
+        for name, t in (("quats", self.quats), ("scales", self.scales), ("features", self.features)):
+            if t.shape[0] != n:
+                raise ValueError(f"{name} has {t.shape[0]} rows, means has {n}")
+        self.device = self.means.device
+        self.alpha_min = float(alpha_min)
+        self.num_features = int(self.features.shape[1])
+        self.n = int(n)
+        L = _lib.lib()
+        s = _lib.Surfels(self.means.data_ptr() if n else None, self.quats.data_ptr() if n else None,
+                         self.scales.data_ptr() if n else None, self.opacity.data_ptr() if n else None,
+                         self.features.data_ptr() if (n and self.num_features) else None,
+                         n, self.num_features)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(L.irgs_build_scene(C.byref(s), self.alpha_min, _stream(self.device), C.byref(h)),
+                       "irgs_build_scene")
+        self._h = h
+
+    @property
+    def handle(self) -> C.c_void_p:
+        if self._h is None:
+            raise ValueError("scene is closed")
+        return self._h
+
+    def device_bytes(self) -> int:
+        b = C.c_int64()
+        _lib.check(_lib.lib().irgs_scene_info(self.handle, None, None, None, C.byref(b)), "irgs_scene_info")
+        return int(b.value)
+
+    def status(self) -> int:
+        """Synchronise and return (and clear) the device error bits."""
+        bits = C.c_uint32()
+        _lib.lib().irgs_scene_status(self.handle, _stream(self.device), C.byref(bits))
+        return int(bits.value)
+
+    def export(self):
+        """Host copies of (perm, keys, nodes[max(n-1,1),16], leaf_boxes[n,6])."""
+        import numpy as np
+        n = self.n
+        perm = np.zeros(max(n, 1), np.int32)
+        keys = np.zeros(max(n, 1), np.uint32)
+        nodes = np.zeros((max(n - 1, 1), 16), np.float32)
+        boxes = np.zeros((max(n, 1), 6), np.float32)
+        p = lambda a: a.ctypes.data_as(C.c_void_p)
+        _lib.check(_lib.lib().irgs_scene_export(self.handle, p(perm), p(keys), p(nodes), p(boxes)),
+                   "irgs_scene_export")
+        return perm[:n], keys[:n], nodes, boxes[:n]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            _lib.lib().irgs_destroy_scene(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _rays(scene: Scene, ray_o, ray_d):
+    o = _dev_f32(ray_o, "ray_o", 3).reshape(-1, 3)
+    d = _dev_f32(ray_d, "ray_d", 3).reshape(-1, 3)
+    if o.shape != d.shape:
+        raise ValueError("ray_o and ray_d must have the same shape")
+    return o, d
+
+
+def trace_forward(scene: Scene, ray_o, ray_d, params: TraceParams = TraceParams(), max_hit_ids: int = 0,
+                  out=None):
+    """Forward trace (Eq. 8). Returns dict feat [R,Fc], depth [R], opacity [R],
+    n_hits [R] int32 and, if max_hit_ids > 0, hit_ids [R,max_hit_ids]."""
+    o, d = _rays(scene, ray_o, ray_d)
+    R = o.shape[0]
+    dev = scene.device
+    if out is None:
+        out = {"feat": torch.empty((R, params.feat_count), device=dev, dtype=torch.float32),
+               "depth": torch.empty(R, device=dev, dtype=torch.float32),
+               "opacity": torch.empty(R, device=dev, dtype=torch.float32),
+               "n_hits": torch.empty(R, device=dev, dtype=torch.int32)}
+    ids = None
+    if max_hit_ids > 0:
+        ids = torch.empty((R, max_hit_ids), device=dev, dtype=torch.int32)
+        out["hit_ids"] = ids
+    p = params.c()
+    with torch.cuda.device(dev):
+        _lib.check(_lib.lib().irgs_trace_forward(
+            scene.handle, _ptr(o), _ptr(d), R, C.byref(p), _ptr(out["feat"]), _ptr(out["depth"]),
+            _ptr(out["opacity"]), _ptr(out["n_hits"]), _ptr(ids), int(max_hit_ids), _stream(dev)),
+            "irgs_trace_forward")
+    return out
+
+
+def trace_backward(scene: Scene, ray_o, ray_d, params: TraceParams, fwd: dict, g_feat, g_depth=None,
+                   g_opacity=None, grads=None):
+    """Backward of trace_forward; returns (or accumulates into) a dict of
+    user-order gradients means/quats/scales/opacity/features."""
+    o, d = _rays(scene, ray_o, ray_d)
+    R = o.shape[0]
+    dev = scene.device
+    n = scene.n
+    if grads is None:
+        grads = {"means": torch.zeros((n, 3), device=dev), "quats": torch.zeros((n, 4), device=dev),
+                 "scales": torch.zeros((n, 2), device=dev), "opacity": torch.zeros(n, device=dev),
+                 "features": torch.zeros((n, scene.num_features), device=dev)}
+    gf = _dev_f32(g_feat, "g_feat").reshape(R, params.feat_count)
+    gd = None if g_depth is None else _dev_f32(g_depth, "g_depth").reshape(R)
+    go = None if g_opacity is None else _dev_f32(g_opacity, "g_opacity").reshape(R)
+    p = params.c()
+    with torch.cuda.device(dev):
+        _lib.check(_lib.lib().irgs_trace_backward(
+            scene.handle, _ptr(o), _ptr(d), R, C.byref(p), _ptr(fwd["feat"]), _ptr(fwd["depth"]),
+            _ptr(fwd["opacity"]), _ptr(fwd["n_hits"]), _ptr(gf), _ptr(gd), _ptr(go),
+            _ptr(grads["means"]), _ptr(grads["quats"]), _ptr(grads["scales"]), _ptr(grads["opacity"]),
+            _ptr(grads["features"]) if scene.num_features else None, _stream(dev)),
+            "irgs_trace_backward")
+    return grads
+
+
+class _TraceFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, quats, scales, opacity, features, ray_o, ray_d, scene, params):
+        out = trace_forward(scene, ray_o, ray_d, params)
+        ctx.scene, ctx.params = scene, params
+        ctx.save_for_backward(ray_o, ray_d, out["feat"], out["depth"], out["opacity"], out["n_hits"])
+        ctx.mark_non_differentiable(out["n_hits"])
+        return out["feat"], out["depth"], out["opacity"], out["n_hits"]
+
+    @staticmethod
+    def backward(ctx, g_feat, g_depth, g_opac, _g_nh):
+        ro, rd, feat, depth, opac, nh = ctx.saved_tensors
+        scene, params = ctx.scene, ctx.params
+        R = ro.reshape(-1, 3).shape[0]
+        dev = scene.device
+        zf = lambda: torch.zeros((R, params.feat_count), device=dev)
+        g_feat = zf() if g_feat is None else g_feat
+        g = trace_backward(scene, ro, rd, params, {"feat": feat, "depth": depth, "opacity": opac, "n_hits": nh},
+                           g_feat, g_depth, g_opac)
+        return (g["means"], g["quats"], g["scales"], g["opacity"].reshape(scene.opacity.shape),
+                g["features"], None, None, None, None)
+
+
+def trace(scene: Scene, ray_o, ray_d, params: TraceParams = TraceParams()):
+    """Differentiable Trace(r_o, r_d): returns (feat, depth, opacity, n_hits);
+    gradients flow to the tensors the scene was built from."""
+    return _TraceFn.apply(scene.means, scene.quats, scene.scales, scene.opacity, scene.features,
+                          ray_o, ray_d, scene, params)
+
+
+def shade_mc(scene: Scene, x, n, albedo, rough, wo, env, n_diffuse: int, n_spec: int, seed: int,
+             params: TraceParams, want_aux: bool = False, out=None):
+    """Monte Carlo rendering equation per G-buffer point (Eq. 13-15).
+    Returns rgb [P,3] (and, with want_aux, vis [P] and ind [P,3])."""
+    x = _dev_f32(x, "x", 3).reshape(-1, 3)
+    P = x.shape[0]
+    n = _dev_f32(n, "n", 3).reshape(P, 3)
+    albedo = _dev_f32(albedo, "albedo", 3).reshape(P, 3)
+    rough = _dev_f32(rough, "rough").reshape(P)
+    wo = _dev_f32(wo, "wo", 3).reshape(P, 3)
+    env = _dev_f32(env, "env", 3)
+    if env.dim() != 3:
+        raise ValueError("env must be [H, W, 3]")
+    dev = scene.device
+    if out is None:
+        out = {"rgb": torch.empty((P, 3), device=dev)}
+        if want_aux:
+            out["vis"] = torch.empty(P, device=dev)
+            out["ind"] = torch.empty((P, 3), device=dev)
+    p = params.c()
+    with torch.cuda.device(dev):
+        _lib.check(_lib.lib().irgs_shade_mc(
+            scene.handle, _ptr(x), _ptr(n), _ptr(albedo), _ptr(rough), _ptr(wo), P, _ptr(env),
+            int(env.shape[0]), int(env.shape[1]), int(n_diffuse), int(n_spec),
+            C.c_uint64(int(seed) & (2 ** 64 - 1)), C.byref(p), _ptr(out["rgb"]), _ptr(out.get("vis")),
+            _ptr(out.get("ind")), _stream(dev)), "irgs_shade_mc")
+    return out

@@ -1,0 +1,175 @@
+// C ABI of libirgs.so (declared in include/irgs.h): argument validation,
+// device selection and dispatch to the kernels' launchers.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/irgs.h"
+#include "scene.h"
+
+namespace {
+
+bool finite(float x) { return isfinite(x) != 0; }
+
+// Validate trace parameters against a scene. t_max may be +inf.
+irgs_status check_params(const irgs_scene sc, const irgs_trace_params* p) {
+    if (p == nullptr) return IRGS_ERR_INVALID_ARG;
+    if (!irgs::k_supported(p->k)) return IRGS_ERR_UNSUPPORTED;
+    if (!finite(p->alpha_min) || !(p->alpha_min >= sc->alpha_min) || !(p->alpha_min > 0.f))
+        return IRGS_ERR_INVALID_ARG;
+    if (!finite(p->alpha_max) || !(p->alpha_max > p->alpha_min) || !(p->alpha_max <= 1.f))
+        return IRGS_ERR_INVALID_ARG;
+    if (!finite(p->T_min) || !(p->T_min >= 0.f) || !(p->T_min < 1.f)) return IRGS_ERR_INVALID_ARG;
+    if (!finite(p->t_min) || !(p->t_min >= 0.f)) return IRGS_ERR_INVALID_ARG;
+    if (isnan(p->t_max) || !(p->t_max > p->t_min)) return IRGS_ERR_INVALID_ARG;
+    if (p->feat_count < 0 || p->feat_count > IRGS_MAX_FEATURES) return IRGS_ERR_INVALID_ARG;
+    if (p->feat_count > 0 && (p->feat_offset < 0 || p->feat_offset + p->feat_count > sc->F))
+        return IRGS_ERR_INVALID_ARG;
+    if (p->flags != 0u) return IRGS_ERR_INVALID_ARG;
+    return IRGS_OK;
+}
+
+irgs_status use_device(const irgs_scene sc) {
+    return cudaSetDevice(sc->device) == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* irgs_status_string(irgs_status s) {
+    switch (s) {
+        case IRGS_OK: return "ok";
+        case IRGS_ERR_INVALID_ARG: return "invalid argument";
+        case IRGS_ERR_OOM: return "out of device memory";
+        case IRGS_ERR_CUDA: return "CUDA error";
+        case IRGS_ERR_NONFINITE: return "non-finite input";
+        case IRGS_ERR_TIMEOUT: return "device wait timed out";
+        case IRGS_ERR_UNSUPPORTED: return "unsupported configuration";
+        case IRGS_ERR_DEVICE: return "device-side error recorded";
+    }
+    return "unknown status";
+}
+
+int32_t irgs_abi_version(void) { return IRGS_ABI_VERSION; }
+
+irgs_status irgs_build_scene(const irgs_surfels* s, float alpha_min, void* stream, irgs_scene* out) {
+    if (s == nullptr || out == nullptr) return IRGS_ERR_INVALID_ARG;
+    if (s->n < 0 || s->n >= INT32_MAX) return IRGS_ERR_INVALID_ARG;
+    if (s->num_features < 0 || s->num_features > 64) return IRGS_ERR_INVALID_ARG;
+    if (!finite(alpha_min) || !(alpha_min > 0.f) || !(alpha_min < 1.f)) return IRGS_ERR_INVALID_ARG;
+    if (s->n > 0 && (!s->means || !s->quats || !s->scales || !s->opacity)) return IRGS_ERR_INVALID_ARG;
+    if (s->n > 0 && s->num_features > 0 && !s->features) return IRGS_ERR_INVALID_ARG;
+    if (s->num_features == 0 && s->features) return IRGS_ERR_INVALID_ARG;
+    if (s->n > 0) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, s->means) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return IRGS_ERR_INVALID_ARG;
+        }
+        if (cudaSetDevice(at.device) != cudaSuccess) return IRGS_ERR_CUDA;
+    }
+    return irgs::build_scene_impl(s, alpha_min, static_cast<cudaStream_t>(stream), out);
+}
+
+irgs_status irgs_destroy_scene(irgs_scene sc) {
+    if (sc == nullptr) return IRGS_OK;
+    cudaSetDevice(sc->device);
+    cudaDeviceSynchronize();
+    irgs::free_scene(sc);
+    return IRGS_OK;
+}
+
+irgs_status irgs_scene_info(irgs_scene sc, int64_t* n, int32_t* F, float* alpha_min, int64_t* bytes) {
+    if (sc == nullptr) return IRGS_ERR_INVALID_ARG;
+    if (n) *n = sc->n;
+    if (F) *F = sc->F;
+    if (alpha_min) *alpha_min = sc->alpha_min;
+    if (bytes) *bytes = sc->bytes;
+    return IRGS_OK;
+}
+
+irgs_status irgs_scene_status(irgs_scene sc, void* stream, uint32_t* bits) {
+    if (sc == nullptr) return IRGS_ERR_INVALID_ARG;
+    if (use_device(sc) != IRGS_OK) return IRGS_ERR_CUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t h = 0;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return IRGS_ERR_CUDA;
+    if (cudaMemcpy(&h, sc->status, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return IRGS_ERR_CUDA;
+    if (cudaMemset(sc->status, 0, sizeof(uint32_t)) != cudaSuccess) return IRGS_ERR_CUDA;
+    if (bits) *bits = h;
+    return h == 0u ? IRGS_OK : IRGS_ERR_DEVICE;
+}
+
+irgs_status irgs_scene_export(irgs_scene sc, int32_t* perm, uint32_t* keys, float* nodes, float* leaf_boxes) {
+    if (sc == nullptr) return IRGS_ERR_INVALID_ARG;
+    if (use_device(sc) != IRGS_OK) return IRGS_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return IRGS_ERR_CUDA;
+    const int64_t n = sc->n, nn = n > 1 ? n - 1 : 1;
+    cudaError_t e = cudaSuccess;
+    if (perm && n > 0) e = cudaMemcpy(perm, sc->perm, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && keys && n > 0) e = cudaMemcpy(keys, sc->keys, sizeof(uint32_t) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && nodes) e = cudaMemcpy(nodes, sc->nodes, sizeof(irgs::Node) * nn, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && leaf_boxes && n > 0)
+        e = cudaMemcpy(leaf_boxes, sc->leaf_box, sizeof(float) * 6 * n, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+}
+
+irgs_status irgs_trace_forward(irgs_scene sc, const float* ray_o, const float* ray_d, int64_t n_rays,
+                               const irgs_trace_params* params, float* out_feat, float* out_depth,
+                               float* out_opacity, int32_t* out_nhits, int32_t* out_hit_ids, int32_t max_hit_ids,
+                               void* stream) {
+    if (sc == nullptr || n_rays < 0) return IRGS_ERR_INVALID_ARG;
+    irgs_status s = check_params(sc, params);
+    if (s != IRGS_OK) return s;
+    if (n_rays > 0 && (!ray_o || !ray_d || !out_depth || !out_opacity)) return IRGS_ERR_INVALID_ARG;
+    if (n_rays > 0 && params->feat_count > 0 && !out_feat) return IRGS_ERR_INVALID_ARG;
+    if (out_hit_ids && max_hit_ids <= 0) return IRGS_ERR_INVALID_ARG;
+    if (n_rays >= (int64_t)UINT32_MAX * 128) return IRGS_ERR_INVALID_ARG;
+    if ((s = use_device(sc)) != IRGS_OK) return s;
+    return irgs::launch_trace_forward(sc->view(), ray_o, ray_d, n_rays, *params, out_feat, out_depth, out_opacity,
+                                      out_nhits, out_hit_ids, out_hit_ids ? max_hit_ids : 0,
+                                      static_cast<cudaStream_t>(stream));
+}
+
+irgs_status irgs_trace_backward(irgs_scene sc, const float* ray_o, const float* ray_d, int64_t n_rays,
+                                const irgs_trace_params* params, const float* out_feat, const float* out_depth,
+                                const float* out_opacity, const int32_t* out_nhits, const float* g_feat,
+                                const float* g_depth, const float* g_opacity, float* g_means, float* g_quats,
+                                float* g_scales, float* g_opacity_param, float* g_features, void* stream) {
+    if (sc == nullptr || n_rays < 0) return IRGS_ERR_INVALID_ARG;
+    irgs_status s = check_params(sc, params);
+    if (s != IRGS_OK) return s;
+    if (params->k != 8 && params->k != 16) return IRGS_ERR_UNSUPPORTED;
+    if (n_rays > 0 && (!ray_o || !ray_d || !out_depth || !out_opacity || !out_nhits)) return IRGS_ERR_INVALID_ARG;
+    if (n_rays > 0 && params->feat_count > 0 && (!out_feat || !g_feat)) return IRGS_ERR_INVALID_ARG;
+    if (sc->n > 0 && (!g_means || !g_quats || !g_scales || !g_opacity_param)) return IRGS_ERR_INVALID_ARG;
+    if (sc->n > 0 && sc->F > 0 && params->feat_count > 0 && !g_features) return IRGS_ERR_INVALID_ARG;
+    if (n_rays >= (int64_t)UINT32_MAX * 128) return IRGS_ERR_INVALID_ARG;
+    if ((s = use_device(sc)) != IRGS_OK) return s;
+    return irgs::launch_trace_backward(sc->view(), ray_o, ray_d, n_rays, *params, out_feat, out_depth, out_opacity,
+                                       out_nhits, g_feat, g_depth, g_opacity, g_means, g_quats, g_scales,
+                                       g_opacity_param, g_features, static_cast<cudaStream_t>(stream));
+}
+
+irgs_status irgs_shade_mc(irgs_scene sc, const float* x, const float* n, const float* albedo, const float* rough,
+                          const float* wo, int64_t n_points, const float* env, int32_t env_h, int32_t env_w,
+                          int32_t n_diffuse, int32_t n_spec, uint64_t seed, const irgs_trace_params* params,
+                          float* out_rgb, float* out_vis, float* out_ind, void* stream) {
+    if (sc == nullptr || n_points < 0) return IRGS_ERR_INVALID_ARG;
+    irgs_status s = check_params(sc, params);
+    if (s != IRGS_OK) return s;
+    if (params->k != 8 && params->k != 16) return IRGS_ERR_UNSUPPORTED;
+    if (params->feat_count != 3 || !(params->t_min > 0.f)) return IRGS_ERR_INVALID_ARG;
+    if (n_diffuse < 0 || n_spec < 0 || n_diffuse + n_spec <= 0 || n_diffuse + n_spec > (1 << 24))
+        return IRGS_ERR_INVALID_ARG;
+    if (env_h <= 0 || env_w <= 0 || !env) return IRGS_ERR_INVALID_ARG;
+    if (n_points > 0 && (!x || !n || !albedo || !rough || !wo || !out_rgb)) return IRGS_ERR_INVALID_ARG;
+    if (n_points >= (int64_t)UINT32_MAX * 4) return IRGS_ERR_INVALID_ARG;
+    if ((s = use_device(sc)) != IRGS_OK) return s;
+    return irgs::launch_shade_mc(sc->view(), x, n, albedo, rough, wo, n_points, env, env_h, env_w, n_diffuse, n_spec,
+                                 seed, *params, out_rgb, out_vis, out_ind, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,447 @@
+// Scene construction: surfel packing and support boxes (K1), Morton codes (K2),
+// stable LSD radix sort (K3), Karras hierarchy emission (K4) and bottom-up box
+// refit (K5). IRGS bounds each 2D Gaussian by a proxy enclosing the region
+// where its response reaches alpha_min (Sec. 3.2, Eq. 5) and builds a BVH over
+// the proxies; here the proxy is the axis-aligned box of the support disk and
+// the BVH is a linear BVH built entirely on the device.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+
+#include "common.cuh"
+#include "scene.h"
+
+namespace irgs {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortChunks = 16;                             // 32-key chunks per warp
+constexpr int kTile = kSortThreads * kSortChunks;           // 4096 keys per tile
+
+__device__ __forceinline__ uint32_t f2ord(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// ---------------------------------------------------------------------------
+// K1: per-surfel frame (FP64, then rounded once), support radius, packed
+// record (user order) and padded support-disk box; centroid bounds.
+__global__ void k_surfel_boxes(const float* __restrict__ means, const float* __restrict__ quats,
+                               const float* __restrict__ scales, const float* __restrict__ opac,
+                               int64_t n, double alpha_min, float4* __restrict__ rec_user,
+                               float* __restrict__ box_user, uint32_t* __restrict__ bounds) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float cmin[3] = {INFINITY, INFINITY, INFINITY}, cmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (i < n) {
+        double mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+        double w = quats[4 * i], x = quats[4 * i + 1], y = quats[4 * i + 2], z = quats[4 * i + 3];
+        double su = scales[2 * i], sv = scales[2 * i + 1];
+        double o = opac[i];
+        double qn = sqrt(w * w + x * x + y * y + z * z);
+        bool ok = qn > 0.0 && isfinite(qn) && su > 0.0 && sv > 0.0 && isfinite(su) && isfinite(sv) &&
+                  isfinite(mu[0]) && isfinite(mu[1]) && isfinite(mu[2]) && isfinite(o);
+        double tu[3] = {1, 0, 0}, tv[3] = {0, 1, 0}, nn[3] = {0, 0, 1};
+        if (ok) {
+            w /= qn; x /= qn; y /= qn; z /= qn;
+            // rotation columns of the unit quaternion (w,x,y,z)
+            tu[0] = 1.0 - 2.0 * (y * y + z * z); tu[1] = 2.0 * (x * y + w * z); tu[2] = 2.0 * (x * z - w * y);
+            tv[0] = 2.0 * (x * y - w * z); tv[1] = 1.0 - 2.0 * (x * x + z * z); tv[2] = 2.0 * (y * z + w * x);
+            nn[0] = 2.0 * (x * z + w * y); nn[1] = 2.0 * (y * z - w * x); nn[2] = 1.0 - 2.0 * (x * x + y * y);
+        }
+        // support radius: alpha reaches alpha_min at rho^2 = 2 ln(o/alpha_min), capped at 3 sigma
+        double rc2 = -1.0;
+        if (ok && o > 0.0) {
+            double r2 = 2.0 * log(o / alpha_min);
+            rc2 = r2 < 9.0 ? r2 : 9.0;
+        }
+        if (!(rc2 >= 0.0)) rc2 = -1.0;
+        if (!ok) su = sv = 1.0;
+        float4* R = rec_user + 4 * i;
+        int32_t uid = (int32_t)i;
+        R[0] = make_float4((float)mu[0], (float)mu[1], (float)mu[2], (float)o);
+        R[1] = make_float4((float)(tu[0] / su), (float)(tu[1] / su), (float)(tu[2] / su), (float)rc2);
+        R[2] = make_float4((float)(tv[0] / sv), (float)(tv[1] / sv), (float)(tv[2] / sv), __int_as_float(uid));
+        R[3] = make_float4((float)nn[0], (float)nn[1], (float)nn[2], 0.f);
+        double rc = rc2 >= 0.0 ? sqrt(rc2) : 0.0;
+        float* B = box_user + 6 * i;
+        for (int k = 0; k < 3; ++k) {
+            double m = ok ? mu[k] : 0.0;
+            double a = su * tu[k], b = sv * tv[k];
+            double e = rc * sqrt(a * a + b * b);
+            e = e * (1.0 + 1e-5) + 1e-6 * (1.0 + fabs(m));
+            if (rc2 < 0.0) e = 0.0;   // never hit: a point box at the centre
+            B[k] = __double2float_rd(m - e);
+            B[3 + k] = __double2float_ru(m + e);
+            cmin[k] = cmax[k] = (float)m;
+        }
+    }
+    // block reduction of the centroid bounds
+    for (int k = 0; k < 3; ++k) {
+        for (int off = 16; off > 0; off >>= 1) {
+            cmin[k] = fminf(cmin[k], __shfl_xor_sync(0xffffffffu, cmin[k], off));
+            cmax[k] = fmaxf(cmax[k], __shfl_xor_sync(0xffffffffu, cmax[k], off));
+        }
+    }
+    if ((threadIdx.x & 31) == 0 && cmin[0] <= cmax[0]) {
+        for (int k = 0; k < 3; ++k) {
+            atomicMin(&bounds[k], f2ord(cmin[k]));
+            atomicMax(&bounds[3 + k], f2ord(cmax[k]));
+        }
+    }
+}
+
+// K2: 30-bit Morton code of each centre inside the centroid bounds.
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void k_morton(const float4* __restrict__ rec_user, int64_t n, const uint32_t* __restrict__ bounds,
+                         uint32_t* __restrict__ keys, int32_t* __restrict__ vals) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 r0 = rec_user[4 * i];
+    float c[3] = {r0.x, r0.y, r0.z};
+    uint32_t q[3];
+    for (int k = 0; k < 3; ++k) {
+        float lo = ord2f(bounds[k]), hi = ord2f(bounds[3 + k]);
+        float ext = hi - lo;
+        float t = ext > 0.f ? (c[k] - lo) / ext : 0.5f;
+        int v = (int)(t * 1024.0f);
+        v = v < 0 ? 0 : (v > 1023 ? 1023 : v);
+        if (!(t == t)) v = 0;
+        q[k] = (uint32_t)v;
+    }
+    keys[i] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+    vals[i] = (int32_t)i;
+}
+
+// ---------------------------------------------------------------------------
+// K3: stable LSD radix sort, 8 bits per pass. Per pass: tile histograms,
+// one exclusive scan over (digit, tile), and a stable scatter that ranks keys
+// inside a tile with warp match masks in (warp, chunk, lane) order.
+__global__ void k_sort_hist(const uint32_t* __restrict__ keys, int64_t n, int shift, int tiles,
+                            uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[256];
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) h[d] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * kTile;
+    for (int j = threadIdx.x; j < kTile; j += blockDim.x) {
+        int64_t i = base + j;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * tiles + blockIdx.x] = h[d];
+}
+
+// Exclusive scan of `m` counters with one block of 1024 threads.
+__global__ void k_scan_exclusive(uint32_t* __restrict__ a, int64_t m) {
+    __shared__ uint32_t part[1024];
+    int t = threadIdx.x;
+    int64_t per = (m + 1023) / 1024;
+    int64_t b = t * per, e = b + per < m ? b + per : m;
+    uint32_t s = 0;
+    for (int64_t i = b; i < e; ++i) s += a[i];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint32_t v = t >= off ? part[t - off] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[t] - s;   // exclusive prefix of this thread's chunk
+    for (int64_t i = b; i < e; ++i) {
+        uint32_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
+    const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, int64_t n, int shift, int tiles,
+    const uint32_t* __restrict__ offs, uint32_t* __restrict__ kout, int32_t* __restrict__ vout) {
+    __shared__ uint32_t wcnt[kSortWarps][256];
+    __shared__ uint32_t gofs[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+        gofs[d] = offs[(int64_t)d * tiles + blockIdx.x];
+        for (int w = 0; w < kSortWarps; ++w) wcnt[w][d] = 0;
+    }
+    __syncthreads();
+    const int64_t wbase = (int64_t)blockIdx.x * kTile + warp * (32 * kSortChunks);
+    uint32_t key[kSortChunks];
+    int32_t val[kSortChunks];
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int c = 0; c < kSortChunks; ++c) {
+        int64_t i = wbase + c * 32 + lane;
+        key[c] = i < n ? kin[i] : 0u;
+        val[c] = i < n ? vin[i] : 0;
+    }
+    // phase 1: per-warp digit counts
+#pragma unroll
+    for (int c = 0; c < kSortChunks; ++c) {
+        int64_t i = wbase + c * 32 + lane;
+        uint32_t dg = i < n ? ((key[c] >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, dg);
+        if (dg < 256u && (peers & lt) == 0u) wcnt[warp][dg] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // phase 2: exclusive scan over warps per digit
+    for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+        uint32_t run = 0;
+        for (int w = 0; w < kSortWarps; ++w) {
+            uint32_t v = wcnt[w][d];
+            wcnt[w][d] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    // phase 3: stable scatter
+#pragma unroll
+    for (int c = 0; c < kSortChunks; ++c) {
+        int64_t i = wbase + c * 32 + lane;
+        uint32_t dg = i < n ? ((key[c] >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, dg);
+        if (dg < 256u) {
+            uint32_t pos = gofs[dg] + wcnt[warp][dg] + __popc(peers & lt);
+            kout[pos] = key[c];
+            vout[pos] = val[c];
+        }
+        __syncwarp();
+        if (dg < 256u && (peers & lt) == 0u) wcnt[warp][dg] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gather into Morton order: packed records, leaf boxes, features, raw
+// quaternions and scales.
+__global__ void k_gather(const int32_t* __restrict__ perm, int64_t n, const float4* __restrict__ rec_user,
+                         const float* __restrict__ box_user, const float* __restrict__ quats,
+                         const float* __restrict__ scales, float4* __restrict__ rec, float* __restrict__ leaf_box,
+                         float4* __restrict__ q_raw, float2* __restrict__ scale) {
+    int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    int64_t u = perm[m];
+    for (int k = 0; k < 4; ++k) rec[4 * m + k] = rec_user[4 * u + k];
+    for (int k = 0; k < 6; ++k) leaf_box[6 * m + k] = box_user[6 * u + k];
+    q_raw[m] = make_float4(quats[4 * u], quats[4 * u + 1], quats[4 * u + 2], quats[4 * u + 3]);
+    scale[m] = make_float2(scales[2 * u], scales[2 * u + 1]);
+}
+
+__global__ void k_gather_feat(const int32_t* __restrict__ perm, int64_t n, int F, const float* __restrict__ fin,
+                              float* __restrict__ fout) {
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n * F) return;
+    int64_t m = j / F, c = j - m * F;
+    fout[j] = fin[(int64_t)perm[m] * F + c];
+}
+
+// ---------------------------------------------------------------------------
+// K4: Karras (2012) hierarchy. delta(i,j) is the common prefix length of the
+// sorted keys, extended by the index bits when keys are equal.
+__device__ __forceinline__ int kdelta(const uint32_t* __restrict__ k, int64_t n, int64_t i, int64_t j) {
+    if (j < 0 || j >= n) return -1;
+    uint32_t a = k[i], b = k[j];
+    if (a == b) return 32 + __clz((uint32_t)i ^ (uint32_t)j);
+    return __clz(a ^ b);
+}
+
+__global__ void k_karras(const uint32_t* __restrict__ keys, int64_t n, Node* __restrict__ nodes,
+                         int32_t* __restrict__ leaf_parent, int32_t* __restrict__ node_parent) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (kdelta(keys, n, i, i + 1) - kdelta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = kdelta(keys, n, i, i - d);
+    int64_t lmax = 2;
+    while (kdelta(keys, n, i, i + lmax * d) > dmin) lmax *= 2;
+    int64_t l = 0;
+    for (int64_t t = lmax / 2; t >= 1; t /= 2)
+        if (kdelta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    int64_t j = i + l * d;
+    int dnode = kdelta(keys, n, i, j);
+    int64_t s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (kdelta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int64_t g = i + s * d + (d < 0 ? -1 : 0);
+    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    int32_t left = (lo == g) ? ~(int32_t)g : (int32_t)g;
+    int32_t right = (hi == g + 1) ? ~(int32_t)(g + 1) : (int32_t)(g + 1);
+    nodes[i].d = make_int4(left, right, 0, 0);
+    if (left < 0) leaf_parent[~left] = (int32_t)i; else node_parent[left] = (int32_t)i;
+    if (right < 0) leaf_parent[~right] = (int32_t)i; else node_parent[right] = (int32_t)i;
+    if (i == 0) node_parent[0] = -1;
+}
+
+// K5: bottom-up refit. The second thread to reach a node writes both child
+// boxes into it and moves up; the first one stops.
+__device__ __forceinline__ void child_box(const Node* nodes, const float* leaf_box, int32_t c, float b[6]) {
+    if (c < 0) {
+        const float* L = leaf_box + 6 * (int64_t)(~c);
+        for (int k = 0; k < 6; ++k) b[k] = __ldcg(L + k);
+    } else {
+        const float4* p = reinterpret_cast<const float4*>(nodes + c);
+        float4 a = __ldcg(p), bb = __ldcg(p + 1), cc = __ldcg(p + 2);
+        b[0] = fminf(a.x, bb.z); b[1] = fminf(a.y, bb.w); b[2] = fminf(a.z, cc.x);
+        b[3] = fmaxf(a.w, cc.y); b[4] = fmaxf(bb.x, cc.z); b[5] = fmaxf(bb.y, cc.w);
+    }
+}
+
+__global__ void k_refit(int64_t n, const float* __restrict__ leaf_box, const int32_t* __restrict__ leaf_parent,
+                        const int32_t* __restrict__ node_parent, Node* nodes, uint32_t* flags, uint32_t* status) {
+    int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    int32_t p = leaf_parent[m];
+    // a valid hierarchy is at most 62 levels deep (30 key bits + 32 index bits)
+    for (int level = 0; p >= 0; ++level) {
+        if (level > 128 || p >= n - 1) {
+            atomicOr(status, kErrBadTree);
+            return;
+        }
+        __threadfence();
+        const uint32_t arrived = atomicAdd(&flags[p], 1u);
+        if (arrived == 0u) return;
+        if (arrived != 1u) {
+            atomicOr(status, kErrBadTree);
+            return;
+        }
+        int4 ch = __ldcg(&nodes[p].d);
+        float b0[6], b1[6];
+        child_box(nodes, leaf_box, ch.x, b0);
+        child_box(nodes, leaf_box, ch.y, b1);
+        nodes[p].a = make_float4(b0[0], b0[1], b0[2], b0[3]);
+        nodes[p].b = make_float4(b0[4], b0[5], b1[0], b1[1]);
+        nodes[p].c = make_float4(b1[2], b1[3], b1[4], b1[5]);
+        p = node_parent[p];
+    }
+}
+
+// Root of a one-surfel (or empty) scene: child 0 = leaf 0 (if any), child 1 absent.
+__global__ void k_tiny_root(int64_t n, const float* __restrict__ leaf_box, Node* nodes) {
+    float b[6] = {0, 0, 0, 0, 0, 0};
+    if (n == 1)
+        for (int k = 0; k < 6; ++k) b[k] = leaf_box[k];
+    nodes[0].a = make_float4(b[0], b[1], b[2], b[3]);
+    nodes[0].b = make_float4(b[4], b[5], 0.f, 0.f);
+    nodes[0].c = make_float4(0.f, 0.f, 0.f, 0.f);
+    nodes[0].d = make_int4(n == 1 ? ~0 : kNoChild, kNoChild, 0, 0);
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count, int64_t& bytes) {
+    size_t b = sizeof(T) * (count > 0 ? count : 1);
+    bytes += (int64_t)b;
+    return cudaMalloc(reinterpret_cast<void**>(p), b);
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
+
+}  // namespace
+
+void free_scene(irgs_scene sc) {
+    if (!sc) return;
+    void* ptrs[] = {sc->nodes, sc->rec, sc->feat, sc->q_raw, sc->scale, sc->leaf_box, sc->keys,
+                    sc->perm, sc->status, sc->rec_user, sc->box_user, sc->keys_tmp, sc->vals_tmp,
+                    sc->hist, sc->bounds, sc->leaf_parent, sc->node_parent, sc->refit_flag};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete sc;
+}
+
+irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_t st, irgs_scene* out) {
+    const int64_t n = s->n;
+    const int32_t F = s->num_features;
+    irgs_scene sc = new (std::nothrow) irgs_scene_s();
+    if (!sc) return IRGS_ERR_OOM;
+    cudaGetDevice(&sc->device);
+    sc->n = n;
+    sc->F = F;
+    sc->alpha_min = alpha_min;
+    const int64_t nn = n > 1 ? n - 1 : 1;
+    const int64_t tiles = (n + kTile - 1) / kTile;
+    int64_t& B = sc->bytes;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(dalloc(&sc->nodes, nn, B));
+    A(dalloc(&sc->rec, 4 * n, B));
+    A(dalloc(&sc->feat, (size_t)n * F, B));
+    A(dalloc(&sc->q_raw, n, B));
+    A(dalloc(&sc->scale, n, B));
+    A(dalloc(&sc->leaf_box, 6 * n, B));
+    A(dalloc(&sc->keys, n, B));
+    A(dalloc(&sc->perm, n, B));
+    A(dalloc(&sc->status, 1, B));
+    A(dalloc(&sc->rec_user, 4 * n, B));
+    A(dalloc(&sc->box_user, 6 * n, B));
+    A(dalloc(&sc->keys_tmp, n, B));
+    A(dalloc(&sc->vals_tmp, n, B));
+    A(dalloc(&sc->hist, 256 * (tiles > 0 ? tiles : 1), B));
+    A(dalloc(&sc->bounds, 6, B));
+    A(dalloc(&sc->leaf_parent, n, B));
+    A(dalloc(&sc->node_parent, nn, B));
+    A(dalloc(&sc->refit_flag, nn, B));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_scene(sc);
+        return e == cudaErrorMemoryAllocation ? IRGS_ERR_OOM : IRGS_ERR_CUDA;
+    }
+    A(cudaMemsetAsync(sc->status, 0, sizeof(uint32_t), st));
+    A(cudaMemsetAsync(sc->nodes, 0, sizeof(Node) * nn, st));
+    A(cudaMemsetAsync(sc->refit_flag, 0, sizeof(uint32_t) * nn, st));
+    // bounds: mins start at the largest ordered value, maxes at the smallest
+    A(cudaMemsetAsync(sc->bounds, 0xff, 3 * sizeof(uint32_t), st));
+    A(cudaMemsetAsync(sc->bounds + 3, 0x00, 3 * sizeof(uint32_t), st));
+    if (n > 0) {
+        const int T = 256;
+        k_surfel_boxes<<<blocks_for(n, T), T, 0, st>>>(s->means, s->quats, s->scales, s->opacity, n,
+                                                       (double)alpha_min, sc->rec_user, sc->box_user, sc->bounds);
+        k_morton<<<blocks_for(n, T), T, 0, st>>>(sc->rec_user, n, sc->bounds, sc->keys, sc->perm);
+        // 4 passes ping-pong: keys/perm -> tmp -> keys/perm ...
+        uint32_t* ka = sc->keys; int32_t* va = sc->perm;
+        uint32_t* kb = sc->keys_tmp; int32_t* vb = sc->vals_tmp;
+        for (int shift = 0; shift < 32; shift += 8) {
+            k_sort_hist<<<(unsigned)tiles, 256, 0, st>>>(ka, n, shift, (int)tiles, sc->hist);
+            k_scan_exclusive<<<1, 1024, 0, st>>>(sc->hist, 256 * tiles);
+            k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(ka, va, n, shift, (int)tiles, sc->hist, kb, vb);
+            uint32_t* tk = ka; ka = kb; kb = tk;
+            int32_t* tv = va; va = vb; vb = tv;
+        }
+        // after an even number of passes the sorted data is back in keys/perm
+        k_gather<<<blocks_for(n, T), T, 0, st>>>(sc->perm, n, sc->rec_user, sc->box_user, s->quats, s->scales,
+                                                 sc->rec, sc->leaf_box, sc->q_raw, sc->scale);
+        if (F > 0)
+            k_gather_feat<<<blocks_for(n * F, T), T, 0, st>>>(sc->perm, n, F, s->features, sc->feat);
+        if (n > 1) {
+            k_karras<<<blocks_for(n - 1, T), T, 0, st>>>(sc->keys, n, sc->nodes, sc->leaf_parent, sc->node_parent);
+            k_refit<<<blocks_for(n, T), T, 0, st>>>(n, sc->leaf_box, sc->leaf_parent, sc->node_parent, sc->nodes,
+                                                    sc->refit_flag, sc->status);
+        }
+    }
+    if (n <= 1) k_tiny_root<<<1, 1, 0, st>>>(n, sc->leaf_box, sc->nodes);
+    A(cudaGetLastError());
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        free_scene(sc);
+        return IRGS_ERR_CUDA;
+    }
+    *out = sc;
+    return IRGS_OK;
+}
+
+}  // namespace irgs

@@ -1,0 +1,81 @@
+// Host-side scene object and the internal launchers each translation unit
+// provides. Not part of the public ABI (see include/irgs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+struct irgs_scene_s {
+    int device = 0;
+    int64_t n = 0;
+    int32_t F = 0;
+    float alpha_min = 0.f;
+    int64_t bytes = 0;
+
+    // persistent scene data (Morton order)
+    irgs::Node* nodes = nullptr;      // [max(n-1,1)]
+    float4* rec = nullptr;            // [n*4]
+    float* feat = nullptr;            // [n*F]
+    float4* q_raw = nullptr;          // [n]
+    float2* scale = nullptr;          // [n]
+    float* leaf_box = nullptr;        // [n*6]
+    uint32_t* keys = nullptr;         // [n] sorted Morton codes
+    int32_t* perm = nullptr;          // [n] user index of Morton slot
+    uint32_t* status = nullptr;       // device error word
+
+    // build scratch (kept for rebuilds)
+    float4* rec_user = nullptr;       // [n*4]
+    float* box_user = nullptr;        // [n*6]
+    uint32_t* keys_tmp = nullptr;     // [n]
+    int32_t* vals_tmp = nullptr;      // [n]
+    uint32_t* hist = nullptr;         // [256 * tiles]
+    uint32_t* bounds = nullptr;       // [6] ordered-bit centroid bounds
+    int32_t* leaf_parent = nullptr;   // [n]
+    int32_t* node_parent = nullptr;   // [max(n-1,1)]
+    uint32_t* refit_flag = nullptr;   // [max(n-1,1)]
+
+    irgs::SceneView view() const {
+        irgs::SceneView v;
+        v.nodes = nodes;
+        v.rec = rec;
+        v.feat = feat;
+        v.q_raw = q_raw;
+        v.scale = scale;
+        v.status = status;
+        v.n = n;
+        v.F = F;
+        v.alpha_min = alpha_min;
+        return v;
+    }
+};
+
+namespace irgs {
+
+// scene.cu
+irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_t st, irgs_scene* out);
+void free_scene(irgs_scene sc);
+
+// trace_fwd.cu
+irgs_status launch_trace_forward(const SceneView& sv, const float* ro, const float* rd, int64_t R,
+                                 const irgs_trace_params& p, float* feat, float* depth, float* opac,
+                                 int32_t* nhits, int32_t* ids, int32_t max_ids, cudaStream_t st);
+// trace_bwd.cu
+irgs_status launch_trace_backward(const SceneView& sv, const float* ro, const float* rd, int64_t R,
+                                  const irgs_trace_params& p, const float* feat, const float* depth,
+                                  const float* opac, const int32_t* nhits, const float* g_feat,
+                                  const float* g_depth, const float* g_opac, float* g_means,
+                                  float* g_quats, float* g_scales, float* g_opacity, float* g_features,
+                                  cudaStream_t st);
+// shade.cu
+irgs_status launch_shade_mc(const SceneView& sv, const float* x, const float* n, const float* albedo,
+                            const float* rough, const float* wo, int64_t P, const float* env, int32_t H,
+                            int32_t W, int32_t n_diffuse, int32_t n_spec, uint64_t seed,
+                            const irgs_trace_params& p, float* rgb, float* vis, float* ind,
+                            cudaStream_t st);
+
+// k-buffer sizes that are compiled in
+inline bool k_supported(int k) { return k == 1 || k == 4 || k == 8 || k == 16 || k == 32; }
+
+}  // namespace irgs

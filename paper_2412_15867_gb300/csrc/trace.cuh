@@ -1,0 +1,319 @@
+// Per-ray traversal of the LBVH with a register k-buffer and front-to-back
+// compositing -- Trace(r_o, r_d) of IRGS Eq. 8 with the intersection of Eq. 6,
+// the response of Eq. 7 and the blending of Eq. 2. Shared by the forward,
+// backward and shading kernels, which must reproduce each other's hit order
+// and arithmetic bit for bit; every operation whose rounding matters is
+// therefore written with explicit round-to-nearest intrinsics.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace irgs {
+
+struct TraceParams {
+    float alpha_min, alpha_max, T_min, t_min, t_max;
+    int32_t off, fc;
+};
+
+struct Ray {
+    f3 o, d;           // origin and direction as given
+    f3 inv;            // 1/d with zero components replaced (slab test only)
+    f3 oinv;           // o * inv
+    float inv_dd;      // 1 / |d|^2
+    float graze;       // 1e-8 |d|
+};
+
+__device__ __forceinline__ Ray make_ray(f3 o, f3 d) {
+    Ray r;
+    r.o = o;
+    r.d = d;
+    auto safe = [](float x) { return fabsf(x) < 1e-20f ? copysignf(1e-20f, x) : x; };
+    r.inv = mk3(1.0f / safe(d.x), 1.0f / safe(d.y), 1.0f / safe(d.z));
+    r.oinv = mk3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+    float dd = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
+    r.inv_dd = 1.0f / dd;
+    r.graze = 1e-8f * sqrtf(dd);
+    return r;
+}
+
+// Geometry of an accepted hit that the backward pass needs.
+struct HitGeom {
+    f3 e;          // p - mu
+    float u, v;    // Eq. 7 local coordinates
+    float G;       // exp(-rho^2/2)
+    float a_raw;   // o G before the clamp
+    float den;     // n . d
+};
+
+// Ray/surfel test (Eq. 6-7) evaluated around a rebased origin
+// o' = o + t_r d, t_r = (mu - o).d / |d|^2 (closest approach to mu), so the
+// cancellation that plain FP32 suffers when |o - mu| >> scale disappears:
+//   a   = mu - o exactly as a float pair (two_sum),
+//   dl  = mu - o' = fma(-t_r, d, a_hi) + a_lo          (small, nearly exact)
+//   tau = t_r + n.dl / n.d,  p - mu = (tau - t_r) d - dl.
+// The depth is returned as the exact pair (kh, kl) = two_sum(t_r, tau - t_r).
+template <bool GEOM>
+__device__ __forceinline__ bool surfel_hit(const float4& r0, const float4& r1, const float4& r2, const float4& r3,
+                                           const Ray& ray, float amin, float amax, float& kh, float& kl,
+                                           float& alpha, HitGeom* g) {
+    float ahx, alx, ahy, aly, ahz, alz;
+    two_sum(r0.x, -ray.o.x, ahx, alx);
+    two_sum(r0.y, -ray.o.y, ahy, aly);
+    two_sum(r0.z, -ray.o.z, ahz, alz);
+    const f3 d = ray.d;
+    float tr = __fmul_rn(__fmaf_rn(ahx, d.x, __fmaf_rn(ahy, d.y, __fmul_rn(ahz, d.z))), ray.inv_dd);
+    float dlx = __fadd_rn(__fmaf_rn(-tr, d.x, ahx), alx);
+    float dly = __fadd_rn(__fmaf_rn(-tr, d.y, ahy), aly);
+    float dlz = __fadd_rn(__fmaf_rn(-tr, d.z, ahz), alz);
+    float den = __fmaf_rn(r3.x, d.x, __fmaf_rn(r3.y, d.y, __fmul_rn(r3.z, d.z)));
+    if (!(fabsf(den) >= ray.graze)) return false;
+    float num = __fmaf_rn(r3.x, dlx, __fmaf_rn(r3.y, dly, __fmul_rn(r3.z, dlz)));
+    float tp = __fdiv_rn(num, den);
+    float ex = __fmaf_rn(tp, d.x, -dlx);
+    float ey = __fmaf_rn(tp, d.y, -dly);
+    float ez = __fmaf_rn(tp, d.z, -dlz);
+    float u = __fmaf_rn(ex, r1.x, __fmaf_rn(ey, r1.y, __fmul_rn(ez, r1.z)));
+    float v = __fmaf_rn(ex, r2.x, __fmaf_rn(ey, r2.y, __fmul_rn(ez, r2.z)));
+    float rho2 = __fmaf_rn(u, u, __fmul_rn(v, v));
+    if (!(rho2 <= r1.w)) return false;
+    float G = __expf(__fmul_rn(-0.5f, rho2));
+    float a_raw = __fmul_rn(r0.w, G);
+    alpha = fminf(a_raw, amax);
+    if (!(alpha >= amin)) return false;
+    two_sum(tr, tp, kh, kl);
+    if (GEOM) {
+        g->e = mk3(ex, ey, ez);
+        g->u = u;
+        g->v = v;
+        g->G = G;
+        g->a_raw = a_raw;
+        g->den = den;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void slab2(const Node& nd, const Ray& r, float& tn0, float& tf0, float& tn1,
+                                      float& tf1) {
+    // child 0: lo = (a.x,a.y,a.z) hi = (a.w,b.x,b.y); child 1: lo = (b.z,b.w,c.x) hi = (c.y,c.z,c.w)
+    float x0 = fmaf(nd.a.x, r.inv.x, -r.oinv.x), x1 = fmaf(nd.a.w, r.inv.x, -r.oinv.x);
+    float y0 = fmaf(nd.a.y, r.inv.y, -r.oinv.y), y1 = fmaf(nd.b.x, r.inv.y, -r.oinv.y);
+    float z0 = fmaf(nd.a.z, r.inv.z, -r.oinv.z), z1 = fmaf(nd.b.y, r.inv.z, -r.oinv.z);
+    tn0 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fminf(z0, z1));
+    tf0 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fmaxf(z0, z1));
+    x0 = fmaf(nd.b.z, r.inv.x, -r.oinv.x); x1 = fmaf(nd.c.y, r.inv.x, -r.oinv.x);
+    y0 = fmaf(nd.b.w, r.inv.y, -r.oinv.y); y1 = fmaf(nd.c.z, r.inv.y, -r.oinv.y);
+    z0 = fmaf(nd.c.x, r.inv.z, -r.oinv.z); z1 = fmaf(nd.c.w, r.inv.z, -r.oinv.z);
+    tn1 = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fminf(z0, z1));
+    tf1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fmaxf(z0, z1));
+}
+
+// Conservative slack on depths compared against box intervals.
+__device__ __forceinline__ float tslack(float t) { return 1e-5f * (1.0f + fabsf(t)); }
+
+__device__ __forceinline__ Node load_node(const Node* nodes, int i) {
+    const float4* p = reinterpret_cast<const float4*>(nodes + i);
+    Node nd;
+    nd.a = ldg4(p);
+    nd.b = ldg4(p + 1);
+    nd.c = ldg4(p + 2);
+    nd.d = ldg4i(reinterpret_cast<const int4*>(p + 3));
+    return nd;
+}
+
+// k-buffer of the nearest hits after `last`, sorted by (key, Morton index).
+template <int K>
+struct KBuffer {
+    uint64_t key[K];
+    int32_t m[K];
+    float a[K];
+    int cnt;
+
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            key[j] = ~0ull;
+            m[j] = INT32_MAX;
+            a[j] = 0.f;
+        }
+        cnt = 0;
+    }
+    __device__ __forceinline__ bool full() const { return cnt == K; }
+    // insert (k, mm, aa); caller guarantees it sorts before the last entry when full
+    __device__ __forceinline__ void insert(uint64_t k, int32_t mm, float aa) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            bool lt = k < key[j] || (k == key[j] && mm < m[j]);
+            uint64_t tk = key[j];
+            int32_t tm = m[j];
+            float ta = a[j];
+            key[j] = lt ? k : tk;
+            m[j] = lt ? mm : tm;
+            a[j] = lt ? aa : ta;
+            k = lt ? tk : k;
+            mm = lt ? tm : mm;
+            aa = lt ? ta : aa;
+        }
+        cnt = cnt < K ? cnt + 1 : K;
+    }
+};
+
+__device__ __forceinline__ float key_depth(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
+
+// One round: gather the K nearest hits strictly after (last_key, last_m).
+// Returns false if the traversal stack overflowed.
+template <int K>
+__device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray, const TraceParams& P,
+                                              uint64_t last_key, int32_t last_m, KBuffer<K>& kb) {
+    int stack_n[kStackSize];
+    float stack_t[kStackSize];
+    int sp = 0;
+    bool ok = true;
+    kb.clear();
+    const float t_lo = key_depth(last_key);
+    const float lo_c = t_lo - tslack(t_lo);
+    float t_hi = P.t_max;
+    int ni = 0;
+    // each internal node is visited at most once per round in a valid tree
+    const int64_t max_visits = 2 * S.n + 64;
+    for (int64_t visits = 0;; ++visits) {
+        if (visits > max_visits) {
+            ok = false;
+            break;
+        }
+        const Node nd = load_node(S.nodes, ni);
+        float tn0, tf0, tn1, tf1;
+        slab2(nd, ray, tn0, tf0, tn1, tf1);
+        const int c0 = nd.d.x, c1 = nd.d.y;
+        float hi_c = t_hi + tslack(t_hi);
+        bool h0 = c0 != kNoChild && tn0 <= tf0 && tf0 >= lo_c && tn0 <= hi_c;
+        bool h1 = c1 != kNoChild && tn1 <= tf1 && tf1 >= lo_c && tn1 <= hi_c;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const bool h = side == 0 ? h0 : h1;
+            const int c = side == 0 ? c0 : c1;
+            if (h && c < 0) {
+                const int32_t m = ~c;
+                const float4* R = S.rec + (int64_t)m * kRecF4;
+                const float4 r0 = ldg4(R), r1 = ldg4(R + 1), r2 = ldg4(R + 2), r3 = ldg4(R + 3);
+                float kh, kl, a;
+                if (surfel_hit<false>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a, nullptr)) {
+                    const uint64_t key = depth_key(kh, kl);
+                    const bool past_min = kh > P.t_min || (kh == P.t_min && kl > 0.f);
+                    const bool after = past_min && (key > last_key || (key == last_key && m > last_m));
+                    const bool before = kh < P.t_max || (kh == P.t_max && kl < 0.f);
+                    const bool fits = !kb.full() || key < kb.key[K - 1] ||
+                                      (key == kb.key[K - 1] && m < kb.m[K - 1]);
+                    if (after && before && fits) {
+                        kb.insert(key, m, a);
+                        if (kb.full()) t_hi = key_depth(kb.key[K - 1]);
+                    }
+                }
+            }
+        }
+        if (c0 < 0) h0 = false;
+        if (c1 < 0) h1 = false;
+        hi_c = t_hi + tslack(t_hi);
+        h0 = h0 && tn0 <= hi_c;
+        h1 = h1 && tn1 <= hi_c;
+        if (h0 && h1) {
+            const bool first0 = tn0 <= tn1;
+            if (sp < kStackSize) {
+                stack_n[sp] = first0 ? c1 : c0;
+                stack_t[sp] = first0 ? tn1 : tn0;
+                ++sp;
+            } else {
+                ok = false;
+            }
+            ni = first0 ? c0 : c1;
+        } else if (h0) {
+            ni = c0;
+        } else if (h1) {
+            ni = c1;
+        } else {
+            // pop the next node that can still hold a hit before t_hi
+            bool found = false;
+            while (sp > 0) {
+                --sp;
+                if (stack_t[sp] <= t_hi + tslack(t_hi)) {
+                    ni = stack_n[sp];
+                    found = true;
+                    break;
+                }
+            }
+            if (!found) break;
+        }
+    }
+    return ok;
+}
+
+// Full forward march of one ray: rounds of collect + blend until the
+// transmittance drops below T_min or no further hit exists.
+template <int K, int FB>
+struct MarchState {
+    float C[FB];
+    float D, T;
+    int nh;
+};
+
+template <int K, int FB>
+__device__ __forceinline__ bool march_forward(const SceneView& S, const Ray& ray, const TraceParams& P,
+                                              MarchState<K, FB>& st, int32_t* ids, int max_ids) {
+#pragma unroll
+    for (int c = 0; c < FB; ++c) st.C[c] = 0.f;
+    st.D = 0.f;
+    st.T = 1.f;
+    st.nh = 0;
+    bool ok = true;
+    if (S.n == 0) return ok;
+    uint64_t last_key = depth_key(P.t_min, 0.f);
+    int32_t last_m = INT32_MAX;
+    KBuffer<K> kb;
+    bool done = false;
+    while (!done) {
+        ok &= collect_round<K>(S, ray, P, last_key, last_m, kb);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            if (j < kb.cnt && !done) {
+                const float a = kb.a[j];
+                const int32_t m = kb.m[j];
+                const float w = __fmul_rn(st.T, a);
+                const float* f = S.feat + (int64_t)m * S.F + P.off;
+#pragma unroll
+                for (int c = 0; c < FB; ++c)
+                    if (c < P.fc) st.C[c] = __fmaf_rn(w, __ldg(f + c), st.C[c]);
+                st.D = __fmaf_rn(w, key_depth(kb.key[j]), st.D);
+                st.T = __fmul_rn(st.T, __fsub_rn(1.0f, a));
+                if (ids != nullptr && st.nh < max_ids)
+                    ids[st.nh] = __float_as_int(__ldg(&S.rec[(int64_t)m * kRecF4 + 2].w));
+                st.nh++;
+                if (st.T < P.T_min) done = true;
+            }
+        }
+        if (!done) {
+            if (kb.cnt < K) {
+                done = true;
+            } else {
+                last_key = kb.key[K - 1];
+                last_m = kb.m[K - 1];
+            }
+        }
+    }
+    return ok;
+}
+
+__host__ __device__ inline TraceParams to_params(const irgs_trace_params& p) {
+    TraceParams t;
+    t.alpha_min = p.alpha_min;
+    t.alpha_max = p.alpha_max;
+    t.T_min = p.T_min;
+    t.t_min = p.t_min;
+    t.t_max = p.t_max;
+    t.off = p.feat_offset;
+    t.fc = p.feat_count;
+    return t;
+}
+
+}  // namespace irgs

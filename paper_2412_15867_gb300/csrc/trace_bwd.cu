@@ -1,0 +1,240 @@
+// Backward trace kernel: the gradient of Trace(r_o, r_d) (IRGS Eq. 8; the
+// tracer is differentiable, Sec. 3.3) with respect to every surfel parameter.
+//
+// Each ray's k-buffer march is replayed exactly (same traversal, same
+// arithmetic), capped at the forward's hit count, and no hit list is stored.
+// For the loss L = g_C.C + g_D D + g_O O and hits j = 0..J-1 in depth order,
+// with w_j = T_j alpha_j and v_j = g_C.f_j + g_D tau_j:
+//   dL/dalpha_j = T_j v_j - (S_j - g_O T_J) / (1 - alpha_j),
+//   S_j = sum_{m>j} w_m v_m = g_C.(C - C_<=j) + g_D (D - D_<=j),
+// where C_<=j, D_<=j are the running sums up to and including hit j (the
+// suffix comes from the forward's totals minus the replayed prefix). The
+// chain then runs alpha -> (o, rho^2) -> (u, v) -> (p - mu, tau) -> (mu, t_u,
+// t_v, n, s_u, s_v) -> raw quaternion (Eq. 6-7 and the rotation of the unit
+// quaternion). Gradients land in user order through warp-aggregated atomics.
+#include <cuda_runtime.h>
+
+#include "scene.h"
+#include "trace.cuh"
+
+namespace irgs {
+namespace {
+
+constexpr int kBwdThreads = 128;
+
+// Per-surfel gradient record: means(3) quats(4) scales(2) opacity(1) features(FB).
+template <int FB>
+struct GradVals {
+    static constexpr int N = 10 + FB;
+    float v[N];
+};
+
+// Add `g` (N values) for surfel `uid`, summing over the lanes of the warp that
+// hold the same uid first (match mask + per-lane rows in shared memory).
+template <int FB>
+__device__ __forceinline__ void scatter_grad(const GradVals<FB>& g, int32_t uid, int fc, int F, int off,
+                                             float* __restrict__ g_means, float* __restrict__ g_quats,
+                                             float* __restrict__ g_scales, float* __restrict__ g_opac,
+                                             float* __restrict__ g_feat, float* rows /* [32][N+1] this warp */) {
+    constexpr int N = GradVals<FB>::N;
+    const unsigned active = __activemask();
+    const unsigned peers = __match_any_sync(active, uid);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    float acc[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc[k] = g.v[k];
+    if (peers != (1u << lane)) {
+        float* mine = rows + lane * (N + 1);
+#pragma unroll
+        for (int k = 0; k < N; ++k) mine[k] = g.v[k];
+        __syncwarp(peers);
+        if (lane == leader) {
+            unsigned rest = peers & ~(1u << lane);
+            while (rest) {
+                const int l = __ffs(rest) - 1;
+                rest &= rest - 1;
+                const float* other = rows + l * (N + 1);
+#pragma unroll
+                for (int k = 0; k < N; ++k) acc[k] += other[k];
+            }
+        }
+        __syncwarp(peers);
+    }
+    if (lane != leader) return;
+    const int64_t u = uid;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) atomicAdd(g_means + 3 * u + k, acc[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) atomicAdd(g_quats + 4 * u + k, acc[3 + k]);
+    atomicAdd(g_scales + 2 * u, acc[7]);
+    atomicAdd(g_scales + 2 * u + 1, acc[8]);
+    atomicAdd(g_opac + u, acc[9]);
+#pragma unroll
+    for (int c = 0; c < FB; ++c)
+        if (c < fc) atomicAdd(g_feat + u * F + off + c, acc[10 + c]);
+}
+
+template <int K, int FB>
+__global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
+    SceneView S, const float* __restrict__ ro, const float* __restrict__ rd, int64_t R, TraceParams P,
+    const float* __restrict__ out_feat, const float* __restrict__ out_depth, const float* __restrict__ out_opac,
+    const int32_t* __restrict__ out_nhits, const float* __restrict__ g_featv, const float* __restrict__ g_depthv,
+    const float* __restrict__ g_opacv, float* __restrict__ g_means, float* __restrict__ g_quats,
+    float* __restrict__ g_scales, float* __restrict__ g_opac, float* __restrict__ g_feat) {
+    constexpr int N = GradVals<FB>::N;
+    __shared__ float rows_all[kBwdThreads * (N + 1)];
+    float* rows = rows_all + (threadIdx.x & ~31) * (N + 1);
+    const int64_t r = blockIdx.x * (int64_t)kBwdThreads + threadIdx.x;
+    if (r >= R) return;
+    const int nh_total = out_nhits[r];
+    if (nh_total <= 0 || S.n == 0) return;
+    const Ray ray = make_ray(mk3(ro[3 * r], ro[3 * r + 1], ro[3 * r + 2]),
+                             mk3(rd[3 * r], rd[3 * r + 1], rd[3 * r + 2]));
+    float gC[FB], Cf[FB], Cacc[FB];
+#pragma unroll
+    for (int c = 0; c < FB; ++c) {
+        gC[c] = c < P.fc ? g_featv[r * P.fc + c] : 0.f;
+        Cf[c] = c < P.fc ? out_feat[r * P.fc + c] : 0.f;
+        Cacc[c] = 0.f;
+    }
+    const float gD = g_depthv != nullptr ? g_depthv[r] : 0.f;
+    const float gO = g_opacv != nullptr ? g_opacv[r] : 0.f;
+    const float Df = out_depth[r];
+    const float Tfin = 1.0f - out_opac[r];
+    float Dacc = 0.f, T = 1.f;
+    int nh = 0;
+    uint64_t last_key = depth_key(P.t_min, 0.f);
+    int32_t last_m = INT32_MAX;
+    KBuffer<K> kb;
+    bool ok = true, done = false;
+    while (!done) {
+        ok &= collect_round<K>(S, ray, P, last_key, last_m, kb);
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            if (j < kb.cnt && nh < nh_total) {
+                const float a = kb.a[j];
+                const int32_t m = kb.m[j];
+                const float tau = key_depth(kb.key[j]);
+                const float w = __fmul_rn(T, a);
+                const float* f = S.feat + (int64_t)m * S.F + P.off;
+                float fv[FB];
+                float v = __fmul_rn(gD, tau), Sj = 0.f;
+#pragma unroll
+                for (int c = 0; c < FB; ++c) {
+                    fv[c] = c < P.fc ? __ldg(f + c) : 0.f;
+                    Cacc[c] = c < P.fc ? __fmaf_rn(w, fv[c], Cacc[c]) : 0.f;
+                    v = fmaf(gC[c], fv[c], v);
+                    Sj = fmaf(gC[c], Cf[c] - Cacc[c], Sj);
+                }
+                Dacc = __fmaf_rn(w, tau, Dacc);
+                Sj = fmaf(gD, Df - Dacc, Sj);
+                const float dA = T * v - (Sj - gO * Tfin) / (1.0f - a);
+
+                // recompute the hit geometry (bitwise identical to the march)
+                const float4* Rp = S.rec + (int64_t)m * kRecF4;
+                const float4 r0 = ldg4(Rp), r1 = ldg4(Rp + 1), r2 = ldg4(Rp + 2), r3 = ldg4(Rp + 3);
+                float kh, kl, a2;
+                HitGeom hg;
+                surfel_hit<true>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a2, &hg);
+                const float2 sc = __ldg(&S.scale[m]);
+                const float4 q = __ldg(&S.q_raw[m]);
+
+                GradVals<FB> gv;
+                const bool clamped = hg.a_raw >= P.alpha_max;
+                const float g_o = clamped ? 0.f : dA * hg.G;
+                const float g_rho2 = clamped ? 0.f : -0.5f * dA * a;
+                const float gu = 2.f * g_rho2 * hg.u, gvv = 2.f * g_rho2 * hg.v;
+                const f3 tus = mk3(r1.x, r1.y, r1.z), tvs = mk3(r2.x, r2.y, r2.z), nn = mk3(r3.x, r3.y, r3.z);
+                const f3 ge = add3(mul3(tus, gu), mul3(tvs, gvv));
+                const float gtau = w * gD + dot3(ge, ray.d);
+                const float s_t = gtau / hg.den;
+                const f3 gmu = sub3(mul3(nn, s_t), ge);
+                const f3 gn = mul3(hg.e, -s_t);
+                const f3 gtu = mul3(hg.e, gu / sc.x);
+                const f3 gtv = mul3(hg.e, gvv / sc.y);
+                // raw quaternion: derivative of the rotation columns, then of q / |q|
+                const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+                const float qw = q.x / qn, qx = q.y / qn, qy = q.z / qn, qz = q.w / qn;
+                const float hw = 2.f * (qz * gtu.y - qy * gtu.z - qz * gtv.x + qx * gtv.z + qy * gn.x - qx * gn.y);
+                const float hx = 2.f * (qy * gtu.y + qz * gtu.z + qy * gtv.x - 2.f * qx * gtv.y + qw * gtv.z +
+                                        qz * gn.x - qw * gn.y - 2.f * qx * gn.z);
+                const float hy = 2.f * (-2.f * qy * gtu.x + qx * gtu.y - qw * gtu.z + qx * gtv.x + qz * gtv.z +
+                                        qw * gn.x + qz * gn.y - 2.f * qy * gn.z);
+                const float hz = 2.f * (-2.f * qz * gtu.x + qw * gtu.y + qx * gtu.z - qw * gtv.x - 2.f * qz * gtv.y +
+                                        qy * gtv.z + qx * gn.x + qy * gn.y);
+                const float proj = qw * hw + qx * hx + qy * hy + qz * hz;
+                gv.v[0] = gmu.x; gv.v[1] = gmu.y; gv.v[2] = gmu.z;
+                gv.v[3] = (hw - qw * proj) / qn;
+                gv.v[4] = (hx - qx * proj) / qn;
+                gv.v[5] = (hy - qy * proj) / qn;
+                gv.v[6] = (hz - qz * proj) / qn;
+                gv.v[7] = -gu * hg.u / sc.x;
+                gv.v[8] = -gvv * hg.v / sc.y;
+                gv.v[9] = g_o;
+#pragma unroll
+                for (int c = 0; c < FB; ++c) gv.v[10 + c] = w * gC[c];
+                const int32_t uid = __float_as_int(r2.w);
+                scatter_grad<FB>(gv, uid, P.fc, S.F, P.off, g_means, g_quats, g_scales, g_opac, g_feat, rows);
+
+                T = __fmul_rn(T, __fsub_rn(1.0f, a));
+                ++nh;
+            }
+        }
+        if (nh >= nh_total || kb.cnt < K) {
+            done = true;
+        } else {
+            last_key = kb.key[K - 1];
+            last_m = kb.m[K - 1];
+        }
+    }
+    if (!ok) atomicOr(S.status, kErrStackOverflow);
+}
+
+template <int K, int FB>
+cudaError_t launch(const SceneView& S, const float* ro, const float* rd, int64_t R, const TraceParams& P,
+                   const float* feat, const float* depth, const float* opac, const int32_t* nhits,
+                   const float* gf, const float* gd, const float* go, float* gm, float* gq, float* gs,
+                   float* gop, float* gfe, cudaStream_t st) {
+    const int64_t blocks = (R + kBwdThreads - 1) / kBwdThreads;
+    k_trace_backward<K, FB><<<(unsigned)blocks, kBwdThreads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac, nhits,
+                                                                      gf, gd, go, gm, gq, gs, gop, gfe);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_f(const SceneView& S, const float* ro, const float* rd, int64_t R, const TraceParams& P,
+                     const float* feat, const float* depth, const float* opac, const int32_t* nhits,
+                     const float* gf, const float* gd, const float* go, float* gm, float* gq, float* gs,
+                     float* gop, float* gfe, cudaStream_t st) {
+    if (P.fc <= 3) return launch<K, 3>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+    if (P.fc <= 10)
+        return launch<K, 10>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+    return launch<K, 16>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+}
+
+}  // namespace
+
+irgs_status launch_trace_backward(const SceneView& S, const float* ro, const float* rd, int64_t R,
+                                  const irgs_trace_params& p, const float* feat, const float* depth,
+                                  const float* opac, const int32_t* nhits, const float* g_feat,
+                                  const float* g_depth, const float* g_opac, float* g_means, float* g_quats,
+                                  float* g_scales, float* g_opacity, float* g_features, cudaStream_t st) {
+    if (R == 0) return IRGS_OK;
+    const TraceParams P = to_params(p);
+    cudaError_t e;
+    switch (p.k) {
+        case 8:
+            e = launch_f<8>(S, ro, rd, R, P, feat, depth, opac, nhits, g_feat, g_depth, g_opac, g_means, g_quats,
+                            g_scales, g_opacity, g_features, st);
+            break;
+        case 16:
+            e = launch_f<16>(S, ro, rd, R, P, feat, depth, opac, nhits, g_feat, g_depth, g_opac, g_means, g_quats,
+                             g_scales, g_opacity, g_features, st);
+            break;
+        default: return IRGS_ERR_UNSUPPORTED;
+    }
+    return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+}
+
+}  // namespace irgs
