@@ -1,0 +1,430 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 2D Gaussian ray tracer (one JSON line on rank 0).
+
+Workload (one GPU): the camera-ray scene-scale configuration -- 300k surfels
+on a synthetic object scene (unit sphere, torus, ground square; tangent with
+1% normal jitter; log-normal scales with median 0.01; opacity Beta(5,1);
+10 feature channels) traced by 100 cameras x 800x800 = 64M rays, k = 16.
+A step is the training-style pass over that batch: rebuild the scene's LBVH
+from the surfel values (K1-K5), trace all rays forward (Eq. 8) and run the
+backward pass for a random N(0,1) upstream gradient. `value` is rays traced
+forward and backward per second (Mrays/s), inputs resident on the device.
+The Monte Carlo rendering-equation configuration (1M surfels, 640k points x
+64 samples = 41M secondary rays) is timed in the same run under "mc".
+
+`--impl reference` times the FP64 CPU oracle (the reference of this build)
+on bounded samples of the same workload, on the host cores.
+
+Run with torchrun for N > 1: each rank traces its own 100-camera batch
+(weak scaling) and the surfel gradients are summed across ranks (the one
+exchange step of a data-parallel backward).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mrays/s traced+composited (fwd, fwd+bwd) vs roofline; served p50/p99 latency"
+UNIT = "Mrays/s"
+WORKLOAD = "camera rays at scene scale: 300k-surfel object scene, 100 cameras x 800x800, k=16, 10 channels"
+
+# FP32 pipe of one GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) at the
+# 2070 MHz maximum SM clock.
+SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+# DRAM traffic per launch of the dominant kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) scaled per ray; keyed by
+# the hash of the sources it was measured on (null once they change).
+TRAFFIC = {}
+
+
+def _kernel_hash(files):
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2412_15867_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cams", type=int, default=100)
+    ap.add_argument("--res", type=int, default=800)
+    ap.add_argument("--surfels", type=int, default=300_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-mc", action="store_true")
+    ap.add_argument("--cpu-rays", type=int, default=4096, help="oracle sample for cpu_baseline")
+    ap.add_argument("--ref-rays", type=int, default=1024, help="oracle rays per reference step")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def algorithmic_flops(nh, k, n_surfels, F, backward=False):
+    """Algorithmic FP32 flops of one launch: per composited hit one Eq. 6-7
+    intersection (45, exp counted as 1) plus blending (2(F+2) + 3); per
+    k-buffer round one root-to-leaf descent of ceil(log2 N) nodes with two
+    slab tests (40). The backward costs about 3x per hit."""
+    import torch
+    nh = nh.to(torch.float64)
+    rounds = torch.floor(nh / k) + 1
+    per_hit = 45 + 2 * (F + 2) + 3
+    depth = math.ceil(math.log2(max(n_surfels, 2)))
+    f = nh * per_hit * (3 if backward else 1) + rounds * depth * 40
+    return float(f.sum())
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import synth
+    import paper_2412_15867_gb300 as irgs
+    from paper_2412_15867_gb300 import _lib
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    L = _lib.lib()
+
+    # ---- synthetic workload (same scene on every rank, own cameras per rank)
+    sc = synth.object_scene(args.surfels, seed=1001)
+    cams = synth.hemisphere_cameras(args.cams, seed=1001 + 7919 * rank)
+    ro_np, rd_np = synth.camera_batch_rays(cams, args.res, args.res)
+    R = ro_np.shape[0]
+    F = sc.features.shape[1]
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    surf = [T(a) for a in sc.arrays()]
+    ro, rd = T(ro_np), T(rd_np)
+    gf_np, gd_np, go_np = synth.upstream_grads(R, F, seed=1004 + rank)
+    gf, gd, go = T(gf_np), T(gd_np), T(go_np)
+    p = irgs.TraceParams(k=16, feat_count=F)
+    scene = irgs.Scene(*surf, alpha_min=1 / 255)
+    out = irgs.trace_forward(scene, ro, rd, p)
+    grads = {"means": torch.zeros((sc.n, 3), device=dev), "quats": torch.zeros((sc.n, 4), device=dev),
+             "scales": torch.zeros((sc.n, 2), device=dev), "opacity": torch.zeros(sc.n, device=dev),
+             "features": torch.zeros((sc.n, F), device=dev)}
+    stream = torch.cuda.current_stream(dev)
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        scene.update()
+        if evs:
+            evs[1].record(stream)
+        irgs.trace_forward(scene, ro, rd, p, out=out)
+        if evs:
+            evs[2].record(stream)
+        for g in grads.values():
+            g.zero_()
+        irgs.trace_backward(scene, ro, rd, p, out, gf, gd, go, grads=grads)
+        if evs:
+            evs[3].record(stream)
+        if world > 1:
+            for g in grads.values():
+                dist.all_reduce(g)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if scene.status() != 0:
+        raise RuntimeError("device error during warm-up")
+
+    clocks = ClockSampler(local)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = L.irgs_kernel_launches()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(evs[i])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    launches = L.irgs_kernel_launches() - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    build_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    fwd_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    bwd_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    tmax = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms = float(tmax.item())
+    ms_per_step = total_ms / args.steps
+    value = R * world * args.steps / (total_ms * 1e-3) / 1e6
+    if scene.status() != 0:
+        raise RuntimeError("device error in the timed region")
+
+    # ---- roofline of the dominant kernel (by time)
+    nh = out["n_hits"]
+    if bwd_ms >= fwd_ms:
+        kname, kms = "k_trace_backward<16,10>", bwd_ms
+        flops = algorithmic_flops(nh, 16, sc.n, F, backward=True)
+        src = ["trace.cuh", "trace_bwd.cu", "common.cuh"]
+    else:
+        kname, kms = "k_trace_forward<16,10>", fwd_ms
+        flops = algorithmic_flops(nh, 16, sc.n, F)
+        src = ["trace.cuh", "trace_fwd.cu", "common.cuh"]
+    achieved = flops / (kms * 1e-3) / 1e12
+    khash = _kernel_hash(src)
+    tr = TRAFFIC.get(kname)
+    traffic = tr["bytes_per_ray"] * R if (tr and tr.get("src_hash") == khash) else None
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "flops_per_launch": flops, "launch_ms": kms,
+                "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz max SM clock",
+                "hbm_bound_mrays_s": None}
+
+    # ---- end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_in = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+                   for k, a in zip(("means", "quats", "scales", "opacity", "features"), sc.arrays())}
+        host_in.update({"ro": torch.from_numpy(ro_np).pin_memory(), "rd": torch.from_numpy(rd_np).pin_memory(),
+                        "gf": torch.from_numpy(gf_np).pin_memory(), "gd": torch.from_numpy(gd_np).pin_memory(),
+                        "go": torch.from_numpy(go_np).pin_memory()})
+        dev_in = {k: torch.empty_like(v, device=dev) for k, v in host_in.items()}
+        host_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in out.items()}
+        host_out.update({("g_" + k): torch.empty_like(v, device="cpu").pin_memory() for k, v in grads.items()})
+        h2d = sum(v.numel() * v.element_size() for v in host_in.values())
+        d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+        scene_e2e = irgs.Scene(dev_in["means"], dev_in["quats"], dev_in["scales"], dev_in["opacity"],
+                               dev_in["features"])
+
+        def e2e_step():
+            for k, v in host_in.items():
+                dev_in[k].copy_(v, non_blocking=True)
+            scene_e2e.update()
+            o_ = irgs.trace_forward(scene_e2e, dev_in["ro"], dev_in["rd"], p, out=out)
+            for g in grads.values():
+                g.zero_()
+            irgs.trace_backward(scene_e2e, dev_in["ro"], dev_in["rd"], p, o_, dev_in["gf"], dev_in["gd"],
+                                dev_in["go"], grads=grads)
+            for k, v in out.items():
+                host_out[k].copy_(v, non_blocking=True)
+            for k, v in grads.items():
+                host_out["g_" + k].copy_(v, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        n_e2e = max(2, min(args.steps, 3))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n_e2e):
+            e2e_step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e_ms = a.elapsed_time(b) / n_e2e
+        e2e = {"value": R * world / (e_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
+        scene_e2e.close()
+
+    # ---- Monte Carlo rendering equation configuration
+    mc = None
+    if not args.no_mc and rank == 0:
+        sc2 = synth.object_scene(1_000_000, seed=1002)
+        gb = synth.gbuffer_points(640_000, seed=1002)
+        env = T(synth.env_map(seed=1003))
+        S2 = irgs.Scene(*(T(a) for a in sc2.arrays()))
+        g2 = [T(a) for a in gb]
+        ps = irgs.TraceParams(k=16, feat_count=3, t_min=1e-3)
+        o2 = irgs.shade_mc(S2, *g2, env, 32, 32, 2024, ps)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        a.record(stream)
+        for _ in range(reps):
+            irgs.shade_mc(S2, *g2, env, 32, 32, 2024, ps, out=o2)
+        b.record(stream)
+        torch.cuda.synchronize()
+        mms = a.elapsed_time(b) / reps
+        rays = 640_000 * 64
+        mc = {"workload": "1M surfels, 640k G-buffer points x (32 cosine + 32 GGX) = 41M secondary rays, "
+                          "512x256 env, k=16", "ms": mms, "mrays_s": rays / (mms * 1e-3) / 1e6,
+              "points_per_s": 640_000 / (mms * 1e-3)}
+        if S2.status() != 0:
+            raise RuntimeError("device error in the MC leg")
+        S2.close()
+
+    # ---- oracle on the host cores, bounded sample of the same workload
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        cpu = cpu_baseline(sc, ro_np, rd_np, gf_np, gd_np, go_np, args.cpu_rays)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded object scene and camera rays; no dataset)",
+            "config": {"workload": WORKLOAD, "surfels": sc.n, "rays_per_step_per_gpu": R,
+                       "cameras": args.cams, "resolution": args.res, "k": 16, "feat_count": F,
+                       "alpha_min": 1 / 255, "T_min": 1e-4,
+                       "step": "LBVH rebuild + forward trace + backward trace",
+                       "l2": "inputs larger than L2 (1.5 GB of rays per step)"},
+            "fwd_mrays_s": R / (fwd_ms * 1e-3) / 1e6, "bwd_mrays_s": R / (bwd_ms * 1e-3) / 1e6,
+            "build_ms": build_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+            "mean_hits_per_ray": float(nh.float().mean()),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk, "mc": mc,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(sc, ro, rd, gf, gd, go, n_rays):
+    """Oracle forward + gradient on a seeded sample of the workload's rays."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(99)
+    idx = np.sort(rng.choice(ro.shape[0], n_rays, replace=False))
+    p = oracle.Params(feat_count=sc.features.shape[1])
+    cores = oracle.num_threads()
+    t0 = time.perf_counter()
+    oracle.trace(sc, ro[idx], rd[idx], p, margins=None)
+    oracle.trace_grad(sc, ro[idx], rd[idx], gf[idx], gd[idx], go[idx], p)
+    dt = time.perf_counter() - t0
+    return {"value": n_rays / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_rays} seeded camera rays of the workload, forward + gradient, FP64 brute force "
+                      f"over all {sc.n} surfels ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    import synth
+    sc = synth.object_scene(args.surfels, seed=1001)
+    cams = synth.hemisphere_cameras(args.cams, seed=1001)
+    rng = np.random.default_rng(5)
+    p = oracle.Params(feat_count=sc.features.shape[1])
+    cores = oracle.num_threads()
+    ci = rng.integers(0, args.cams, size=args.ref_rays)
+    # rays of random pixels of random cameras of the workload
+    ro_l, rd_l = [], []
+    for c in np.unique(ci):
+        o, d = synth.look_at_rays(cams[c], (0, 0, 0), args.res, args.res)
+        pick = rng.integers(0, o.shape[0], size=int((ci == c).sum()))
+        ro_l.append(o[pick]); rd_l.append(d[pick])
+    ro, rd = np.concatenate(ro_l), np.concatenate(rd_l)
+    gf, gd, go = synth.upstream_grads(ro.shape[0], sc.features.shape[1], seed=7)
+
+    def step():
+        oracle.trace(sc, ro, rd, p, margins=None)
+        oracle.trace_grad(sc, ro, rd, gf, gd, go, p)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = ro.shape[0] * args.steps / dt / 1e6
+    sample = (f"{ro.shape[0]} camera rays per step (random pixels of the workload's cameras), "
+              f"forward + gradient, FP64 brute force over {sc.n} surfels")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded object scene and camera rays)",
+            "config": {"workload": WORKLOAD, "surfels": sc.n, "rays_per_step": int(ro.shape[0]),
+                       "k": 16, "feat_count": int(sc.features.shape[1])},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

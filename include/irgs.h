@@ -82,6 +82,10 @@ const char* irgs_status_string(irgs_status status);
 /* IRGS_ABI_VERSION of the loaded library. */
 int32_t irgs_abi_version(void);
 
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all devices and threads; a diagnostic for benchmarks). */
+uint64_t irgs_kernel_launches(void);
+
 /*
  * Build a scene from a surfel cloud (Sec. 3.2, bounding proxies and BVH;
  * Eq. 5 gives the support radius). Each surfel is bounded by the box of its
@@ -99,6 +103,16 @@ int32_t irgs_abi_version(void);
  */
 irgs_status irgs_build_scene(const irgs_surfels* surfels, float alpha_min, void* stream,
                              irgs_scene* out);
+
+/*
+ * Rebuild an existing scene in place from new surfel values (same n and
+ * num_features): the per-iteration BVH update of a training loop (Sec. 4,
+ * "updating the BVH at each training iteration for the varying geometry").
+ * Reuses the scene's device buffers, allocates nothing, and is enqueued on
+ * `stream`; traces already enqueued on other streams must finish first.
+ * IRGS_ERR_INVALID_ARG if n or num_features differ from the scene's.
+ */
+irgs_status irgs_update_scene(irgs_scene scene, const irgs_surfels* surfels, void* stream);
 
 /* Free a scene and all its device memory (synchronises the device first).
  * NULL is accepted and ignored. */

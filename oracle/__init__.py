@@ -64,7 +64,7 @@ class Margins:
     alpha_abs: float = 1e-6
     rho_rel: float = 1e-5
     T_rel: float = 1e-5
-    tie_abs: float = 1e-7
+    tie_abs: float = 2e-8
     t_abs: float = 1e-6
     clamp_abs: float = 1e-5
 

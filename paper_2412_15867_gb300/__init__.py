@@ -92,15 +92,34 @@ class Scene:
         self.num_features = int(self.features.shape[1])
         self.n = int(n)
         L = _lib.lib()
-        s = _lib.Surfels(self.means.data_ptr() if n else None, self.quats.data_ptr() if n else None,
-                         self.scales.data_ptr() if n else None, self.opacity.data_ptr() if n else None,
-                         self.features.data_ptr() if (n and self.num_features) else None,
-                         n, self.num_features)
+        s = self._surfels()
         h = C.c_void_p()
         with torch.cuda.device(self.device):
             _lib.check(L.irgs_build_scene(C.byref(s), self.alpha_min, _stream(self.device), C.byref(h)),
                        "irgs_build_scene")
         self._h = h
+
+    def _surfels(self) -> _lib.Surfels:
+        n = self.n
+        return _lib.Surfels(self.means.data_ptr() if n else None, self.quats.data_ptr() if n else None,
+                            self.scales.data_ptr() if n else None, self.opacity.data_ptr() if n else None,
+                            self.features.data_ptr() if (n and self.num_features) else None,
+                            n, self.num_features)
+
+    def update(self, means=None, quats=None, scales=None, opacity=None, features=None) -> None:
+        """Rebuild the BVH in place after the surfel values changed (same count).
+        Tensors given here replace the stored ones (same shapes)."""
+        for name, t in (("means", means), ("quats", quats), ("scales", scales), ("opacity", opacity),
+                        ("features", features)):
+            if t is not None:
+                t = _dev_f32(t, name)
+                if t.numel() != getattr(self, name).numel():
+                    raise ValueError(f"{name} must keep its shape")
+                setattr(self, name, t.reshape(getattr(self, name).shape))
+        s = self._surfels()
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.lib().irgs_update_scene(self.handle, C.byref(s), _stream(self.device)),
+                       "irgs_update_scene")
 
     @property
     def handle(self) -> C.c_void_p:

@@ -41,7 +41,9 @@ P = C.c_void_p
 _SIGS = {
     "irgs_status_string": (C.c_char_p, [C.c_int]),
     "irgs_abi_version": (C.c_int32, []),
+    "irgs_kernel_launches": (C.c_uint64, []),
     "irgs_build_scene": (C.c_int, [C.POINTER(Surfels), C.c_float, P, C.POINTER(P)]),
+    "irgs_update_scene": (C.c_int, [P, C.POINTER(Surfels), P]),
     "irgs_destroy_scene": (C.c_int, [P]),
     "irgs_scene_info": (C.c_int, [P, P, P, P, P]),
     "irgs_scene_status": (C.c_int, [P, P, P]),

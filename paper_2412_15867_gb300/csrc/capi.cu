@@ -5,8 +5,15 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
+
 #include "../../include/irgs.h"
 #include "scene.h"
+
+namespace irgs {
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace irgs
 
 namespace {
 
@@ -54,6 +61,8 @@ const char* irgs_status_string(irgs_status s) {
 
 int32_t irgs_abi_version(void) { return IRGS_ABI_VERSION; }
 
+uint64_t irgs_kernel_launches(void) { return irgs::g_launches.load(std::memory_order_relaxed); }
+
 irgs_status irgs_build_scene(const irgs_surfels* s, float alpha_min, void* stream, irgs_scene* out) {
     if (s == nullptr || out == nullptr) return IRGS_ERR_INVALID_ARG;
     if (s->n < 0 || s->n >= INT32_MAX) return IRGS_ERR_INVALID_ARG;
@@ -71,6 +80,16 @@ irgs_status irgs_build_scene(const irgs_surfels* s, float alpha_min, void* strea
         if (cudaSetDevice(at.device) != cudaSuccess) return IRGS_ERR_CUDA;
     }
     return irgs::build_scene_impl(s, alpha_min, static_cast<cudaStream_t>(stream), out);
+}
+
+irgs_status irgs_update_scene(irgs_scene sc, const irgs_surfels* s, void* stream) {
+    if (sc == nullptr || s == nullptr) return IRGS_ERR_INVALID_ARG;
+    if (s->n != sc->n || s->num_features != sc->F) return IRGS_ERR_INVALID_ARG;
+    if (s->n > 0 && (!s->means || !s->quats || !s->scales || !s->opacity)) return IRGS_ERR_INVALID_ARG;
+    if (s->n > 0 && s->num_features > 0 && !s->features) return IRGS_ERR_INVALID_ARG;
+    irgs_status st = use_device(sc);
+    if (st != IRGS_OK) return st;
+    return irgs::update_scene_impl(sc, s, static_cast<cudaStream_t>(stream));
 }
 
 irgs_status irgs_destroy_scene(irgs_scene sc) {

@@ -102,6 +102,10 @@ __device__ __forceinline__ float u01_from_bits(uint64_t z) {
 }
 
 // ---------------------------------------------------------------------------
+// Process-wide count of kernel launches (capi.cu owns the counter).
+void count_launches(uint64_t k);
+
+// ---------------------------------------------------------------------------
 // Device view of a scene (plain pointers, passed by value to kernels).
 struct SceneView {
     const Node* nodes;     // [max(n-1,1)]

@@ -364,6 +364,52 @@ void free_scene(irgs_scene sc) {
     delete sc;
 }
 
+// Enqueue the whole build (K1-K5) for surfels `s` into the scene's buffers.
+static irgs_status enqueue_build(irgs_scene sc, const irgs_surfels* s, cudaStream_t st) {
+    const int64_t n = sc->n;
+    const int32_t F = sc->F;
+    const int64_t nn = n > 1 ? n - 1 : 1;
+    const int64_t tiles = (n + kTile - 1) / kTile;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(cudaMemsetAsync(sc->nodes, 0, sizeof(Node) * nn, st));
+    A(cudaMemsetAsync(sc->refit_flag, 0, sizeof(uint32_t) * nn, st));
+    // bounds: mins start at the largest ordered value, maxes at the smallest
+    A(cudaMemsetAsync(sc->bounds, 0xff, 3 * sizeof(uint32_t), st));
+    A(cudaMemsetAsync(sc->bounds + 3, 0x00, 3 * sizeof(uint32_t), st));
+    if (n > 0) {
+        const int T = 256;
+        k_surfel_boxes<<<blocks_for(n, T), T, 0, st>>>(s->means, s->quats, s->scales, s->opacity, n,
+                                                       (double)sc->alpha_min, sc->rec_user, sc->box_user, sc->bounds);
+        k_morton<<<blocks_for(n, T), T, 0, st>>>(sc->rec_user, n, sc->bounds, sc->keys, sc->perm);
+        // 4 passes ping-pong: keys/perm -> tmp -> keys/perm ...
+        uint32_t* ka = sc->keys; int32_t* va = sc->perm;
+        uint32_t* kb = sc->keys_tmp; int32_t* vb = sc->vals_tmp;
+        for (int shift = 0; shift < 32; shift += 8) {
+            k_sort_hist<<<(unsigned)tiles, 256, 0, st>>>(ka, n, shift, (int)tiles, sc->hist);
+            k_scan_exclusive<<<1, 1024, 0, st>>>(sc->hist, 256 * tiles);
+            k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(ka, va, n, shift, (int)tiles, sc->hist, kb, vb);
+            uint32_t* tk = ka; ka = kb; kb = tk;
+            int32_t* tv = va; va = vb; vb = tv;
+        }
+        // after an even number of passes the sorted data is back in keys/perm
+        k_gather<<<blocks_for(n, T), T, 0, st>>>(sc->perm, n, sc->rec_user, sc->box_user, s->quats, s->scales,
+                                                 sc->rec, sc->leaf_box, sc->q_raw, sc->scale);
+        if (F > 0)
+            k_gather_feat<<<blocks_for(n * F, T), T, 0, st>>>(sc->perm, n, F, s->features, sc->feat);
+        if (n > 1) {
+            k_karras<<<blocks_for(n - 1, T), T, 0, st>>>(sc->keys, n, sc->nodes, sc->leaf_parent, sc->node_parent);
+            k_refit<<<blocks_for(n, T), T, 0, st>>>(n, sc->leaf_box, sc->leaf_parent, sc->node_parent, sc->nodes,
+                                                    sc->refit_flag, sc->status);
+        }
+    }
+    if (n <= 1) k_tiny_root<<<1, 1, 0, st>>>(n, sc->leaf_box, sc->nodes);
+    // boxes, morton, 4 x (hist, scan, scatter), gather = 15; + features; + karras/refit or the tiny root
+    count_launches(n == 0 ? 1 : 15 + (F > 0) + (n == 1 ? 1 : 2));
+    A(cudaGetLastError());
+    return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+}
+
 irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_t st, irgs_scene* out) {
     const int64_t n = s->n;
     const int32_t F = s->num_features;
@@ -401,47 +447,22 @@ irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_
         free_scene(sc);
         return e == cudaErrorMemoryAllocation ? IRGS_ERR_OOM : IRGS_ERR_CUDA;
     }
-    A(cudaMemsetAsync(sc->status, 0, sizeof(uint32_t), st));
-    A(cudaMemsetAsync(sc->nodes, 0, sizeof(Node) * nn, st));
-    A(cudaMemsetAsync(sc->refit_flag, 0, sizeof(uint32_t) * nn, st));
-    // bounds: mins start at the largest ordered value, maxes at the smallest
-    A(cudaMemsetAsync(sc->bounds, 0xff, 3 * sizeof(uint32_t), st));
-    A(cudaMemsetAsync(sc->bounds + 3, 0x00, 3 * sizeof(uint32_t), st));
-    if (n > 0) {
-        const int T = 256;
-        k_surfel_boxes<<<blocks_for(n, T), T, 0, st>>>(s->means, s->quats, s->scales, s->opacity, n,
-                                                       (double)alpha_min, sc->rec_user, sc->box_user, sc->bounds);
-        k_morton<<<blocks_for(n, T), T, 0, st>>>(sc->rec_user, n, sc->bounds, sc->keys, sc->perm);
-        // 4 passes ping-pong: keys/perm -> tmp -> keys/perm ...
-        uint32_t* ka = sc->keys; int32_t* va = sc->perm;
-        uint32_t* kb = sc->keys_tmp; int32_t* vb = sc->vals_tmp;
-        for (int shift = 0; shift < 32; shift += 8) {
-            k_sort_hist<<<(unsigned)tiles, 256, 0, st>>>(ka, n, shift, (int)tiles, sc->hist);
-            k_scan_exclusive<<<1, 1024, 0, st>>>(sc->hist, 256 * tiles);
-            k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(ka, va, n, shift, (int)tiles, sc->hist, kb, vb);
-            uint32_t* tk = ka; ka = kb; kb = tk;
-            int32_t* tv = va; va = vb; vb = tv;
-        }
-        // after an even number of passes the sorted data is back in keys/perm
-        k_gather<<<blocks_for(n, T), T, 0, st>>>(sc->perm, n, sc->rec_user, sc->box_user, s->quats, s->scales,
-                                                 sc->rec, sc->leaf_box, sc->q_raw, sc->scale);
-        if (F > 0)
-            k_gather_feat<<<blocks_for(n * F, T), T, 0, st>>>(sc->perm, n, F, s->features, sc->feat);
-        if (n > 1) {
-            k_karras<<<blocks_for(n - 1, T), T, 0, st>>>(sc->keys, n, sc->nodes, sc->leaf_parent, sc->node_parent);
-            k_refit<<<blocks_for(n, T), T, 0, st>>>(n, sc->leaf_box, sc->leaf_parent, sc->node_parent, sc->nodes,
-                                                    sc->refit_flag, sc->status);
-        }
-    }
-    if (n <= 1) k_tiny_root<<<1, 1, 0, st>>>(n, sc->leaf_box, sc->nodes);
-    A(cudaGetLastError());
-    if (e != cudaSuccess) {
-        cudaStreamSynchronize(st);
+    if (cudaMemsetAsync(sc->status, 0, sizeof(uint32_t), st) != cudaSuccess) {
         free_scene(sc);
         return IRGS_ERR_CUDA;
     }
+    irgs_status r = enqueue_build(sc, s, st);
+    if (r != IRGS_OK) {
+        cudaStreamSynchronize(st);
+        free_scene(sc);
+        return r;
+    }
     *out = sc;
     return IRGS_OK;
+}
+
+irgs_status update_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t st) {
+    return enqueue_build(sc, s, st);
 }
 
 }  // namespace irgs

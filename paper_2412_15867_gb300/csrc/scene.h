@@ -55,6 +55,7 @@ namespace irgs {
 
 // scene.cu
 irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_t st, irgs_scene* out);
+irgs_status update_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t st);
 void free_scene(irgs_scene sc);
 
 // trace_fwd.cu

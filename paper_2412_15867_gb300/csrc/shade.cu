@@ -174,6 +174,7 @@ irgs_status launch_shade_mc(const SceneView& S, const float* x, const float* n, 
             break;
         default: return IRGS_ERR_UNSUPPORTED;
     }
+    count_launches(1);
     return cudaGetLastError() == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
 }
 

@@ -199,6 +199,7 @@ cudaError_t launch(const SceneView& S, const float* ro, const float* rd, int64_t
     const int64_t blocks = (R + kBwdThreads - 1) / kBwdThreads;
     k_trace_backward<K, FB><<<(unsigned)blocks, kBwdThreads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac, nhits,
                                                                       gf, gd, go, gm, gq, gs, gop, gfe);
+    count_launches(1);
     return cudaGetLastError();
 }
 

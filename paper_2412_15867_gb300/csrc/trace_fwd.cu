@@ -43,6 +43,7 @@ cudaError_t launch(const SceneView& S, const float* ro, const float* rd, int64_t
     const int64_t blocks = (R + kFwdThreads - 1) / kFwdThreads;
     k_trace_forward<K, FB><<<(unsigned)blocks, kFwdThreads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac, nhits,
                                                                      ids, max_ids);
+    count_launches(1);
     return cudaGetLastError();
 }
 

@@ -39,8 +39,9 @@ def check(out, ref, frac=0.999):
     g = out["rgb"].cpu().numpy().astype(np.float64)
     err = np.abs(g - ref["rgb"]).max(1) / np.maximum(1.0, np.abs(ref["rgb"]).max(1))
     ok = ref["flags"] == 0
-    st = {"points": int(err.size), "unflagged": float(ok.mean()), "max_err_unflagged": float(err[ok].max()),
-          "within": float((err <= 1e-4).mean())}
+    st = {"points": int(err.size), "unflagged": float(ok.mean()),
+          "max_err_unflagged": float(err[ok].max()) if ok.any() else None,
+          "max_err_all": float(err.max()), "within": float((err <= 1e-4).mean())}
     assert (err <= 1e-4).mean() >= frac, st
     assert np.all(err[ok] <= 2e-3), st
     v = out["vis"].cpu().numpy()
