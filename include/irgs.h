@@ -218,6 +218,39 @@ irgs_status irgs_shade_mc(irgs_scene scene, const float* x, const float* n, cons
                           uint64_t seed, const irgs_trace_params* params, float* out_rgb,
                           float* out_vis, float* out_ind, void* stream);
 
+/*
+ * Allocation-free LBVH build (the paper has no counterpart; this is a
+ * deployment variant of irgs_build_scene).
+ *
+ * Some callers cannot let a library allocate device memory: applications
+ * that own every byte of GPU memory through their own arena or budget, and
+ * loops that cannot afford the device-wide synchronisation a cudaMalloc or
+ * cudaFree implies. For them this call builds the same hierarchy as
+ * irgs_build_scene -- Morton order, sorted keys, internal nodes and leaf
+ * boxes, identical to what irgs_scene_export returns for the same surfels
+ * -- into buffers the caller passes, and allocates nothing: its working
+ * memory is one fixed array of about 6.5 MB inside the library (a
+ * file-scope __device__ array that every GPU which loads the library holds
+ * until the process exits).
+ *   surfels   : device arrays as for irgs_build_scene; features are ignored.
+ *               n must not exceed IRGS_NOALLOC_MAX_SURFELS, otherwise the
+ *               call returns IRGS_ERR_INVALID_ARG and does nothing.
+ *   alpha_min : as for irgs_build_scene (> 0).
+ *   perm      : [n] int32 device buffer, user index of each Morton slot.
+ *   keys      : [n] uint32 device buffer, sorted Morton codes.
+ *   nodes     : [max(n-1,1), 16] float32 device buffer (layout as in
+ *               irgs_scene_export).
+ *   leaf_boxes: [n, 6] float32 device buffer.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. All calls share the one array and it keeps the last call's
+ * contents; calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it, so serialise them. Work is enqueued on `stream`.
+ */
+#define IRGS_NOALLOC_MAX_SURFELS 32768
+irgs_status irgs_build_lbvh_noalloc(const irgs_surfels* surfels, float alpha_min, int32_t* perm,
+                                    uint32_t* keys, float* nodes, float* leaf_boxes, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -191,4 +191,22 @@ irgs_status irgs_shade_mc(irgs_scene sc, const float* x, const float* n, const f
                                  seed, *params, out_rgb, out_vis, out_ind, static_cast<cudaStream_t>(stream));
 }
 
+irgs_status irgs_build_lbvh_noalloc(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,
+                                    float* nodes, float* leaf_boxes, void* stream) {
+    if (s == nullptr) return IRGS_ERR_INVALID_ARG;
+    if (s->n < 0 || s->n > IRGS_NOALLOC_MAX_SURFELS) return IRGS_ERR_INVALID_ARG;
+    if (!finite(alpha_min) || !(alpha_min > 0.f) || !(alpha_min < 1.f)) return IRGS_ERR_INVALID_ARG;
+    if (!nodes) return IRGS_ERR_INVALID_ARG;
+    if (s->n > 0 && (!s->means || !s->quats || !s->scales || !s->opacity || !perm || !keys || !leaf_boxes))
+        return IRGS_ERR_INVALID_ARG;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, nodes) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return IRGS_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(at.device) != cudaSuccess) return IRGS_ERR_CUDA;
+    return irgs::build_lbvh_noalloc_impl(s, alpha_min, perm, keys, nodes, leaf_boxes,
+                                         static_cast<cudaStream_t>(stream));
+}
+
 }  // extern "C"

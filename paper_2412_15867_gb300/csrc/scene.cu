@@ -9,6 +9,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -463,6 +464,88 @@ irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_
 
 irgs_status update_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t st) {
     return enqueue_build(sc, s, st);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free build: all working memory of the build comes from one
+// file-scope device array; the caller provides the outputs.
+namespace {
+
+constexpr int64_t kNoallocMax = IRGS_NOALLOC_MAX_SURFELS;
+constexpr size_t kAlign = 256;
+constexpr size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign; }
+constexpr int64_t kNoallocTiles = (kNoallocMax + kTile - 1) / kTile;
+constexpr size_t kNoallocBytes =
+    align_up(sizeof(float4) * 4 * kNoallocMax) * 2 +      // records in user and Morton order
+    align_up(sizeof(float) * 6 * kNoallocMax) +           // user-order boxes
+    align_up(sizeof(float4) * kNoallocMax) +              // raw quaternions
+    align_up(sizeof(float2) * kNoallocMax) +              // scales
+    align_up(sizeof(uint32_t) * kNoallocMax) * 2 +        // sort ping-pong keys / values
+    align_up(sizeof(int32_t) * kNoallocMax) * 3 +         // leaf parents, node parents, refit flags
+    align_up(sizeof(uint32_t) * 256 * kNoallocTiles) +    // digit histograms
+    align_up(sizeof(uint32_t) * 6) + align_up(sizeof(uint32_t));   // bounds, status word
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_ptr[256] = {};
+
+// Device address of the scratch array on the current device (looked up once
+// per device). Returns nullptr if the lookup fails.
+void* noalloc_scratch(int device) {
+    if (device < 0 || device >= 256) return nullptr;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_ptr[device] == nullptr) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_noalloc_ptr[device] = p;
+    }
+    return g_noalloc_ptr[device];
+}
+
+}  // namespace
+
+irgs_status build_lbvh_noalloc_impl(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,
+                                    float* nodes, float* leaf_boxes, cudaStream_t st) {
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return IRGS_ERR_CUDA;
+    unsigned char* base = static_cast<unsigned char*>(noalloc_scratch(device));
+    if (base == nullptr) return IRGS_ERR_CUDA;
+    const int64_t n = s->n, M = kNoallocMax;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        unsigned char* p = base + off;
+        off += align_up(bytes);
+        return p;
+    };
+    irgs_scene_s sc;   // a view onto caller buffers and the scratch array
+    sc.device = device;
+    sc.n = n;
+    sc.F = 0;
+    sc.alpha_min = alpha_min;
+    sc.rec_user = reinterpret_cast<float4*>(take(sizeof(float4) * 4 * M));
+    sc.rec = reinterpret_cast<float4*>(take(sizeof(float4) * 4 * M));
+    sc.box_user = reinterpret_cast<float*>(take(sizeof(float) * 6 * M));
+    sc.q_raw = reinterpret_cast<float4*>(take(sizeof(float4) * M));
+    sc.scale = reinterpret_cast<float2*>(take(sizeof(float2) * M));
+    sc.keys_tmp = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * M));
+    sc.vals_tmp = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * M));
+    sc.leaf_parent = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * M));
+    sc.node_parent = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * M));
+    sc.refit_flag = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * M));
+    sc.hist = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * 256 * kNoallocTiles));
+    sc.bounds = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * 6));
+    sc.status = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t)));
+    sc.keys = keys;
+    sc.perm = perm;
+    sc.nodes = reinterpret_cast<Node*>(nodes);
+    sc.leaf_box = leaf_boxes;
+    if (off > kNoallocBytes) return IRGS_ERR_CUDA;   // carve-out mismatch (cannot happen)
+    if (cudaMemsetAsync(sc.status, 0, sizeof(uint32_t), st) != cudaSuccess) return IRGS_ERR_CUDA;
+    return enqueue_build(&sc, s, st);
 }
 
 }  // namespace irgs
