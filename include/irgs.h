@@ -5,8 +5,8 @@
  * (Gu et al., "IRGS: Inter-Reflective Gaussian Splatting with 2D Gaussian Ray
  * Tracing", CVPR 2025, arXiv 2412.15867): the ray-splat intersection of
  * Eq. 6, the surfel response of Eq. 7, front-to-back alpha blending (Eq. 2)
- * into Trace(r_o, r_d) of Eq. 8, its gradient (Sec. 3.3, "our 2D Gaussian ray
- * tracing approach is fully differentiable"), and the Monte Carlo rendering
+ * into Trace(r_o, r_d) of Eq. 8, its gradient (the tracer is differentiable,
+ * Sec. 3.3, so indirect radiance can be optimised), and the Monte Carlo rendering
  * equation of Eq. 15 with the light split of Eq. 13-14.
  *
  * Conventions shared by every entry point
@@ -106,8 +106,8 @@ irgs_status irgs_build_scene(const irgs_surfels* surfels, float alpha_min, void*
 
 /*
  * Rebuild an existing scene in place from new surfel values (same n and
- * num_features): the per-iteration BVH update of a training loop (Sec. 4,
- * "updating the BVH at each training iteration for the varying geometry").
+ * num_features): the BVH update that a training loop runs every iteration
+ * because the geometry changes (Sec. 4).
  * Reuses the scene's device buffers, allocates nothing, and is enqueued on
  * `stream`; traces already enqueued on other streams must finish first.
  * IRGS_ERR_INVALID_ARG if n or num_features differ from the scene's.

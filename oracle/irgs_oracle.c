@@ -13,7 +13,7 @@
  *                    with early termination on transmittance (Sec. 4 impl.).
  *   - oracle_trace_grad: the analytic gradient of the blended outputs with
  *                    respect to every surfel parameter (the tracer is
- *                    differentiable, Sec. 3.3 "Light parametrization"),
+ *                    differentiable, Sec. 3.3, light parametrization),
  *                    accumulating the suffix sum with a reverse loop.
  *   - oracle_shade:  the Monte Carlo rendering-equation estimate of Eq. 15
  *                    with Eq. 13-14 light decomposition, using cosine and GGX

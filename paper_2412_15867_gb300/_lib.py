@@ -74,7 +74,7 @@ def lib() -> C.CDLL:
             return _lib
         if not os.path.exists(LIB_PATH):
             raise ImportError(f"libirgs.so is not built ({LIB_PATH}); run "
-                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+                              "`python -m paper_2412_15867_gb300._build`")
         L = C.CDLL(LIB_PATH)
         for name, (res, args) in _SIGS.items():
             f = getattr(L, name)
