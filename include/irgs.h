@@ -73,8 +73,17 @@ typedef struct {
     float t_max;          /* hits need tau < t_max (may be +inf)                    */
     int32_t feat_offset;  /* first blended feature channel                          */
     int32_t feat_count;   /* blended channels, 0 .. IRGS_MAX_FEATURES               */
-    uint32_t flags;       /* reserved, must be 0                                    */
+    uint32_t flags;       /* IRGS_FLAG_* bits, 0 for the defaults                   */
 } irgs_trace_params;
+
+/* Traversal policy (results are identical either way, only speed differs).
+ * Default for irgs_trace_forward / irgs_trace_backward: warp-coherent -- the
+ * 32 rays of a warp walk one shared stack, best for coherent batches such as
+ * camera rays in image order. Default for irgs_shade_mc: per ray.
+ * IRGS_FLAG_PER_THREAD forces an independent stack per ray; IRGS_FLAG_WARP
+ * forces the warp-coherent walk. Setting both is invalid. */
+#define IRGS_FLAG_PER_THREAD 1u
+#define IRGS_FLAG_WARP 2u
 
 /* Human-readable name of a status code (static storage). */
 const char* irgs_status_string(irgs_status status);

@@ -24,6 +24,10 @@ __all__ = ["TraceParams", "Scene", "trace", "trace_forward", "trace_backward", "
            "IrgsError", "library_path"]
 
 
+FLAG_PER_THREAD = 1   # one traversal stack per ray
+FLAG_WARP = 2         # one traversal stack per warp of 32 rays
+
+
 def library_path() -> str:
     return _lib.LIB_PATH
 
@@ -39,11 +43,12 @@ class TraceParams:
     t_max: float = math.inf
     feat_offset: int = 0
     feat_count: int = 3
+    flags: int = 0          # FLAG_PER_THREAD / FLAG_WARP traversal policy (0: library default)
 
     def c(self) -> _lib.TraceParamsC:
         return _lib.TraceParamsC(int(self.k), float(self.alpha_min), float(self.alpha_max),
                                  float(self.T_min), float(self.t_min), float(self.t_max),
-                                 int(self.feat_offset), int(self.feat_count), 0)
+                                 int(self.feat_offset), int(self.feat_count), int(self.flags))
 
     def with_(self, **kw) -> "TraceParams":
         return replace(self, **kw)

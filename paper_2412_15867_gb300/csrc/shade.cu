@@ -8,7 +8,10 @@
 //
 // One warp shades one point: lanes take samples s = lane, lane + 32, ... and
 // the per-point sums are reduced with a fixed butterfly, so a point's result
-// depends only on (seed, point index, inputs), not on batching.
+// depends only on (seed, point index, inputs), not on batching. The traced
+// rays of a point share their origin; by default each lane walks its own
+// stack (the directions spread over the hemisphere), IRGS_FLAG_WARP walks
+// one stack for the warp. Both give identical results.
 #include <cuda_runtime.h>
 
 #include "scene.h"
@@ -65,7 +68,7 @@ __device__ __forceinline__ f3 env_lookup(const float* __restrict__ env, int H, i
 
 __device__ __forceinline__ f3 ld3(const float* p, int64_t i) { return mk3(p[3 * i], p[3 * i + 1], p[3 * i + 2]); }
 
-template <int K>
+template <int K, bool WARP>
 __global__ void __launch_bounds__(kShadeThreads) k_shade(SceneView S, const float* __restrict__ xg,
                                                          const float* __restrict__ ng, const float* __restrict__ ag,
                                                          const float* __restrict__ rg, const float* __restrict__ wog,
@@ -94,30 +97,39 @@ __global__ void __launch_bounds__(kShadeThreads) k_shade(SceneView S, const floa
     onb(n, b1, b2);
     const int St = nd + ns;
     float sd[3] = {0.f, 0.f, 0.f}, ss[3] = {0.f, 0.f, 0.f}, si[3] = {0.f, 0.f, 0.f}, sv = 0.f;
-    for (int s = lane; s < St; s += 32) {
-        const uint64_t i0 = ((uint64_t)p * (uint64_t)St + (uint64_t)s) * 2ull;
-        const float u1 = u01_from_bits(splitmix64_at(seed, i0));
-        const float u2 = u01_from_bits(splitmix64_at(seed, i0 + 1));
-        float sp, cp;
-        sincospif(2.f * u2, &sp, &cp);
-        f3 wi, h;
-        bool diffuse = s < nd;
+    // lane l takes samples l, l + 32, ...; the trip count is the same for the
+    // whole warp so the warp-coherent walk keeps every lane in the loop
+    for (int base = 0; base < St; base += 32) {
+        const int s = base + lane;
+        const bool diffuse = s < nd;
+        bool valid = s < St;
+        f3 wi = mk3(0.f, 0.f, 1.f), h = mk3(0.f, 0.f, 1.f);
         float oh = 0.f, nh = 0.f;
-        if (diffuse) {
-            const float r = sqrtf(u1);
-            wi = normalize3(from_local(mk3(r * cp, r * sp, sqrtf(fmaxf(0.f, 1.f - u1))), b1, b2, n));
-        } else {
-            const float c2 = (1.f - u1) / (1.f + (a2 - 1.f) * u1);
-            const float ct = sqrtf(c2), st = sqrtf(fmaxf(0.f, 1.f - c2));
-            h = normalize3(from_local(mk3(st * cp, st * sp, ct), b1, b2, n));
-            oh = dot3(wo, h);
-            wi = normalize3(sub3(mul3(h, 2.f * oh), wo));
-            nh = dot3(n, h);
-            if (!(oh > 0.f) || !(dot3(wi, n) > 0.f)) continue;   // below the horizon: adds 0
+        if (valid) {
+            const uint64_t i0 = ((uint64_t)p * (uint64_t)St + (uint64_t)s) * 2ull;
+            const float u1 = u01_from_bits(splitmix64_at(seed, i0));
+            const float u2 = u01_from_bits(splitmix64_at(seed, i0 + 1));
+            float sp, cp;
+            sincospif(2.f * u2, &sp, &cp);
+            if (diffuse) {
+                const float r = sqrtf(u1);
+                wi = normalize3(from_local(mk3(r * cp, r * sp, sqrtf(fmaxf(0.f, 1.f - u1))), b1, b2, n));
+            } else {
+                const float c2 = (1.f - u1) / (1.f + (a2 - 1.f) * u1);
+                const float ct = sqrtf(c2), st = sqrtf(fmaxf(0.f, 1.f - c2));
+                h = normalize3(from_local(mk3(st * cp, st * sp, ct), b1, b2, n));
+                oh = dot3(wo, h);
+                wi = normalize3(sub3(mul3(h, 2.f * oh), wo));
+                nh = dot3(n, h);
+                valid = oh > 0.f && dot3(wi, n) > 0.f;   // below the horizon: adds 0
+            }
         }
+        if (!WARP && !valid) continue;
         const Ray ray = make_ray(x, wi);
         MarchState<K, 3> st;
-        if (!march_forward<K, 3>(S, ray, TP, st, nullptr, 0)) atomicOr(S.status, kErrStackOverflow);
+        const bool ok = march_forward<K, 3, WARP>(S, ray, TP, st, nullptr, 0, valid);
+        if (!valid) continue;
+        if (!ok) atomicOr(S.status, kErrStackOverflow);
         const float V = st.T;
         const f3 Ld = env_lookup(env, H, W, wi);
         const float Li[3] = {V * Ld.x + st.C[0], V * Ld.y + st.C[1], V * Ld.z + st.C[2]};
@@ -163,17 +175,20 @@ irgs_status launch_shade_mc(const SceneView& S, const float* x, const float* n, 
     if (P == 0) return IRGS_OK;
     const TraceParams TP = to_params(p);
     const int64_t blocks = (P + (kShadeThreads / 32) - 1) / (kShadeThreads / 32);
+    const bool warp = (p.flags & IRGS_FLAG_WARP) != 0u;
+#define IRGS_SHADE_LAUNCH(KK, WW)                                                                        \
+    k_shade<KK, WW><<<(unsigned)blocks, kShadeThreads, 0, st>>>(S, x, n, albedo, rough, wo, P, env, H, W, \
+                                                               n_diffuse, n_spec, seed, TP, rgb, vis, ind)
     switch (p.k) {
         case 8:
-            k_shade<8><<<(unsigned)blocks, kShadeThreads, 0, st>>>(S, x, n, albedo, rough, wo, P, env, H, W, n_diffuse,
-                                                                   n_spec, seed, TP, rgb, vis, ind);
+            if (warp) IRGS_SHADE_LAUNCH(8, true); else IRGS_SHADE_LAUNCH(8, false);
             break;
         case 16:
-            k_shade<16><<<(unsigned)blocks, kShadeThreads, 0, st>>>(S, x, n, albedo, rough, wo, P, env, H, W,
-                                                                    n_diffuse, n_spec, seed, TP, rgb, vis, ind);
+            if (warp) IRGS_SHADE_LAUNCH(16, true); else IRGS_SHADE_LAUNCH(16, false);
             break;
         default: return IRGS_ERR_UNSUPPORTED;
     }
+#undef IRGS_SHADE_LAUNCH
     count_launches(1);
     return cudaGetLastError() == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
 }

@@ -162,6 +162,26 @@ struct KBuffer {
 
 __device__ __forceinline__ float key_depth(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
 
+// Test surfel m against the ray and insert it into the k-buffer if it lies
+// strictly after (last_key, last_m) and before the buffer's last entry.
+template <int K>
+__device__ __forceinline__ void leaf_insert(const SceneView& S, const Ray& ray, const TraceParams& P, int32_t m,
+                                            uint64_t last_key, int32_t last_m, KBuffer<K>& kb, float& t_hi) {
+    const float4* R = S.rec + (int64_t)m * kRecF4;
+    const float4 r0 = ldg4(R), r1 = ldg4(R + 1), r2 = ldg4(R + 2), r3 = ldg4(R + 3);
+    float kh, kl, a;
+    if (!surfel_hit<false>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a, nullptr)) return;
+    const uint64_t key = depth_key(kh, kl);
+    const bool past_min = kh > P.t_min || (kh == P.t_min && kl > 0.f);
+    const bool after = past_min && (key > last_key || (key == last_key && m > last_m));
+    const bool before = kh < P.t_max || (kh == P.t_max && kl < 0.f);
+    const bool fits = !kb.full() || key < kb.key[K - 1] || (key == kb.key[K - 1] && m < kb.m[K - 1]);
+    if (after && before && fits) {
+        kb.insert(key, m, a);
+        if (kb.full()) t_hi = key_depth(kb.key[K - 1]);
+    }
+}
+
 // One round: gather the K nearest hits strictly after (last_key, last_m).
 // Returns false if the traversal stack overflowed.
 template <int K>
@@ -190,29 +210,8 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
         float hi_c = t_hi + tslack(t_hi);
         bool h0 = c0 != kNoChild && tn0 <= tf0 && tf0 >= lo_c && tn0 <= hi_c;
         bool h1 = c1 != kNoChild && tn1 <= tf1 && tf1 >= lo_c && tn1 <= hi_c;
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const bool h = side == 0 ? h0 : h1;
-            const int c = side == 0 ? c0 : c1;
-            if (h && c < 0) {
-                const int32_t m = ~c;
-                const float4* R = S.rec + (int64_t)m * kRecF4;
-                const float4 r0 = ldg4(R), r1 = ldg4(R + 1), r2 = ldg4(R + 2), r3 = ldg4(R + 3);
-                float kh, kl, a;
-                if (surfel_hit<false>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a, nullptr)) {
-                    const uint64_t key = depth_key(kh, kl);
-                    const bool past_min = kh > P.t_min || (kh == P.t_min && kl > 0.f);
-                    const bool after = past_min && (key > last_key || (key == last_key && m > last_m));
-                    const bool before = kh < P.t_max || (kh == P.t_max && kl < 0.f);
-                    const bool fits = !kb.full() || key < kb.key[K - 1] ||
-                                      (key == kb.key[K - 1] && m < kb.m[K - 1]);
-                    if (after && before && fits) {
-                        kb.insert(key, m, a);
-                        if (kb.full()) t_hi = key_depth(kb.key[K - 1]);
-                    }
-                }
-            }
-        }
+        if (h0 && c0 < 0) leaf_insert<K>(S, ray, P, ~c0, last_key, last_m, kb, t_hi);
+        if (h1 && c1 < 0) leaf_insert<K>(S, ray, P, ~c1, last_key, last_m, kb, t_hi);
         if (c0 < 0) h0 = false;
         if (c1 < 0) h1 = false;
         hi_c = t_hi + tslack(t_hi);
@@ -249,6 +248,76 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
     return ok;
 }
 
+constexpr unsigned kFullWarp = 0xffffffffu;
+
+// Warp-coherent round: the 32 lanes of a warp walk one shared traversal
+// stack (entry e lives in register e/32 of lane e%32). A child is visited when
+// any lane's ray overlaps its box inside that lane's (t_lo, t_hi) window;
+// each lane tests leaves with its own ray and keeps its own k-buffer, so the
+// result per ray equals the per-thread round. All 32 lanes must call this
+// together (inactive lanes pass active = false).
+template <int K>
+__device__ __forceinline__ bool collect_round_warp(const SceneView& S, const Ray& ray, const TraceParams& P,
+                                                   uint64_t last_key, int32_t last_m, KBuffer<K>& kb,
+                                                   bool active) {
+    kb.clear();
+    const int lane = threadIdx.x & 31;
+    const float t_lo = key_depth(last_key);
+    const float lo_c = t_lo - tslack(t_lo);
+    float t_hi = P.t_max;
+    int st0 = 0, st1 = 0;
+    int sp = 0;
+    bool ok = true;
+    int ni = 0;
+    const int64_t max_visits = 2 * S.n + 64;
+    for (int64_t visits = 0;; ++visits) {
+        if (visits > max_visits) {
+            ok = false;
+            break;
+        }
+        const Node nd = load_node(S.nodes, ni);
+        float tn0, tf0, tn1, tf1;
+        slab2(nd, ray, tn0, tf0, tn1, tf1);
+        const int c0 = nd.d.x, c1 = nd.d.y;
+        float hi_c = t_hi + tslack(t_hi);
+        const bool h0 = active && c0 != kNoChild && tn0 <= tf0 && tf0 >= lo_c && tn0 <= hi_c;
+        const bool h1 = active && c1 != kNoChild && tn1 <= tf1 && tf1 >= lo_c && tn1 <= hi_c;
+        if (h0 && c0 < 0) leaf_insert<K>(S, ray, P, ~c0, last_key, last_m, kb, t_hi);
+        if (h1 && c1 < 0) leaf_insert<K>(S, ray, P, ~c1, last_key, last_m, kb, t_hi);
+        hi_c = t_hi + tslack(t_hi);
+        const bool v0 = c0 >= 0 && h0 && tn0 <= hi_c;
+        const bool v1 = c1 >= 0 && h1 && tn1 <= hi_c;
+        const unsigned b0 = __ballot_sync(kFullWarp, v0);
+        const unsigned b1 = __ballot_sync(kFullWarp, v1);
+        if (b0 != 0u && b1 != 0u) {
+            // go first where most of the lanes that need both go first
+            const unsigned both = b0 & b1;
+            const unsigned pref1 = __ballot_sync(kFullWarp, v0 && v1 && tn1 < tn0);
+            const bool first1 = 2 * __popc(pref1) > __popc(both);
+            const int farc = first1 ? c0 : c1;
+            if (sp < kStackSize) {
+                if (lane == (sp & 31)) {
+                    if (sp >> 5) st1 = farc; else st0 = farc;
+                }
+                ++sp;
+            } else {
+                ok = false;
+            }
+            ni = first1 ? c1 : c0;
+        } else if (b0 != 0u) {
+            ni = c0;
+        } else if (b1 != 0u) {
+            ni = c1;
+        } else {
+            if (sp == 0) break;
+            --sp;
+            const int v = __shfl_sync(kFullWarp, (sp >> 5) ? st1 : st0, sp & 31);
+            ni = v;
+        }
+    }
+    return ok;
+}
+
 // Full forward march of one ray: rounds of collect + blend until the
 // transmittance drops below T_min or no further hit exists.
 template <int K, int FB>
@@ -258,9 +327,12 @@ struct MarchState {
     int nh;
 };
 
-template <int K, int FB>
+// WARP = true: all 32 lanes of the warp call this together (lanes without a
+// ray pass live = false) and traverse warp-coherently.
+template <int K, int FB, bool WARP>
 __device__ __forceinline__ bool march_forward(const SceneView& S, const Ray& ray, const TraceParams& P,
-                                              MarchState<K, FB>& st, int32_t* ids, int max_ids) {
+                                              MarchState<K, FB>& st, int32_t* ids, int max_ids,
+                                              bool live = true) {
 #pragma unroll
     for (int c = 0; c < FB; ++c) st.C[c] = 0.f;
     st.D = 0.f;
@@ -271,9 +343,13 @@ __device__ __forceinline__ bool march_forward(const SceneView& S, const Ray& ray
     uint64_t last_key = depth_key(P.t_min, 0.f);
     int32_t last_m = INT32_MAX;
     KBuffer<K> kb;
-    bool done = false;
-    while (!done) {
-        ok &= collect_round<K>(S, ray, P, last_key, last_m, kb);
+    bool done = !live;
+    while (WARP ? __any_sync(kFullWarp, !done) : !done) {
+        if (WARP)
+            ok &= collect_round_warp<K>(S, ray, P, last_key, last_m, kb, !done);
+        else
+            ok &= collect_round<K>(S, ray, P, last_key, last_m, kb);
+        if (done) continue;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             if (j < kb.cnt && !done) {

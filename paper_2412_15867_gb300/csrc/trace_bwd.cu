@@ -75,7 +75,7 @@ __device__ __forceinline__ void scatter_grad(const GradVals<FB>& g, int32_t uid,
         if (c < fc) atomicAdd(g_feat + u * F + off + c, acc[10 + c]);
 }
 
-template <int K, int FB>
+template <int K, int FB, bool WARP>
 __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
     SceneView S, const float* __restrict__ ro, const float* __restrict__ rd, int64_t R, TraceParams P,
     const float* __restrict__ out_feat, const float* __restrict__ out_depth, const float* __restrict__ out_opac,
@@ -86,30 +86,36 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
     __shared__ float rows_all[kBwdThreads * (N + 1)];
     float* rows = rows_all + (threadIdx.x & ~31) * (N + 1);
     const int64_t r = blockIdx.x * (int64_t)kBwdThreads + threadIdx.x;
-    if (r >= R) return;
-    const int nh_total = out_nhits[r];
-    if (nh_total <= 0 || S.n == 0) return;
-    const Ray ray = make_ray(mk3(ro[3 * r], ro[3 * r + 1], ro[3 * r + 2]),
-                             mk3(rd[3 * r], rd[3 * r + 1], rd[3 * r + 2]));
+    if (S.n == 0) return;
+    const int nh_total = r < R ? out_nhits[r] : 0;
+    const bool live = nh_total > 0;
+    if (!WARP && !live) return;
+    const int64_t q = live ? r : 0;   // lanes without work follow the warp with a dummy ray
+    const Ray ray = make_ray(mk3(ro[3 * q], ro[3 * q + 1], ro[3 * q + 2]),
+                             mk3(rd[3 * q], rd[3 * q + 1], rd[3 * q + 2]));
     float gC[FB], Cf[FB], Cacc[FB];
 #pragma unroll
     for (int c = 0; c < FB; ++c) {
-        gC[c] = c < P.fc ? g_featv[r * P.fc + c] : 0.f;
-        Cf[c] = c < P.fc ? out_feat[r * P.fc + c] : 0.f;
+        gC[c] = c < P.fc ? g_featv[q * P.fc + c] : 0.f;
+        Cf[c] = c < P.fc ? out_feat[q * P.fc + c] : 0.f;
         Cacc[c] = 0.f;
     }
-    const float gD = g_depthv != nullptr ? g_depthv[r] : 0.f;
-    const float gO = g_opacv != nullptr ? g_opacv[r] : 0.f;
-    const float Df = out_depth[r];
-    const float Tfin = 1.0f - out_opac[r];
+    const float gD = g_depthv != nullptr ? g_depthv[q] : 0.f;
+    const float gO = g_opacv != nullptr ? g_opacv[q] : 0.f;
+    const float Df = out_depth[q];
+    const float Tfin = 1.0f - out_opac[q];
     float Dacc = 0.f, T = 1.f;
     int nh = 0;
     uint64_t last_key = depth_key(P.t_min, 0.f);
     int32_t last_m = INT32_MAX;
     KBuffer<K> kb;
-    bool ok = true, done = false;
-    while (!done) {
-        ok &= collect_round<K>(S, ray, P, last_key, last_m, kb);
+    bool ok = true, done = !live;
+    while (WARP ? __any_sync(kFullWarp, !done) : !done) {
+        if (WARP)
+            ok &= collect_round_warp<K>(S, ray, P, last_key, last_m, kb, !done);
+        else
+            ok &= collect_round<K>(S, ray, P, last_key, last_m, kb);
+        if (done) continue;
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             if (j < kb.cnt && nh < nh_total) {
@@ -188,30 +194,40 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
             last_m = kb.m[K - 1];
         }
     }
-    if (!ok) atomicOr(S.status, kErrStackOverflow);
+    if (live && !ok) atomicOr(S.status, kErrStackOverflow);
 }
 
-template <int K, int FB>
+template <int K, int FB, bool WARP>
 cudaError_t launch(const SceneView& S, const float* ro, const float* rd, int64_t R, const TraceParams& P,
                    const float* feat, const float* depth, const float* opac, const int32_t* nhits,
                    const float* gf, const float* gd, const float* go, float* gm, float* gq, float* gs,
                    float* gop, float* gfe, cudaStream_t st) {
     const int64_t blocks = (R + kBwdThreads - 1) / kBwdThreads;
-    k_trace_backward<K, FB><<<(unsigned)blocks, kBwdThreads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac, nhits,
+    k_trace_backward<K, FB, WARP><<<(unsigned)blocks, kBwdThreads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac, nhits,
                                                                       gf, gd, go, gm, gq, gs, gop, gfe);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <int K>
+template <int K, bool WARP>
 cudaError_t launch_f(const SceneView& S, const float* ro, const float* rd, int64_t R, const TraceParams& P,
                      const float* feat, const float* depth, const float* opac, const int32_t* nhits,
                      const float* gf, const float* gd, const float* go, float* gm, float* gq, float* gs,
                      float* gop, float* gfe, cudaStream_t st) {
-    if (P.fc <= 3) return launch<K, 3>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+    if (P.fc <= 3)
+        return launch<K, 3, WARP>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
     if (P.fc <= 10)
-        return launch<K, 10>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
-    return launch<K, 16>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+        return launch<K, 10, WARP>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+    return launch<K, 16, WARP>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+}
+
+template <int K>
+cudaError_t launch_k(bool warp, const SceneView& S, const float* ro, const float* rd, int64_t R,
+                     const TraceParams& P, const float* feat, const float* depth, const float* opac,
+                     const int32_t* nhits, const float* gf, const float* gd, const float* go, float* gm, float* gq,
+                     float* gs, float* gop, float* gfe, cudaStream_t st) {
+    return warp ? launch_f<K, true>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st)
+                : launch_f<K, false>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
 }
 
 }  // namespace
@@ -224,14 +240,15 @@ irgs_status launch_trace_backward(const SceneView& S, const float* ro, const flo
     if (R == 0) return IRGS_OK;
     const TraceParams P = to_params(p);
     cudaError_t e;
+    const bool warp = (p.flags & IRGS_FLAG_PER_THREAD) == 0u;
     switch (p.k) {
         case 8:
-            e = launch_f<8>(S, ro, rd, R, P, feat, depth, opac, nhits, g_feat, g_depth, g_opac, g_means, g_quats,
-                            g_scales, g_opacity, g_features, st);
+            e = launch_k<8>(warp, S, ro, rd, R, P, feat, depth, opac, nhits, g_feat, g_depth, g_opac, g_means,
+                            g_quats, g_scales, g_opacity, g_features, st);
             break;
         case 16:
-            e = launch_f<16>(S, ro, rd, R, P, feat, depth, opac, nhits, g_feat, g_depth, g_opac, g_means, g_quats,
-                             g_scales, g_opacity, g_features, st);
+            e = launch_k<16>(warp, S, ro, rd, R, P, feat, depth, opac, nhits, g_feat, g_depth, g_opac, g_means,
+                             g_quats, g_scales, g_opacity, g_features, st);
             break;
         default: return IRGS_ERR_UNSUPPORTED;
     }

@@ -9,7 +9,7 @@ namespace {
 
 constexpr int kFwdThreads = 128;
 
-template <int K, int FB>
+template <int K, int FB, bool WARP>
 __global__ void __launch_bounds__(kFwdThreads) k_trace_forward(SceneView S, const float* __restrict__ ro,
                                                                const float* __restrict__ rd, int64_t R,
                                                                TraceParams P, float* __restrict__ feat,
@@ -17,16 +17,19 @@ __global__ void __launch_bounds__(kFwdThreads) k_trace_forward(SceneView S, cons
                                                                int32_t* __restrict__ nhits, int32_t* __restrict__ ids,
                                                                int max_ids) {
     const int64_t r = blockIdx.x * (int64_t)kFwdThreads + threadIdx.x;
-    if (r >= R) return;
-    const Ray ray = make_ray(mk3(ro[3 * r], ro[3 * r + 1], ro[3 * r + 2]),
-                             mk3(rd[3 * r], rd[3 * r + 1], rd[3 * r + 2]));
+    const bool live = r < R;
+    if (!WARP && !live) return;
+    const int64_t q = live ? r : 0;   // lanes without a ray follow the warp with a dummy ray
+    const Ray ray = make_ray(mk3(ro[3 * q], ro[3 * q + 1], ro[3 * q + 2]),
+                             mk3(rd[3 * q], rd[3 * q + 1], rd[3 * q + 2]));
     int32_t* my_ids = nullptr;
-    if (ids != nullptr) {
+    if (ids != nullptr && live) {
         my_ids = ids + r * (int64_t)max_ids;
         for (int j = 0; j < max_ids; ++j) my_ids[j] = -1;
     }
     MarchState<K, FB> st;
-    const bool ok = march_forward<K, FB>(S, ray, P, st, my_ids, max_ids);
+    const bool ok = march_forward<K, FB, WARP>(S, ray, P, st, my_ids, max_ids, live);
+    if (!live) return;
     if (!ok) atomicOr(S.status, kErrStackOverflow);
 #pragma unroll
     for (int c = 0; c < FB; ++c)
@@ -36,24 +39,32 @@ __global__ void __launch_bounds__(kFwdThreads) k_trace_forward(SceneView S, cons
     if (nhits != nullptr) nhits[r] = st.nh;
 }
 
-template <int K, int FB>
+template <int K, int FB, bool WARP>
 cudaError_t launch(const SceneView& S, const float* ro, const float* rd, int64_t R, const TraceParams& P,
                    float* feat, float* depth, float* opac, int32_t* nhits, int32_t* ids, int max_ids,
                    cudaStream_t st) {
     const int64_t blocks = (R + kFwdThreads - 1) / kFwdThreads;
-    k_trace_forward<K, FB><<<(unsigned)blocks, kFwdThreads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac, nhits,
-                                                                     ids, max_ids);
+    k_trace_forward<K, FB, WARP><<<(unsigned)blocks, kFwdThreads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac,
+                                                                           nhits, ids, max_ids);
     count_launches(1);
     return cudaGetLastError();
 }
 
-template <int K>
+template <int K, bool WARP>
 cudaError_t launch_f(const SceneView& S, const float* ro, const float* rd, int64_t R, const TraceParams& P,
                      float* feat, float* depth, float* opac, int32_t* nhits, int32_t* ids, int max_ids,
                      cudaStream_t st) {
-    if (P.fc <= 3) return launch<K, 3>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st);
-    if (P.fc <= 10) return launch<K, 10>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st);
-    return launch<K, 16>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st);
+    if (P.fc <= 3) return launch<K, 3, WARP>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st);
+    if (P.fc <= 10) return launch<K, 10, WARP>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st);
+    return launch<K, 16, WARP>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st);
+}
+
+template <int K>
+cudaError_t launch_k(bool warp, const SceneView& S, const float* ro, const float* rd, int64_t R,
+                     const TraceParams& P, float* feat, float* depth, float* opac, int32_t* nhits, int32_t* ids,
+                     int max_ids, cudaStream_t st) {
+    return warp ? launch_f<K, true>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st)
+                : launch_f<K, false>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st);
 }
 
 }  // namespace
@@ -64,12 +75,13 @@ irgs_status launch_trace_forward(const SceneView& S, const float* ro, const floa
     if (R == 0) return IRGS_OK;
     const TraceParams P = to_params(p);
     cudaError_t e;
+    const bool warp = (p.flags & IRGS_FLAG_PER_THREAD) == 0u;
     switch (p.k) {
-        case 1: e = launch_f<1>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st); break;
-        case 4: e = launch_f<4>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st); break;
-        case 8: e = launch_f<8>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st); break;
-        case 16: e = launch_f<16>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st); break;
-        case 32: e = launch_f<32>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st); break;
+        case 1: e = launch_k<1>(warp, S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st); break;
+        case 4: e = launch_k<4>(warp, S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st); break;
+        case 8: e = launch_k<8>(warp, S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st); break;
+        case 16: e = launch_k<16>(warp, S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st); break;
+        case 32: e = launch_k<32>(warp, S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st); break;
         default: return IRGS_ERR_UNSUPPORTED;
     }
     return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;

@@ -28,7 +28,7 @@ __all__ = [
     "Surfels", "tiny_scene", "object_scene", "object_scene_median_scale",
     "look_at_rays", "tiny_camera", "hemisphere_cameras", "camera_batch_rays",
     "gbuffer_points", "env_map", "upstream_grads", "random_rays_through_scene",
-    "frame_to_quat",
+    "frame_to_quat", "tile_order",
 ]
 
 # Scene geometry of the object-centric stand-in (sphere, torus, ground).
@@ -167,9 +167,20 @@ def object_scene(n: int = 300_000, seed: int = 1001, median_scale: float | None 
                      for a in (p, q, scales, opacity, feats)))
 
 
+def tile_order(width: int, height: int, tile=(8, 4)) -> np.ndarray:
+    """Pixel indices (row-major numbering) listed tile by tile: tiles of
+    tile[0] x tile[1] pixels in row-major tile order, row-major inside a tile.
+    Edge tiles are clipped when the image is not a multiple of the tile."""
+    tw, th = tile
+    ys, xs = np.mgrid[0:height, 0:width]
+    key = ((ys // th) * ((width + tw - 1) // tw) + xs // tw) * (tw * th) + (ys % th) * tw + xs % tw
+    return np.argsort(key.reshape(-1), kind="stable")
+
+
 def look_at_rays(pos, target=(0.0, 0.0, 0.0), width: int = 64, height: int = 64,
-                 fov_deg: float = 60.0):
-    """Pinhole camera rays through pixel centres (row-major, top row first).
+                 fov_deg: float = 60.0, tile=None):
+    """Pinhole camera rays through pixel centres (row-major, top row first,
+    or tile by tile if `tile` = (tw, th) is given).
 
     z-up; if the view direction is within ~8 degrees of z, x is used as up.
     Returns float32 (origins [H*W,3], unit directions [H*W,3])."""
@@ -187,6 +198,8 @@ def look_at_rays(pos, target=(0.0, 0.0, 0.0), width: int = 64, height: int = 64,
     X, Y = np.meshgrid(xs, ys)
     d = fwd[None, :] + X.reshape(-1, 1) * right[None, :] + Y.reshape(-1, 1) * up2[None, :]
     d /= np.linalg.norm(d, axis=1, keepdims=True)
+    if tile is not None:
+        d = d[tile_order(width, height, tile)]
     o = np.broadcast_to(pos, d.shape)
     return np.ascontiguousarray(o, dtype=np.float32), np.ascontiguousarray(d, dtype=np.float32)
 
@@ -209,8 +222,9 @@ def hemisphere_cameras(n: int = 100, seed: int = 1001, radius: float = 4.0,
 
 
 def camera_batch_rays(cams: np.ndarray, width: int = 800, height: int = 800,
-                      fov_deg: float = 60.0, out_o=None, out_d=None):
-    """Rays of several cameras, concatenated camera-major (float32)."""
+                      fov_deg: float = 60.0, out_o=None, out_d=None, tile=None):
+    """Rays of several cameras, concatenated camera-major (float32); pixels
+    row-major or tile by tile (see look_at_rays)."""
     m = width * height
     n = cams.shape[0] * m
     if out_o is None:
@@ -218,7 +232,7 @@ def camera_batch_rays(cams: np.ndarray, width: int = 800, height: int = 800,
     if out_d is None:
         out_d = np.empty((n, 3), np.float32)
     for i, c in enumerate(cams):
-        o, d = look_at_rays(c, (0.0, 0.0, 0.0), width, height, fov_deg)
+        o, d = look_at_rays(c, (0.0, 0.0, 0.0), width, height, fov_deg, tile)
         out_o[i * m:(i + 1) * m] = o
         out_d[i * m:(i + 1) * m] = d
     return out_o, out_d

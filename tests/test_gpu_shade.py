@@ -119,3 +119,18 @@ def test_mc_config_full_size_sampled():
     it = torch.from_numpy(idx).cuda()
     sub = {k: v[it] for k, v in out.items()}
     print(check(sub, ref, frac=0.95))
+
+
+def test_shading_traversal_modes_identical():
+    sc = synth.object_scene(n=10_000, seed=91)
+    x, n, a, r, wo = synth.gbuffer_points(50, seed=92)
+    env = synth.env_map(seed=93, height=32, width=64)
+    S = make_scene(irgs, sc)
+    p = irgs.TraceParams(k=16, feat_count=3, t_min=1e-3)
+    args = (dev(x), dev(n), dev(a), dev(r), dev(wo), dev(env), 21, 19, 5)
+    o1 = irgs.shade_mc(S, *args, p, want_aux=True)
+    o2 = irgs.shade_mc(S, *args, p.with_(flags=irgs.FLAG_WARP), want_aux=True)
+    # the traces are identical; the two kernel instantiations may round the
+    # estimator arithmetic differently
+    for k in o1:
+        assert torch.allclose(o1[k], o2[k], rtol=1e-6, atol=1e-6), k

@@ -204,12 +204,13 @@ def test_lbvh_structure_invariants():
 
 @pytest.mark.slow
 def test_camera_config_full_size_sampled():
-    """300k-surfel object scene, 100 cameras x 800x800 = 64M rays, k = 16,
-    10 channels: the full batch in the benchmark's launch configuration,
+    """300k-surfel object scene, 100 cameras x 800x800 = 64M rays in 8x4 pixel
+    tiles, k = 16, 10 channels, warp-coherent traversal: the full batch in the
+    benchmark's launch configuration,
     2,048 sampled rays checked against the oracle, invariants on all rays."""
     sc = synth.object_scene(n=300_000, seed=1001)
     cams = synth.hemisphere_cameras(100, seed=1001)
-    ro, rd = synth.camera_batch_rays(cams, 800, 800)
+    ro, rd = synth.camera_batch_rays(cams, 800, 800, tile=(8, 4))
     p = irgs.TraceParams(k=16, feat_count=10)
     S = make_scene(irgs, sc)
     out = irgs.trace_forward(S, dev(ro), dev(rd), p)
@@ -223,3 +224,24 @@ def test_camera_config_full_size_sampled():
     sub = {k: v[torch.from_numpy(idx).cuda()] for k, v in out.items()}
     st = assert_forward_parity(sub, ref, sc.features)
     print(st, "mean hits", float(out["n_hits"].float().mean()))
+
+
+def test_traversal_modes_give_identical_results():
+    """Warp-coherent and per-ray traversal return bit-identical outputs
+    (the k-buffer holds the K nearest hits whatever the visiting order)."""
+    sc = synth.object_scene(n=20_000, seed=15)
+    ro, rd = synth.camera_batch_rays(synth.hemisphere_cameras(2, seed=15), 61, 33)
+    ri, di = synth.random_rays_through_scene(3000, seed=16, box=2.0, radius=4.0)
+    S = make_scene(irgs, sc)
+    for o, d in ((ro, rd), (ri, di)):
+        for k in (8, 16):
+            pw = irgs.TraceParams(k=k, feat_count=10)
+            pt = pw.with_(flags=1)
+            a = irgs.trace_forward(S, dev(o), dev(d), pw, max_hit_ids=16)
+            b = irgs.trace_forward(S, dev(o), dev(d), pt, max_hit_ids=16)
+            for key in a:
+                assert torch.equal(a[key], b[key]), (k, key)
+    with pytest.raises(irgs.IrgsError):
+        irgs.trace_forward(S, dev(ro), dev(rd), irgs.TraceParams(flags=3))
+    with pytest.raises(irgs.IrgsError):
+        irgs.trace_forward(S, dev(ro), dev(rd), irgs.TraceParams(flags=4))
