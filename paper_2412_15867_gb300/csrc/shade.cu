@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(kShadeThreads) k_shade(SceneView S, const floa
                                                          int nd, int ns, uint64_t seed, TraceParams TP,
                                                          float* __restrict__ rgb, float* __restrict__ vis,
                                                          float* __restrict__ ind) {
+    static_assert(kShadeThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
     const int lane = threadIdx.x & 31;
     const int64_t p = blockIdx.x * (int64_t)(kShadeThreads / 32) + (threadIdx.x >> 5);
     if (p >= Pn) return;

@@ -123,50 +123,73 @@ __device__ __forceinline__ Node load_node(const Node* nodes, int i) {
     return nd;
 }
 
-// k-buffer of the nearest hits after `last`, sorted by (key, Morton index).
-template <int K>
+// k-buffer of the K nearest hits after `last`, sorted by (key, Morton index),
+// kept in shared memory: slot j of thread t lives at [j * THREADS + t], so a
+// warp touching the same slot hits consecutive words. Insertion shifts only
+// the entries behind the new one (hits mostly arrive front to back, so the
+// shift is usually short); the last entry is cached in registers for the
+// cheap "does it fit" test and the traversal's far bound.
+template <int K, int THREADS>
 struct KBuffer {
-    uint64_t key[K];
-    int32_t m[K];
-    float a[K];
+    uint64_t* key;
+    int32_t* m;
+    float* a;
     int cnt;
+    uint64_t tail_key;
+    int32_t tail_m;
 
-    __device__ __forceinline__ void clear() {
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            key[j] = ~0ull;
-            m[j] = INT32_MAX;
-            a[j] = 0.f;
-        }
+    __device__ __forceinline__ void bind() {
+        __shared__ uint64_t s_key[K * THREADS];
+        __shared__ int32_t s_m[K * THREADS];
+        __shared__ float s_a[K * THREADS];
+        key = s_key + threadIdx.x;
+        m = s_m + threadIdx.x;
+        a = s_a + threadIdx.x;
         cnt = 0;
     }
+    __device__ __forceinline__ void clear() { cnt = 0; }
     __device__ __forceinline__ bool full() const { return cnt == K; }
-    // insert (k, mm, aa); caller guarantees it sorts before the last entry when full
+    __device__ __forceinline__ uint64_t key_at(int j) const { return key[j * THREADS]; }
+    __device__ __forceinline__ int32_t m_at(int j) const { return m[j * THREADS]; }
+    __device__ __forceinline__ float a_at(int j) const { return a[j * THREADS]; }
+    __device__ __forceinline__ bool fits(uint64_t k, int32_t mm) const {
+        return cnt < K || k < tail_key || (k == tail_key && mm < tail_m);
+    }
+    // insert (k, mm, aa); the caller checked fits()
     __device__ __forceinline__ void insert(uint64_t k, int32_t mm, float aa) {
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            bool lt = k < key[j] || (k == key[j] && mm < m[j]);
-            uint64_t tk = key[j];
-            int32_t tm = m[j];
-            float ta = a[j];
-            key[j] = lt ? k : tk;
-            m[j] = lt ? mm : tm;
-            a[j] = lt ? aa : ta;
-            k = lt ? tk : k;
-            mm = lt ? tm : mm;
-            aa = lt ? ta : aa;
+        int j = (cnt < K ? cnt : K - 1) - 1;
+        while (j >= 0) {
+            const uint64_t kj = key[j * THREADS];
+            const int32_t mj = m[j * THREADS];
+            if (!(k < kj || (k == kj && mm < mj))) break;
+            key[(j + 1) * THREADS] = kj;
+            m[(j + 1) * THREADS] = mj;
+            a[(j + 1) * THREADS] = a[j * THREADS];
+            --j;
         }
-        cnt = cnt < K ? cnt + 1 : K;
+        key[(j + 1) * THREADS] = k;
+        m[(j + 1) * THREADS] = mm;
+        a[(j + 1) * THREADS] = aa;
+        if (cnt < K) ++cnt;
+        if (cnt == K) {
+            tail_key = key[(K - 1) * THREADS];
+            tail_m = m[(K - 1) * THREADS];
+        }
     }
 };
+
+// Threads per block of the tracing kernels for a k-buffer of K entries
+// (the shared-memory k-buffer takes K * THREADS * 16 bytes).
+template <int K>
+__host__ __device__ constexpr int trace_threads() { return K > 16 ? 64 : 128; }
 
 __device__ __forceinline__ float key_depth(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
 
 // Test surfel m against the ray and insert it into the k-buffer if it lies
 // strictly after (last_key, last_m) and before the buffer's last entry.
-template <int K>
+template <class KB>
 __device__ __forceinline__ void leaf_insert(const SceneView& S, const Ray& ray, const TraceParams& P, int32_t m,
-                                            uint64_t last_key, int32_t last_m, KBuffer<K>& kb, float& t_hi) {
+                                            uint64_t last_key, int32_t last_m, KB& kb, float& t_hi) {
     const float4* R = S.rec + (int64_t)m * kRecF4;
     const float4 r0 = ldg4(R), r1 = ldg4(R + 1), r2 = ldg4(R + 2), r3 = ldg4(R + 3);
     float kh, kl, a;
@@ -175,18 +198,17 @@ __device__ __forceinline__ void leaf_insert(const SceneView& S, const Ray& ray, 
     const bool past_min = kh > P.t_min || (kh == P.t_min && kl > 0.f);
     const bool after = past_min && (key > last_key || (key == last_key && m > last_m));
     const bool before = kh < P.t_max || (kh == P.t_max && kl < 0.f);
-    const bool fits = !kb.full() || key < kb.key[K - 1] || (key == kb.key[K - 1] && m < kb.m[K - 1]);
-    if (after && before && fits) {
+    if (after && before && kb.fits(key, m)) {
         kb.insert(key, m, a);
-        if (kb.full()) t_hi = key_depth(kb.key[K - 1]);
+        if (kb.full()) t_hi = key_depth(kb.tail_key);
     }
 }
 
 // One round: gather the K nearest hits strictly after (last_key, last_m).
 // Returns false if the traversal stack overflowed.
-template <int K>
+template <class KB>
 __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray, const TraceParams& P,
-                                              uint64_t last_key, int32_t last_m, KBuffer<K>& kb) {
+                                              uint64_t last_key, int32_t last_m, KB& kb) {
     int stack_n[kStackSize];
     float stack_t[kStackSize];
     int sp = 0;
@@ -210,8 +232,8 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
         float hi_c = t_hi + tslack(t_hi);
         bool h0 = c0 != kNoChild && tn0 <= tf0 && tf0 >= lo_c && tn0 <= hi_c;
         bool h1 = c1 != kNoChild && tn1 <= tf1 && tf1 >= lo_c && tn1 <= hi_c;
-        if (h0 && c0 < 0) leaf_insert<K>(S, ray, P, ~c0, last_key, last_m, kb, t_hi);
-        if (h1 && c1 < 0) leaf_insert<K>(S, ray, P, ~c1, last_key, last_m, kb, t_hi);
+        if (h0 && c0 < 0) leaf_insert(S, ray, P, ~c0, last_key, last_m, kb, t_hi);
+        if (h1 && c1 < 0) leaf_insert(S, ray, P, ~c1, last_key, last_m, kb, t_hi);
         if (c0 < 0) h0 = false;
         if (c1 < 0) h1 = false;
         hi_c = t_hi + tslack(t_hi);
@@ -256,10 +278,9 @@ constexpr unsigned kFullWarp = 0xffffffffu;
 // each lane tests leaves with its own ray and keeps its own k-buffer, so the
 // result per ray equals the per-thread round. All 32 lanes must call this
 // together (inactive lanes pass active = false).
-template <int K>
+template <class KB>
 __device__ __forceinline__ bool collect_round_warp(const SceneView& S, const Ray& ray, const TraceParams& P,
-                                                   uint64_t last_key, int32_t last_m, KBuffer<K>& kb,
-                                                   bool active) {
+                                                   uint64_t last_key, int32_t last_m, KB& kb, bool active) {
     kb.clear();
     const int lane = threadIdx.x & 31;
     const float t_lo = key_depth(last_key);
@@ -282,8 +303,8 @@ __device__ __forceinline__ bool collect_round_warp(const SceneView& S, const Ray
         float hi_c = t_hi + tslack(t_hi);
         const bool h0 = active && c0 != kNoChild && tn0 <= tf0 && tf0 >= lo_c && tn0 <= hi_c;
         const bool h1 = active && c1 != kNoChild && tn1 <= tf1 && tf1 >= lo_c && tn1 <= hi_c;
-        if (h0 && c0 < 0) leaf_insert<K>(S, ray, P, ~c0, last_key, last_m, kb, t_hi);
-        if (h1 && c1 < 0) leaf_insert<K>(S, ray, P, ~c1, last_key, last_m, kb, t_hi);
+        if (h0 && c0 < 0) leaf_insert(S, ray, P, ~c0, last_key, last_m, kb, t_hi);
+        if (h1 && c1 < 0) leaf_insert(S, ray, P, ~c1, last_key, last_m, kb, t_hi);
         hi_c = t_hi + tslack(t_hi);
         const bool v0 = c0 >= 0 && h0 && tn0 <= hi_c;
         const bool v1 = c1 >= 0 && h1 && tn1 <= hi_c;
@@ -342,25 +363,25 @@ __device__ __forceinline__ bool march_forward(const SceneView& S, const Ray& ray
     if (S.n == 0) return ok;
     uint64_t last_key = depth_key(P.t_min, 0.f);
     int32_t last_m = INT32_MAX;
-    KBuffer<K> kb;
+    KBuffer<K, trace_threads<K>()> kb;
+    kb.bind();
     bool done = !live;
     while (WARP ? __any_sync(kFullWarp, !done) : !done) {
         if (WARP)
-            ok &= collect_round_warp<K>(S, ray, P, last_key, last_m, kb, !done);
+            ok &= collect_round_warp(S, ray, P, last_key, last_m, kb, !done);
         else
-            ok &= collect_round<K>(S, ray, P, last_key, last_m, kb);
+            ok &= collect_round(S, ray, P, last_key, last_m, kb);
         if (done) continue;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            if (j < kb.cnt && !done) {
-                const float a = kb.a[j];
-                const int32_t m = kb.m[j];
+        for (int j = 0; j < kb.cnt && !done; ++j) {
+            {
+                const float a = kb.a_at(j);
+                const int32_t m = kb.m_at(j);
                 const float w = __fmul_rn(st.T, a);
                 const float* f = S.feat + (int64_t)m * S.F + P.off;
 #pragma unroll
                 for (int c = 0; c < FB; ++c)
                     if (c < P.fc) st.C[c] = __fmaf_rn(w, __ldg(f + c), st.C[c]);
-                st.D = __fmaf_rn(w, key_depth(kb.key[j]), st.D);
+                st.D = __fmaf_rn(w, key_depth(kb.key_at(j)), st.D);
                 st.T = __fmul_rn(st.T, __fsub_rn(1.0f, a));
                 if (ids != nullptr && st.nh < max_ids)
                     ids[st.nh] = __float_as_int(__ldg(&S.rec[(int64_t)m * kRecF4 + 2].w));
@@ -372,8 +393,8 @@ __device__ __forceinline__ bool march_forward(const SceneView& S, const Ray& ray
             if (kb.cnt < K) {
                 done = true;
             } else {
-                last_key = kb.key[K - 1];
-                last_m = kb.m[K - 1];
+                last_key = kb.tail_key;
+                last_m = kb.tail_m;
             }
         }
     }

@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
     const float* __restrict__ g_opacv, float* __restrict__ g_means, float* __restrict__ g_quats,
     float* __restrict__ g_scales, float* __restrict__ g_opac, float* __restrict__ g_feat) {
     constexpr int N = GradVals<FB>::N;
+    static_assert(kBwdThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
     __shared__ float rows_all[kBwdThreads * (N + 1)];
     float* rows = rows_all + (threadIdx.x & ~31) * (N + 1);
     const int64_t r = blockIdx.x * (int64_t)kBwdThreads + threadIdx.x;
@@ -108,20 +109,20 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
     int nh = 0;
     uint64_t last_key = depth_key(P.t_min, 0.f);
     int32_t last_m = INT32_MAX;
-    KBuffer<K> kb;
+    KBuffer<K, kBwdThreads> kb;
+    kb.bind();
     bool ok = true, done = !live;
     while (WARP ? __any_sync(kFullWarp, !done) : !done) {
         if (WARP)
-            ok &= collect_round_warp<K>(S, ray, P, last_key, last_m, kb, !done);
+            ok &= collect_round_warp(S, ray, P, last_key, last_m, kb, !done);
         else
-            ok &= collect_round<K>(S, ray, P, last_key, last_m, kb);
+            ok &= collect_round(S, ray, P, last_key, last_m, kb);
         if (done) continue;
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            if (j < kb.cnt && nh < nh_total) {
-                const float a = kb.a[j];
-                const int32_t m = kb.m[j];
-                const float tau = key_depth(kb.key[j]);
+        for (int j = 0; j < kb.cnt && nh < nh_total; ++j) {
+            {
+                const float a = kb.a_at(j);
+                const int32_t m = kb.m_at(j);
+                const float tau = key_depth(kb.key_at(j));
                 const float w = __fmul_rn(T, a);
                 const float* f = S.feat + (int64_t)m * S.F + P.off;
                 float fv[FB];
@@ -190,8 +191,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
         if (nh >= nh_total || kb.cnt < K) {
             done = true;
         } else {
-            last_key = kb.key[K - 1];
-            last_m = kb.m[K - 1];
+            last_key = kb.tail_key;
+            last_m = kb.tail_m;
         }
     }
     if (live && !ok) atomicOr(S.status, kErrStackOverflow);

@@ -7,16 +7,15 @@
 namespace irgs {
 namespace {
 
-constexpr int kFwdThreads = 128;
 
 template <int K, int FB, bool WARP>
-__global__ void __launch_bounds__(kFwdThreads) k_trace_forward(SceneView S, const float* __restrict__ ro,
+__global__ void __launch_bounds__(trace_threads<K>()) k_trace_forward(SceneView S, const float* __restrict__ ro,
                                                                const float* __restrict__ rd, int64_t R,
                                                                TraceParams P, float* __restrict__ feat,
                                                                float* __restrict__ depth, float* __restrict__ opac,
                                                                int32_t* __restrict__ nhits, int32_t* __restrict__ ids,
                                                                int max_ids) {
-    const int64_t r = blockIdx.x * (int64_t)kFwdThreads + threadIdx.x;
+    const int64_t r = blockIdx.x * (int64_t)trace_threads<K>() + threadIdx.x;
     const bool live = r < R;
     if (!WARP && !live) return;
     const int64_t q = live ? r : 0;   // lanes without a ray follow the warp with a dummy ray
@@ -43,8 +42,9 @@ template <int K, int FB, bool WARP>
 cudaError_t launch(const SceneView& S, const float* ro, const float* rd, int64_t R, const TraceParams& P,
                    float* feat, float* depth, float* opac, int32_t* nhits, int32_t* ids, int max_ids,
                    cudaStream_t st) {
-    const int64_t blocks = (R + kFwdThreads - 1) / kFwdThreads;
-    k_trace_forward<K, FB, WARP><<<(unsigned)blocks, kFwdThreads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac,
+    constexpr int threads = trace_threads<K>();
+    const int64_t blocks = (R + threads - 1) / threads;
+    k_trace_forward<K, FB, WARP><<<(unsigned)blocks, threads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac,
                                                                            nhits, ids, max_ids);
     count_launches(1);
     return cudaGetLastError();
