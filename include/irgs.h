@@ -227,6 +227,103 @@ irgs_status irgs_shade_mc(irgs_scene scene, const float* x, const float* n, cons
                           uint64_t seed, const irgs_trace_params* params, float* out_rgb,
                           float* out_vis, float* out_ind, void* stream);
 
+/* ---------------------------------------------------------------------- */
+/* Serving: several resident scenes, many requests per persistent launch. */
+/* ---------------------------------------------------------------------- */
+
+/* Pinhole camera. Pixel p of a request is numbered tile by tile: tiles of
+ * tile_w x tile_h pixels in row-major tile order, row-major inside a tile
+ * (tile_w = tile_h = 1 gives plain row-major order); width and height must
+ * be multiples of the tile. The ray of pixel (px, py) starts at `origin`
+ * and points along normalize(forward + x right + y up) with
+ * x = ((px + 0.5)/width * 2 - 1) tan_half_fov width/height and
+ * y = (1 - (py + 0.5)/height * 2) tan_half_fov. */
+typedef struct {
+    float origin[3];
+    float forward[3];       /* unit view direction          */
+    float right[3];         /* unit image x axis            */
+    float up[3];            /* unit image y axis (up)       */
+    float tan_half_fov;     /* tan(vertical field of view/2) */
+    int32_t width, height;
+    int32_t tile_w, tile_h;
+} irgs_camera;
+
+typedef enum { IRGS_JOB_RENDER = 0, IRGS_JOB_RELIGHT = 1 } irgs_job_kind;
+
+/* One request of a serving step. Device pointers; the caller owns them.
+ *   render : feat [P, render.feat_count], depth [P], opacity [P] (Eq. 8).
+ *   relight: gbuffer [P, 16] (written by G-buffer tiles, read by shade
+ *            tiles: x(3) n(3) albedo(3) roughness w_o(3) valid opacity -),
+ *            rgb [P, 3] (Eq. 15 with n_diffuse cosine + n_spec GGX samples
+ *            per pixel against env [env_h, env_w, 3], random stream `seed`,
+ *            stream point = pixel index p; background pixels get 0).
+ * P = width x height of the camera. */
+typedef struct {
+    int32_t kind;           /* irgs_job_kind (informational)          */
+    int32_t scene;          /* index into the server's scenes         */
+    irgs_camera cam;
+    int32_t n_diffuse, n_spec;
+    uint64_t seed;
+    const float* env;
+    int32_t env_h, env_w;
+    float* feat;
+    float* depth;
+    float* opacity;
+    float* gbuffer;
+    float* rgb;
+} irgs_job;
+
+typedef enum { IRGS_TILE_RENDER = 0, IRGS_TILE_GBUFFER = 1, IRGS_TILE_SHADE = 2 } irgs_tile_kind;
+
+/* A unit of work: pixels (render / G-buffer) or G-buffer points (shade)
+ * [first, first + count) of job `job`. A shade tile must run in a later
+ * step than the G-buffer tiles of the same pixels. */
+typedef struct {
+    int32_t kind;
+    int32_t job;
+    int32_t first;
+    int32_t count;
+} irgs_tile;
+
+typedef struct irgs_server_s* irgs_server;
+
+/*
+ * Create a server over resident scenes (the scenes must outlive it and must
+ * not be rebuilt while a step runs). `render` traces camera rays (k = 16,
+ * feat_count <= 10); G-buffer tiles trace the 7 material channels starting
+ * at `material_offset` (albedo 3, roughness 1, normal 3) with the render
+ * parameters otherwise; `shade` traces the secondary rays (k = 16,
+ * feat_count = 3 radiance channels, t_min > 0). Allocates pinned staging
+ * for max_jobs jobs and max_tiles tiles and its device copy.
+ */
+irgs_status irgs_server_create(const irgs_scene* scenes, int32_t n_scenes, int32_t max_jobs, int32_t max_tiles,
+                               int32_t material_offset, const irgs_trace_params* render,
+                               const irgs_trace_params* shade, irgs_server* out);
+
+/* Host (pinned) tables the caller fills before each step: jobs[max_jobs],
+ * tiles[max_tiles]. They may be rewritten only after the previous step's
+ * work has completed on its stream. */
+irgs_status irgs_server_staging(irgs_server server, irgs_job** jobs, irgs_tile** tiles);
+
+/*
+ * Run one step: validate the first n_jobs / n_tiles table entries, copy the
+ * tables to the device and launch one persistent kernel whose blocks pull
+ * tiles until none is left. With use_graph != 0 the copy, counter reset and
+ * launch are captured into a CUDA graph on the first such call and replayed
+ * afterwards. Ordered after prior work on `stream`; later work on `stream`
+ * waits for the step. Returns once the work is enqueued.
+ */
+irgs_status irgs_server_step(irgs_server server, int32_t n_jobs, int32_t n_tiles, int32_t use_graph,
+                             void* stream);
+
+/* Free a server (synchronises its stream first). NULL is ignored. */
+irgs_status irgs_server_destroy(irgs_server server);
+
+/* Rays of pixels [first, first + count) of a camera, written to device
+ * arrays ray_o / ray_d [count, 3] (the same rays a server step traces). */
+irgs_status irgs_camera_rays(const irgs_camera* cam, int64_t first, int64_t count, float* ray_o, float* ray_d,
+                             void* stream);
+
 /*
  * Allocation-free LBVH build (the paper has no counterpart; this is a
  * deployment variant of irgs_build_scene).

@@ -60,7 +60,7 @@ _SIGS = {
 
 def declared_symbols() -> list[str]:
     """Function names declared in include/irgs.h."""
-    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", " ", open(HEADER).read(), flags=re.S)
     return sorted(set(re.findall(r"\b(irgs_[a-z_0-9]+)\s*\(", text)))
 
 

@@ -1,0 +1,355 @@
+// Serving: one persistent launch per scheduling step processes tiles of many
+// requests over several resident scenes. Blocks pull tiles from the step's
+// tile table with an atomic counter until it is exhausted; a tile is up to a
+// few thousand camera rays (render / G-buffer) or G-buffer points to shade.
+// The step (staging copy, counter reset, kernel) can be captured once into a
+// CUDA graph and replayed with new table contents.
+//
+// Work per tile kind (IRGS Eq. 8 for the traces, Eq. 13-15 for shading):
+//   render  : camera rays -> Trace -> feat / depth / opacity per pixel;
+//   gbuffer : camera rays -> Trace of the material channels (albedo,
+//             roughness, normal) -> per-pixel G-buffer normalised by the
+//             opacity (Eq. 9): x = o + (D/O) d, n, a, r, w_o = -d;
+//   shade   : G-buffer points -> Monte Carlo rendering equation.
+// Each result depends only on its own request (camera, seed, pixel index),
+// never on what else shares the launch.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/irgs.h"
+#include "scene.h"
+#include "shade.cuh"
+#include "trace.cuh"
+
+struct irgs_server_s {
+    int device = 0;
+    int n_scenes = 0;
+    int max_jobs = 0, max_tiles = 0;
+    size_t stage_bytes = 0;
+    unsigned char* host_stage = nullptr;   // pinned: [header 16 B][jobs][tiles]
+    unsigned char* dev_stage = nullptr;
+    irgs::SceneView* dev_scenes = nullptr;
+    int* dev_next = nullptr;
+    int grid = 0;
+    irgs::TraceParams render{}, gbuf{}, shade{};
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace irgs {
+namespace {
+
+constexpr int kServeThreads = 128;
+constexpr int kServeK = 16;
+constexpr size_t kHeaderBytes = 16;
+
+struct ServeArgs {
+    const SceneView* scenes;
+    const int32_t* header;   // [0] jobs, [1] tiles
+    const irgs_job* jobs;
+    const irgs_tile* tiles;
+    int* next_tile;
+    TraceParams render, gbuf, shade;
+};
+
+// Pixel p of a camera (tile by tile when tile_w x tile_h > 1) -> ray.
+__device__ __forceinline__ void camera_ray(const irgs_camera& c, int64_t p, f3& o, f3& d) {
+    const int tw = c.tile_w, th = c.tile_h;
+    const int64_t per = (int64_t)tw * th;
+    const int64_t tile = p / per, within = p - tile * per;
+    const int64_t tiles_x = c.width / tw;
+    const int64_t ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const float px = (float)(tx * tw + within % tw), py = (float)(ty * th + within / tw);
+    const float aspect = (float)c.width / (float)c.height;
+    const float xn = ((px + 0.5f) / (float)c.width * 2.f - 1.f) * c.tan_half_fov * aspect;
+    const float yn = (1.f - (py + 0.5f) / (float)c.height * 2.f) * c.tan_half_fov;
+    const f3 f = mk3(c.forward[0], c.forward[1], c.forward[2]);
+    const f3 r = mk3(c.right[0], c.right[1], c.right[2]);
+    const f3 u = mk3(c.up[0], c.up[1], c.up[2]);
+    d = normalize3(add3(f, add3(mul3(r, xn), mul3(u, yn))));
+    o = mk3(c.origin[0], c.origin[1], c.origin[2]);
+}
+
+__global__ void k_camera_rays(irgs_camera c, int64_t first, int64_t count, float* __restrict__ ro,
+                              float* __restrict__ rd) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    f3 o, d;
+    camera_ray(c, first + i, o, d);
+    ro[3 * i] = o.x; ro[3 * i + 1] = o.y; ro[3 * i + 2] = o.z;
+    rd[3 * i] = d.x; rd[3 * i + 1] = d.y; rd[3 * i + 2] = d.z;
+}
+
+__global__ void __launch_bounds__(kServeThreads) k_serve(ServeArgs A) {
+    static_assert(kServeThreads == trace_threads<kServeK>(), "k-buffer slots are laid out per block thread");
+    __shared__ int s_tile;
+    const int n_tiles = A.header[1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(A.next_tile, 1);
+        __syncthreads();
+        const int t = s_tile;
+        __syncthreads();
+        if (t >= n_tiles) return;
+        const irgs_tile tile = A.tiles[t];
+        const irgs_job& job = A.jobs[tile.job];
+        const SceneView S = A.scenes[job.scene];
+        if (tile.kind == IRGS_TILE_RENDER || tile.kind == IRGS_TILE_GBUFFER) {
+            const bool render = tile.kind == IRGS_TILE_RENDER;
+            const TraceParams& P = render ? A.render : A.gbuf;
+            for (int i0 = 0; i0 < tile.count; i0 += kServeThreads) {
+                const int i = i0 + threadIdx.x;
+                const bool live = i < tile.count;
+                const int64_t p = (int64_t)tile.first + (live ? i : 0);
+                f3 o, d;
+                camera_ray(job.cam, p, o, d);
+                const Ray ray = make_ray(o, d);
+                MarchState<kServeK, 10> st;
+                const bool ok = march_forward<kServeK, 10, true>(S, ray, P, st, nullptr, 0, live);
+                if (!live) continue;
+                if (!ok) atomicOr(S.status, kErrStackOverflow);
+                if (render) {
+#pragma unroll
+                    for (int c = 0; c < 10; ++c)
+                        if (c < P.fc) job.feat[p * P.fc + c] = st.C[c];
+                    job.depth[p] = st.D;
+                    job.opacity[p] = 1.f - st.T;
+                } else {
+                    // Eq. 9 normalisation by the accumulated opacity
+                    const float O = 1.f - st.T;
+                    float* g = job.gbuffer + p * 16;
+                    const bool valid = O > 0.5f;
+                    const float inv = valid ? 1.f / O : 0.f;
+                    const f3 x = add3(o, mul3(d, st.D * inv));
+                    f3 nn = mk3(st.C[4], st.C[5], st.C[6]);
+                    const float nl = sqrtf(dot3(nn, nn));
+                    nn = nl > 0.f ? mul3(nn, 1.f / nl) : mk3(0.f, 0.f, 1.f);
+                    g[0] = x.x; g[1] = x.y; g[2] = x.z;
+                    g[3] = nn.x; g[4] = nn.y; g[5] = nn.z;
+                    g[6] = st.C[0] * inv; g[7] = st.C[1] * inv; g[8] = st.C[2] * inv;
+                    g[9] = st.C[3] * inv;
+                    g[10] = -d.x; g[11] = -d.y; g[12] = -d.z;
+                    g[13] = valid ? 1.f : 0.f;
+                    g[14] = O; g[15] = 0.f;
+                }
+            }
+        } else {
+            // one warp per G-buffer point
+            for (int j = warp; j < tile.count; j += kServeThreads / 32) {
+                const int64_t p = (int64_t)tile.first + j;
+                const float* g = job.gbuffer + p * 16;
+                float out[3] = {0.f, 0.f, 0.f};
+                if (g[13] > 0.5f) {
+                    ShadeSums sums;
+                    shade_point_warp<kServeK, false>(S, mk3(g[0], g[1], g[2]), mk3(g[3], g[4], g[5]),
+                                                     mk3(g[10], g[11], g[12]), mk3(g[6], g[7], g[8]), g[9],
+                                                     (uint64_t)p, job.n_diffuse, job.n_spec, job.seed, job.env,
+                                                     job.env_h, job.env_w, A.shade, sums);
+                    out[0] = sums.rgb[0]; out[1] = sums.rgb[1]; out[2] = sums.rgb[2];
+                }
+                if (lane == 0)
+                    for (int c = 0; c < 3; ++c) job.rgb[3 * p + c] = out[c];
+            }
+        }
+    }
+}
+
+void server_free(irgs_server s) {
+    if (!s) return;
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->ev_in) cudaEventDestroy(s->ev_in);
+    if (s->ev_out) cudaEventDestroy(s->ev_out);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->host_stage) cudaFreeHost(s->host_stage);
+    if (s->dev_stage) cudaFree(s->dev_stage);
+    if (s->dev_scenes) cudaFree(s->dev_scenes);
+    if (s->dev_next) cudaFree(s->dev_next);
+    delete s;
+}
+
+ServeArgs args_of(irgs_server s) {
+    ServeArgs A;
+    A.scenes = s->dev_scenes;
+    A.header = reinterpret_cast<const int32_t*>(s->dev_stage);
+    A.jobs = reinterpret_cast<const irgs_job*>(s->dev_stage + kHeaderBytes);
+    A.tiles = reinterpret_cast<const irgs_tile*>(s->dev_stage + kHeaderBytes + sizeof(irgs_job) * s->max_jobs);
+    A.next_tile = s->dev_next;
+    A.render = s->render;
+    A.gbuf = s->gbuf;
+    A.shade = s->shade;
+    return A;
+}
+
+// The step's device work on the server stream: staging copy, counter reset,
+// persistent kernel.
+cudaError_t enqueue_step(irgs_server s) {
+    cudaError_t e = cudaMemcpyAsync(s->dev_stage, s->host_stage, s->stage_bytes, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->dev_next, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess) {
+        k_serve<<<s->grid, kServeThreads, 0, s->stream>>>(args_of(s));
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace
+}  // namespace irgs
+
+extern "C" {
+
+irgs_status irgs_server_create(const irgs_scene* scenes, int32_t n_scenes, int32_t max_jobs, int32_t max_tiles,
+                               int32_t material_offset, const irgs_trace_params* render,
+                               const irgs_trace_params* shade, irgs_server* out) {
+    using namespace irgs;
+    if (!scenes || n_scenes <= 0 || max_jobs <= 0 || max_tiles <= 0 || !render || !shade || !out)
+        return IRGS_ERR_INVALID_ARG;
+    if (render->k != kServeK || shade->k != kServeK) return IRGS_ERR_UNSUPPORTED;
+    if (render->feat_count < 0 || render->feat_count > 10 || shade->feat_count != 3 || !(shade->t_min > 0.f))
+        return IRGS_ERR_INVALID_ARG;
+    for (int i = 0; i < n_scenes; ++i) {
+        if (!scenes[i]) return IRGS_ERR_INVALID_ARG;
+        const irgs_scene sc = scenes[i];
+        if (render->feat_offset + render->feat_count > sc->F || material_offset < 0 || material_offset + 7 > sc->F ||
+            shade->feat_offset + 3 > sc->F || render->alpha_min < sc->alpha_min || shade->alpha_min < sc->alpha_min)
+            return IRGS_ERR_INVALID_ARG;
+        if (sc->device != scenes[0]->device) return IRGS_ERR_INVALID_ARG;
+    }
+    irgs_server s = new (std::nothrow) irgs_server_s();
+    if (!s) return IRGS_ERR_OOM;
+    s->device = scenes[0]->device;
+    if (cudaSetDevice(s->device) != cudaSuccess) {
+        delete s;
+        return IRGS_ERR_CUDA;
+    }
+    s->n_scenes = n_scenes;
+    s->max_jobs = max_jobs;
+    s->max_tiles = max_tiles;
+    s->stage_bytes = kHeaderBytes + sizeof(irgs_job) * (size_t)max_jobs + sizeof(irgs_tile) * (size_t)max_tiles;
+    s->render = to_params(*render);
+    s->shade = to_params(*shade);
+    s->gbuf = s->render;
+    s->gbuf.off = material_offset;
+    s->gbuf.fc = 7;
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&s->host_stage), s->stage_bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->dev_stage), s->stage_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->dev_scenes), sizeof(SceneView) * n_scenes);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->dev_next), sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        memset(s->host_stage, 0, s->stage_bytes);
+        SceneView views[64];
+        int done = 0;
+        while (e == cudaSuccess && done < n_scenes) {
+            const int m = n_scenes - done < 64 ? n_scenes - done : 64;
+            for (int i = 0; i < m; ++i) views[i] = scenes[done + i]->view();
+            e = cudaMemcpy(s->dev_scenes + done, views, sizeof(SceneView) * m, cudaMemcpyHostToDevice);
+            done += m;
+        }
+    }
+    int per_sm = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, kServeThreads, 0);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (e != cudaSuccess || per_sm <= 0) {
+        cudaGetLastError();
+        server_free(s);
+        return e == cudaErrorMemoryAllocation ? IRGS_ERR_OOM : IRGS_ERR_CUDA;
+    }
+    s->grid = per_sm * sms;
+    *out = s;
+    return IRGS_OK;
+}
+
+irgs_status irgs_server_staging(irgs_server s, irgs_job** jobs, irgs_tile** tiles) {
+    if (!s) return IRGS_ERR_INVALID_ARG;
+    if (jobs) *jobs = reinterpret_cast<irgs_job*>(s->host_stage + irgs::kHeaderBytes);
+    if (tiles) *tiles = reinterpret_cast<irgs_tile*>(s->host_stage + irgs::kHeaderBytes + sizeof(irgs_job) * s->max_jobs);
+    return IRGS_OK;
+}
+
+irgs_status irgs_server_step(irgs_server s, int32_t n_jobs, int32_t n_tiles, int32_t use_graph, void* stream) {
+    using namespace irgs;
+    if (!s || n_jobs < 0 || n_jobs > s->max_jobs || n_tiles < 0 || n_tiles > s->max_tiles) return IRGS_ERR_INVALID_ARG;
+    const irgs_job* jobs = reinterpret_cast<const irgs_job*>(s->host_stage + kHeaderBytes);
+    const irgs_tile* tiles = reinterpret_cast<const irgs_tile*>(s->host_stage + kHeaderBytes + sizeof(irgs_job) * s->max_jobs);
+    for (int t = 0; t < n_tiles; ++t) {   // validate the tables before any device work
+        const irgs_tile& tl = tiles[t];
+        if (tl.job < 0 || tl.job >= n_jobs || tl.count < 0 || tl.first < 0 || tl.kind < 0 || tl.kind > 2)
+            return IRGS_ERR_INVALID_ARG;
+        const irgs_job& jb = jobs[tl.job];
+        if (jb.scene < 0 || jb.scene >= s->n_scenes) return IRGS_ERR_INVALID_ARG;
+        const int64_t P = (int64_t)jb.cam.width * jb.cam.height;
+        if (jb.cam.tile_w <= 0 || jb.cam.tile_h <= 0 || jb.cam.width % jb.cam.tile_w || jb.cam.height % jb.cam.tile_h ||
+            (int64_t)tl.first + tl.count > P)
+            return IRGS_ERR_INVALID_ARG;
+        if (tl.kind == IRGS_TILE_RENDER && (!jb.depth || !jb.opacity || (s->render.fc > 0 && !jb.feat)))
+            return IRGS_ERR_INVALID_ARG;
+        if (tl.kind == IRGS_TILE_GBUFFER && !jb.gbuffer) return IRGS_ERR_INVALID_ARG;
+        if (tl.kind == IRGS_TILE_SHADE &&
+            (!jb.gbuffer || !jb.rgb || !jb.env || jb.env_h <= 0 || jb.env_w <= 0 || jb.n_diffuse < 0 || jb.n_spec < 0 ||
+             jb.n_diffuse + jb.n_spec <= 0))
+            return IRGS_ERR_INVALID_ARG;
+    }
+    int32_t* hdr = reinterpret_cast<int32_t*>(s->host_stage);
+    hdr[0] = n_jobs;
+    hdr[1] = n_tiles;
+    if (cudaSetDevice(s->device) != cudaSuccess) return IRGS_ERR_CUDA;
+    cudaStream_t caller = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaEventRecord(s->ev_in, caller);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_in, 0);
+    if (e == cudaSuccess && use_graph && !s->graph) {
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = enqueue_step(s);
+            e = cudaStreamEndCapture(s->stream, &g);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&s->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+    }
+    if (e == cudaSuccess) {
+        if (use_graph) {
+            e = cudaGraphLaunch(s->graph, s->stream);
+        } else {
+            e = enqueue_step(s);
+        }
+    }
+    count_launches(1);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_out, s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, s->ev_out, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return IRGS_ERR_CUDA;
+    }
+    return IRGS_OK;
+}
+
+irgs_status irgs_server_destroy(irgs_server s) {
+    if (!s) return IRGS_OK;
+    cudaSetDevice(s->device);
+    cudaStreamSynchronize(s->stream);
+    irgs::server_free(s);
+    return IRGS_OK;
+}
+
+irgs_status irgs_camera_rays(const irgs_camera* cam, int64_t first, int64_t count, float* ray_o, float* ray_d,
+                             void* stream) {
+    if (!cam || first < 0 || count < 0 || (count > 0 && (!ray_o || !ray_d))) return IRGS_ERR_INVALID_ARG;
+    if (cam->width <= 0 || cam->height <= 0 || cam->tile_w <= 0 || cam->tile_h <= 0 ||
+        cam->width % cam->tile_w || cam->height % cam->tile_h || first + count > (int64_t)cam->width * cam->height)
+        return IRGS_ERR_INVALID_ARG;
+    if (count == 0) return IRGS_OK;
+    const int T = 256;
+    irgs::k_camera_rays<<<(unsigned)((count + T - 1) / T), T, 0, static_cast<cudaStream_t>(stream)>>>(*cam, first, count,
+                                                                                                     ray_o, ray_d);
+    irgs::count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+}
+
+}  // extern "C"
