@@ -70,6 +70,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mc", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
+    ap.add_argument("--serve-seconds", type=float, default=8.0)
+    ap.add_argument("--serve-warmup", type=float, default=2.0)
     ap.add_argument("--cpu-rays", type=int, default=4096, help="oracle sample for cpu_baseline")
     ap.add_argument("--ref-rays", type=int, default=1024, help="oracle rays per reference step")
     return ap.parse_args()
@@ -329,6 +333,13 @@ def run_ours(args):
             raise RuntimeError("device error in the MC leg")
         S2.close()
 
+    # ---- serving mix (continuous batching vs one request at a time)
+    serving = None
+    if not args.no_serve and rank == 0:
+        del out, grads, ro, rd, gf, gd, go
+        torch.cuda.empty_cache()
+        serving = serve_leg(args, dev)
+
     # ---- oracle on the host cores, bounded sample of the same workload
     cpu = None
     if not args.no_cpu and rank == 0:
@@ -350,11 +361,82 @@ def run_ours(args):
             "build_ms": build_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
             "mean_hits_per_ray": float(nh.float().mean()),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk, "mc": mc,
+            "clocks": clk, "mc": mc, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def serve_leg(args, dev):
+    """Serving mix: 4 resident scenes (100k, 300k, 1M, 2M surfels, object scene
+    with median scale 0.01 sqrt(300k/N)); 50% render (camera rays, 10
+    channels) / 50% relight (G-buffer + Monte Carlo shading, spp log-uniform
+    in [1, 128]) requests at resolutions {128, 256, 512, 1024}^2 from random
+    hemisphere cameras. Saturated throughput first (all requests queued at
+    once), then a Poisson stream at 0.7x that rate served with continuous
+    batching and, separately, one request at a time."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2412_15867_gb300 as irgs
+    from paper_2412_15867_gb300 import serve
+
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    sizes = [100_000, 300_000, 1_000_000, 2_000_000]
+    scenes = [irgs.Scene(*(T(a) for a in synth.object_scene(n, seed=1010 + i).arrays())) for i, n in enumerate(sizes)]
+    env = T(synth.env_map(seed=1003))
+    res = [128, 256, 512, 1024]
+
+    def maker(seed):
+        rng = np.random.default_rng(seed)
+
+        def make(i):
+            scene = int(rng.integers(0, 4))
+            r = res[int(rng.integers(0, 4))]
+            z = rng.uniform(np.sin(np.radians(5)), 1.0)
+            ph = rng.uniform(0, 2 * np.pi)
+            eye = (4 * np.sqrt(1 - z * z) * np.cos(ph), 4 * np.sqrt(1 - z * z) * np.sin(ph), 4 * z)
+            if rng.uniform() < 0.5:
+                return serve.RenderRequest(scene, eye, r, r)
+            spp = int(np.clip(np.round(np.exp(rng.uniform(0, np.log(128)))), 1, 128))
+            return serve.RelightRequest(scene, eye, r, r, spp=spp, env=env, seed=int(rng.integers(1 << 62)))
+        return make
+
+    budget = 24 << 30
+    # saturated: a burst of requests served with continuous batching
+    srv = serve.Server(scenes, hbm_budget=budget, max_jobs=64, max_tiles=8192)
+    mk = maker(11)
+    n_burst = 48
+    for i in range(4):                                   # warm-up (graph capture, caches)
+        srv.submit(mk(i))
+    srv.run_until_idle()
+    rays0 = srv.rays_total
+    t0 = time.perf_counter()
+    burst = [srv.submit(mk(100 + i), arrival=t0) for i in range(n_burst)]
+    srv.run_until_idle()
+    sat_wall = time.perf_counter() - t0
+    sat_rate = n_burst / sat_wall
+    sat_mrays = (srv.rays_total - rays0) / sat_wall / 1e6
+    rate = 0.7 * sat_rate
+    out = {"scenes_surfels": sizes, "mix": "50% render (10 ch) / 50% relight (spp log-uniform 1-128), "
+           "res {128,256,512,1024}^2, random hemisphere cameras, Poisson arrivals",
+           "saturated": {"requests_per_s": sat_rate, "mrays_s": sat_mrays, "requests": n_burst},
+           "rate_requests_per_s": rate}
+    for name, batching in (("batched", True), ("one_at_a_time", False)):
+        srv2 = serve.Server(scenes, hbm_budget=budget, max_jobs=64, max_tiles=8192, batching=batching)
+        hs, wall, rays = serve.run_poisson(srv2, maker(23), rate, args.serve_seconds, args.serve_warmup, seed=5)
+        st = serve.latency_stats(hs)
+        st.update({"mrays_s": rays / wall / 1e6, "requests_per_s": len(hs) / wall, "steps": srv2.steps})
+        out[name] = st
+        srv2.close()
+    status = sum(S.status() for S in scenes)
+    if status:
+        raise RuntimeError("device error in the serving leg")
+    srv.close()
+    for S in scenes:
+        S.close()
+    return out
 
 
 def cpu_baseline(sc, ro, rd, gf, gd, go, n_rays):
@@ -422,6 +504,10 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.serve_only:
+        import torch
+        print(json.dumps({"serving": serve_leg(args, torch.device("cuda", 0))}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

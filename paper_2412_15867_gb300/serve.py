@@ -149,7 +149,7 @@ class Server:
     """Continuous-batching scheduler over `scenes` (resident Scene objects)."""
 
     def __init__(self, scenes, hbm_budget: int = 8 << 30, max_jobs: int = 64, max_tiles: int = 8192,
-                 tile_px: int = 4096, step_rays: int = 16 << 20, use_graph: bool = True,
+                 tile_px: int = 4096, step_rays: int = 8 << 20, use_graph: bool = True,
                  material_offset: int = 3, render: TraceParams | None = None,
                  shade: TraceParams | None = None, batching: bool = True):
         self.scenes = list(scenes)
@@ -209,6 +209,16 @@ class Server:
             self.used += h.bytes
             self.active.append(h)
 
+    @staticmethod
+    def _remaining_rays(h: Handle) -> int:
+        req = h.request
+        P = req.pixels()
+        if isinstance(req, RenderRequest):
+            return P - h.next_px
+        if h.phase == 0:
+            return (P - h.next_px) + P * max(1, req.spp)
+        return (P - h.next_px) * max(1, req.spp)
+
     def _job_struct(self, h: Handle, j: Job):
         req = h.request
         j.kind = JOB_RENDER if isinstance(req, RenderRequest) else JOB_RELIGHT
@@ -229,9 +239,10 @@ class Server:
 
     # ---- one scheduling step
     def step(self) -> bool:
-        """Admit what fits, run one persistent launch over the tiles of all
-        active requests (oldest first, up to step_rays), retire finished
-        requests. Returns False when there was nothing to do."""
+        """Admit what fits, run one persistent launch over the tiles of the
+        active requests (shortest remaining work first, up to step_rays
+        rays), retire finished requests. Returns False if there was nothing
+        to do."""
         self._admit()
         if not self.active:
             return False
@@ -239,7 +250,9 @@ class Server:
         n_tiles = 0
         budget = self.step_rays
         plan = []
-        for h in self.active:
+        # shortest remaining work first: small requests finish in the step
+        # they join, large ones take what is left of the ray budget
+        for h in sorted(self.active, key=self._remaining_rays):
             req = h.request
             P = req.pixels()
             if h.phase < 0:
