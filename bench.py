@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--serve-warmup", type=float, default=2.0)
-    ap.add_argument("--cpu-rays", type=int, default=4096, help="oracle sample for cpu_baseline")
+    ap.add_argument("--cpu-rays", type=int, default=20480, help="oracle sample for cpu_baseline")
     ap.add_argument("--ref-rays", type=int, default=1024, help="oracle rays per reference step")
     return ap.parse_args()
 
