@@ -157,6 +157,7 @@ def run_ours(args):
     import synth
     import paper_2412_15867_gb300 as irgs
     from paper_2412_15867_gb300 import _lib
+    from paper_2412_15867_gb300.dist import allreduce_grads
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -202,8 +203,7 @@ def run_ours(args):
         if evs:
             evs[3].record(stream)
         if world > 1:
-            for g in grads.values():
-                dist.all_reduce(g)
+            allreduce_grads(grads)
 
     for _ in range(args.warmup):
         step()
