@@ -153,6 +153,16 @@ irgs_status irgs_scene_export(irgs_scene scene, int32_t* perm, uint32_t* keys, f
                               float* leaf_boxes);
 
 /*
+ * Copy the 4-wide hierarchy the tracing kernels walk (root = node 0) to a
+ * HOST buffer (synchronous). *n_wide receives the node count; nodes [cap,
+ * 32] float32 receives min(cap, n_wide) nodes laid out as six float4 rows
+ * lo.x lo.y lo.z hi.x hi.y hi.z (component k = child k), one int4 row of
+ * child ids (>= 0 wide node, < 0 leaf ~m, INT32_MIN none) and one row whose
+ * first int is the child count. Either pointer may be NULL.
+ */
+irgs_status irgs_scene_export_wide(irgs_scene scene, float* nodes, int64_t cap, int64_t* n_wide);
+
+/*
  * Forward trace, Trace(r_o, r_d) of Eq. 8 for n_rays rays. For each ray
  * every surfel hit with t_min < tau < t_max is found (Eq. 6-7: tau =
  * n.(mu - o)/(n.d), u = (p - mu).t_u / s_u, v = (p - mu).t_v / s_v, alpha =
@@ -175,6 +185,16 @@ irgs_status irgs_trace_forward(irgs_scene scene, const float* ray_o, const float
                                float* out_feat, float* out_depth, float* out_opacity,
                                int32_t* out_nhits, int32_t* out_hit_ids, int32_t max_hit_ids,
                                void* stream);
+
+/*
+ * Diagnostic: the forward march of irgs_trace_forward (k = 16, feat_count
+ * <= 10, same traversal policy flags) with per-ray counters instead of
+ * outputs. out_stats [n_rays, 4] int32: k-buffer rounds, BVH nodes fetched
+ * (in the warp-coherent walk: fetched by the warp while this ray was still
+ * marching), surfel tests, k-buffer insertions.
+ */
+irgs_status irgs_trace_stats(irgs_scene scene, const float* ray_o, const float* ray_d, int64_t n_rays,
+                             const irgs_trace_params* params, int32_t* out_stats, void* stream);
 
 /*
  * Backward of irgs_trace_forward for the loss

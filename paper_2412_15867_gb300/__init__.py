@@ -156,6 +156,17 @@ class Scene:
                    "irgs_scene_export")
         return perm[:n], keys[:n], nodes, boxes[:n]
 
+    def export_wide(self):
+        """Host copy of the 4-wide hierarchy: float32 [n_wide, 32] (see
+        irgs_scene_export_wide for the layout)."""
+        import numpy as np
+        nw = C.c_int64()
+        _lib.check(_lib.lib().irgs_scene_export_wide(self.handle, None, 0, C.byref(nw)), "irgs_scene_export_wide")
+        out = np.zeros((max(nw.value, 1), 32), np.float32)
+        _lib.check(_lib.lib().irgs_scene_export_wide(self.handle, out.ctypes.data_as(C.c_void_p), out.shape[0],
+                                                     C.byref(nw)), "irgs_scene_export_wide")
+        return out[:nw.value]
+
     def close(self) -> None:
         if getattr(self, "_h", None) is not None:
             _lib.lib().irgs_destroy_scene(self._h)
@@ -198,6 +209,19 @@ def trace_forward(scene: Scene, ray_o, ray_d, params: TraceParams = TraceParams(
             scene.handle, _ptr(o), _ptr(d), R, C.byref(p), _ptr(out["feat"]), _ptr(out["depth"]),
             _ptr(out["opacity"]), _ptr(out["n_hits"]), _ptr(ids), int(max_hit_ids), _stream(dev)),
             "irgs_trace_forward")
+    return out
+
+
+def trace_stats(scene: Scene, ray_o, ray_d, params: TraceParams = TraceParams()):
+    """Per-ray traversal counters [R, 4] int32: rounds, node fetches, surfel
+    tests, k-buffer insertions (diagnostic run of the forward march)."""
+    o, d = _rays(scene, ray_o, ray_d)
+    R = o.shape[0]
+    out = torch.empty((R, 4), device=scene.device, dtype=torch.int32)
+    p = params.c()
+    with torch.cuda.device(scene.device):
+        _lib.check(_lib.lib().irgs_trace_stats(scene.handle, _ptr(o), _ptr(d), R, C.byref(p), _ptr(out),
+                                               _stream(scene.device)), "irgs_trace_stats")
     return out
 
 

@@ -48,8 +48,10 @@ _SIGS = {
     "irgs_scene_info": (C.c_int, [P, P, P, P, P]),
     "irgs_scene_status": (C.c_int, [P, P, P]),
     "irgs_scene_export": (C.c_int, [P, P, P, P, P]),
+    "irgs_scene_export_wide": (C.c_int, [P, P, C.c_int64, P]),
     "irgs_trace_forward": (C.c_int, [P, P, P, C.c_int64, C.POINTER(TraceParamsC), P, P, P, P, P,
                                      C.c_int32, P]),
+    "irgs_trace_stats": (C.c_int, [P, P, P, C.c_int64, C.POINTER(TraceParamsC), P, P]),
     "irgs_trace_backward": (C.c_int, [P, P, P, C.c_int64, C.POINTER(TraceParamsC), P, P, P, P, P, P,
                                       P, P, P, P, P, P, P]),
     "irgs_build_lbvh_noalloc": (C.c_int, [C.POINTER(Surfels), C.c_float, P, P, P, P, P]),

@@ -136,6 +136,26 @@ irgs_status irgs_scene_export(irgs_scene sc, int32_t* perm, uint32_t* keys, floa
     return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
 }
 
+irgs_status irgs_scene_export_wide(irgs_scene sc, float* nodes, int64_t cap, int64_t* n_wide) {
+    if (sc == nullptr || cap < 0) return IRGS_ERR_INVALID_ARG;
+    if (use_device(sc) != IRGS_OK) return IRGS_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return IRGS_ERR_CUDA;
+    int64_t nw = 1;
+    if (sc->n > 1) {
+        uint32_t last[2] = {0, 0};
+        if (cudaMemcpy(&last[0], sc->wide_rank + (sc->n - 2), sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(&last[1], sc->refit_flag + (sc->n - 2), sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return IRGS_ERR_CUDA;
+        nw = (int64_t)last[0] + last[1];
+    }
+    if (n_wide) *n_wide = nw;
+    const int64_t m = nw < cap ? nw : cap;
+    if (nodes && m > 0 &&
+        cudaMemcpy(nodes, sc->wide, sizeof(irgs::WideNode) * m, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return IRGS_ERR_CUDA;
+    return IRGS_OK;
+}
+
 irgs_status irgs_trace_forward(irgs_scene sc, const float* ray_o, const float* ray_d, int64_t n_rays,
                                const irgs_trace_params* params, float* out_feat, float* out_depth,
                                float* out_opacity, int32_t* out_nhits, int32_t* out_hit_ids, int32_t max_hit_ids,
@@ -153,6 +173,19 @@ irgs_status irgs_trace_forward(irgs_scene sc, const float* ray_o, const float* r
                                       static_cast<cudaStream_t>(stream));
 }
 
+irgs_status irgs_trace_stats(irgs_scene sc, const float* ray_o, const float* ray_d, int64_t n_rays,
+                             const irgs_trace_params* params, int32_t* out_stats, void* stream) {
+    if (sc == nullptr || n_rays < 0) return IRGS_ERR_INVALID_ARG;
+    irgs_status s = check_params(sc, params);
+    if (s != IRGS_OK) return s;
+    if (params->k != 16 || params->feat_count > 10) return IRGS_ERR_UNSUPPORTED;
+    if (n_rays > 0 && (!ray_o || !ray_d || !out_stats)) return IRGS_ERR_INVALID_ARG;
+    if (n_rays >= (int64_t)UINT32_MAX * 128) return IRGS_ERR_INVALID_ARG;
+    if ((s = use_device(sc)) != IRGS_OK) return s;
+    return irgs::launch_trace_stats(sc->view(), ray_o, ray_d, n_rays, *params, out_stats,
+                                    static_cast<cudaStream_t>(stream));
+}
+
 irgs_status irgs_trace_backward(irgs_scene sc, const float* ray_o, const float* ray_d, int64_t n_rays,
                                 const irgs_trace_params* params, const float* out_feat, const float* out_depth,
                                 const float* out_opacity, const int32_t* out_nhits, const float* g_feat,
@@ -168,7 +201,7 @@ irgs_status irgs_trace_backward(irgs_scene sc, const float* ray_o, const float* 
     if (sc->n > 0 && sc->F > 0 && params->feat_count > 0 && !g_features) return IRGS_ERR_INVALID_ARG;
     if (n_rays >= (int64_t)UINT32_MAX * 128) return IRGS_ERR_INVALID_ARG;
     if ((s = use_device(sc)) != IRGS_OK) return s;
-    return irgs::launch_trace_backward(sc->view(), ray_o, ray_d, n_rays, *params, out_feat, out_depth, out_opacity,
+    return irgs::launch_trace_backward(sc->view(), sc->perm, ray_o, ray_d, n_rays, *params, out_feat, out_depth, out_opacity,
                                        out_nhits, g_feat, g_depth, g_opacity, g_means, g_quats, g_scales,
                                        g_opacity_param, g_features, static_cast<cudaStream_t>(stream));
 }

@@ -37,6 +37,15 @@ struct __align__(16) Node {
     int4 d;
 };
 
+// 4-wide node (128 B, one cache line): the boxes of up to four children in
+// structure-of-arrays form (component k of each float4 belongs to child k)
+// and the child ids (same encoding as Node; kNoChild for empty slots).
+struct __align__(16) WideNode {
+    float4 lox, loy, loz, hix, hiy, hiz;
+    int4 child;
+    int4 pad;
+};
+
 // Packed surfel record, Morton order (64 B = 4 x float4):
 //   r0 = {mu.x, mu.y, mu.z, opacity}
 //   r1 = {t_u/s_u (xyz), rho_c^2}        rho_c^2 < 0: never hit
@@ -108,7 +117,8 @@ void count_launches(uint64_t k);
 // ---------------------------------------------------------------------------
 // Device view of a scene (plain pointers, passed by value to kernels).
 struct SceneView {
-    const Node* nodes;     // [max(n-1,1)]
+    const Node* nodes;     // [max(n-1,1)] binary hierarchy
+    const WideNode* wide;  // 4-wide hierarchy traversed by the kernels, root 0
     const float4* rec;     // [n * 4]
     const float* feat;     // [n, F] Morton order
     const float4* q_raw;   // [n] raw quaternion (w,x,y,z), Morton order

@@ -344,6 +344,101 @@ __global__ void k_tiny_root(int64_t n, const float* __restrict__ leaf_box, Node*
     nodes[0].d = make_int4(n == 1 ? ~0 : kNoChild, kNoChild, 0, 0);
 }
 
+// K6: 4-wide hierarchy. Every internal node at even depth of the binary tree
+// becomes a wide node whose children are its grandchildren (or its children
+// where those are leaves); the boxes come from the binary nodes, so no box
+// is recomputed.
+__global__ void k_wide_mark(int64_t n, const int32_t* __restrict__ node_parent, uint32_t* __restrict__ flag,
+                            uint32_t* status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int depth = 0;
+    int32_t p = (int32_t)i;
+    while (p != 0) {
+        p = node_parent[p];
+        if (++depth > 128 || p < 0) {
+            atomicOr(status, kErrBadTree);
+            flag[i] = 0;
+            return;
+        }
+    }
+    flag[i] = (depth & 1) == 0 ? 1u : 0u;
+}
+
+__device__ __forceinline__ void node_child(const Node& nd, int s, int32_t& c, float b[6]) {
+    if (s == 0) {
+        c = nd.d.x;
+        b[0] = nd.a.x; b[1] = nd.a.y; b[2] = nd.a.z; b[3] = nd.a.w; b[4] = nd.b.x; b[5] = nd.b.y;
+    } else {
+        c = nd.d.y;
+        b[0] = nd.b.z; b[1] = nd.b.w; b[2] = nd.c.x; b[3] = nd.c.y; b[4] = nd.c.z; b[5] = nd.c.w;
+    }
+}
+
+__global__ void k_wide_emit(int64_t n, const Node* __restrict__ nodes, const uint32_t* __restrict__ flag,
+                            const uint32_t* __restrict__ rank, int64_t max_wide, WideNode* __restrict__ wide,
+                            uint32_t* status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n - 1 || flag[i] == 0u) return;
+    const uint32_t w = rank[i];
+    if ((int64_t)w >= max_wide) {
+        atomicOr(status, kErrBadTree);
+        return;
+    }
+    int32_t cid[4] = {kNoChild, kNoChild, kNoChild, kNoChild};
+    float box[4][6] = {};
+    int m = 0;
+    const Node nd = nodes[i];
+    for (int s = 0; s < 2; ++s) {
+        int32_t c;
+        float b[6];
+        node_child(nd, s, c, b);
+        if (c < 0) {
+            cid[m] = c;
+            for (int k = 0; k < 6; ++k) box[m][k] = b[k];
+            ++m;
+        } else {
+            const Node cn = nodes[c];
+            for (int t = 0; t < 2; ++t) {
+                int32_t g;
+                float gb[6];
+                node_child(cn, t, g, gb);
+                cid[m] = g < 0 ? g : (int32_t)rank[g];
+                for (int k = 0; k < 6; ++k) box[m][k] = gb[k];
+                ++m;
+            }
+        }
+    }
+    WideNode o;
+    o.lox = make_float4(box[0][0], box[1][0], box[2][0], box[3][0]);
+    o.loy = make_float4(box[0][1], box[1][1], box[2][1], box[3][1]);
+    o.loz = make_float4(box[0][2], box[1][2], box[2][2], box[3][2]);
+    o.hix = make_float4(box[0][3], box[1][3], box[2][3], box[3][3]);
+    o.hiy = make_float4(box[0][4], box[1][4], box[2][4], box[3][4]);
+    o.hiz = make_float4(box[0][5], box[1][5], box[2][5], box[3][5]);
+    o.child = make_int4(cid[0], cid[1], cid[2], cid[3]);
+    o.pad = make_int4(m, 0, 0, 0);
+    wide[w] = o;
+}
+
+// Wide root of a one-surfel (or empty) scene.
+__global__ void k_wide_tiny(int64_t n, const float* __restrict__ leaf_box, WideNode* wide) {
+    WideNode o;
+    const float z = 0.f;
+    float b[6] = {z, z, z, z, z, z};
+    if (n == 1)
+        for (int k = 0; k < 6; ++k) b[k] = leaf_box[k];
+    o.lox = make_float4(b[0], z, z, z);
+    o.loy = make_float4(b[1], z, z, z);
+    o.loz = make_float4(b[2], z, z, z);
+    o.hix = make_float4(b[3], z, z, z);
+    o.hiy = make_float4(b[4], z, z, z);
+    o.hiz = make_float4(b[5], z, z, z);
+    o.child = make_int4(n == 1 ? ~0 : kNoChild, kNoChild, kNoChild, kNoChild);
+    o.pad = make_int4(n == 1 ? 1 : 0, 0, 0, 0);
+    wide[0] = o;
+}
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count, int64_t& bytes) {
     size_t b = sizeof(T) * (count > 0 ? count : 1);
@@ -359,7 +454,8 @@ void free_scene(irgs_scene sc) {
     if (!sc) return;
     void* ptrs[] = {sc->nodes, sc->rec, sc->feat, sc->q_raw, sc->scale, sc->leaf_box, sc->keys,
                     sc->perm, sc->status, sc->rec_user, sc->box_user, sc->keys_tmp, sc->vals_tmp,
-                    sc->hist, sc->bounds, sc->leaf_parent, sc->node_parent, sc->refit_flag};
+                    sc->hist, sc->bounds, sc->leaf_parent, sc->node_parent, sc->refit_flag, sc->wide,
+                    sc->wide_rank};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete sc;
@@ -407,6 +503,20 @@ static irgs_status enqueue_build(irgs_scene sc, const irgs_surfels* s, cudaStrea
     if (n <= 1) k_tiny_root<<<1, 1, 0, st>>>(n, sc->leaf_box, sc->nodes);
     // boxes, morton, 4 x (hist, scan, scatter), gather = 15; + features; + karras/refit or the tiny root
     count_launches(n == 0 ? 1 : 15 + (F > 0) + (n == 1 ? 1 : 2));
+    if (sc->wide != nullptr) {
+        if (n > 1) {
+            const int T = 256;
+            k_wide_mark<<<blocks_for(n - 1, T), T, 0, st>>>(n, sc->node_parent, sc->refit_flag, sc->status);
+            A(cudaMemcpyAsync(sc->wide_rank, sc->refit_flag, sizeof(uint32_t) * (n - 1), cudaMemcpyDeviceToDevice, st));
+            k_scan_exclusive<<<1, 1024, 0, st>>>(sc->wide_rank, n - 1);
+            k_wide_emit<<<blocks_for(n - 1, T), T, 0, st>>>(n, sc->nodes, sc->refit_flag, sc->wide_rank, sc->max_wide,
+                                                           sc->wide, sc->status);
+            count_launches(3);
+        } else {
+            k_wide_tiny<<<1, 1, 0, st>>>(n, sc->leaf_box, sc->wide);
+            count_launches(1);
+        }
+    }
     A(cudaGetLastError());
     return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
 }
@@ -443,6 +553,10 @@ irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_
     A(dalloc(&sc->leaf_parent, n, B));
     A(dalloc(&sc->node_parent, nn, B));
     A(dalloc(&sc->refit_flag, nn, B));
+    A(dalloc(&sc->wide_rank, nn, B));
+    // even-depth internal nodes of a binary tree with n leaves: at most 2(n-1)/3 + 1
+    sc->max_wide = 2 * nn / 3 + 2;
+    A(dalloc(&sc->wide, sc->max_wide, B));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_scene(sc);

@@ -24,6 +24,8 @@ struct irgs_scene_s {
     uint32_t* keys = nullptr;         // [n] sorted Morton codes
     int32_t* perm = nullptr;          // [n] user index of Morton slot
     uint32_t* status = nullptr;       // device error word
+    irgs::WideNode* wide = nullptr;   // [max_wide] 4-wide hierarchy
+    int64_t max_wide = 0;
 
     // build scratch (kept for rebuilds)
     float4* rec_user = nullptr;       // [n*4]
@@ -35,10 +37,12 @@ struct irgs_scene_s {
     int32_t* leaf_parent = nullptr;   // [n]
     int32_t* node_parent = nullptr;   // [max(n-1,1)]
     uint32_t* refit_flag = nullptr;   // [max(n-1,1)]
+    uint32_t* wide_rank = nullptr;    // [max(n-1,1)] even-depth flag, then its exclusive scan
 
     irgs::SceneView view() const {
         irgs::SceneView v;
         v.nodes = nodes;
+        v.wide = wide;
         v.rec = rec;
         v.feat = feat;
         v.q_raw = q_raw;
@@ -64,8 +68,10 @@ void free_scene(irgs_scene sc);
 irgs_status launch_trace_forward(const SceneView& sv, const float* ro, const float* rd, int64_t R,
                                  const irgs_trace_params& p, float* feat, float* depth, float* opac,
                                  int32_t* nhits, int32_t* ids, int32_t max_ids, cudaStream_t st);
+irgs_status launch_trace_stats(const SceneView& S, const float* ro, const float* rd, int64_t R,
+                               const irgs_trace_params& p, int32_t* stats, cudaStream_t st);
 // trace_bwd.cu
-irgs_status launch_trace_backward(const SceneView& sv, const float* ro, const float* rd, int64_t R,
+irgs_status launch_trace_backward(const SceneView& sv, const int32_t* perm, const float* ro, const float* rd, int64_t R,
                                   const irgs_trace_params& p, const float* feat, const float* depth,
                                   const float* opac, const int32_t* nhits, const float* g_feat,
                                   const float* g_depth, const float* g_opac, float* g_means,

@@ -110,6 +110,45 @@ __device__ __forceinline__ void slab2(const Node& nd, const Ray& r, float& tn0, 
     tf1 = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fmaxf(z0, z1));
 }
 
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+__device__ __forceinline__ WideNode load_wide(const WideNode* w, int i) {
+    const float4* p = reinterpret_cast<const float4*>(w + i);
+    WideNode n;
+    n.lox = ldg4(p);
+    n.loy = ldg4(p + 1);
+    n.loz = ldg4(p + 2);
+    n.hix = ldg4(p + 3);
+    n.hiy = ldg4(p + 4);
+    n.hiz = ldg4(p + 5);
+    n.child = ldg4i(reinterpret_cast<const int4*>(p + 6));
+    return n;
+}
+
+// Slab intervals of the four children of a wide node.
+__device__ __forceinline__ void slab4(const WideNode& w, const Ray& r, float tn[4], float tf[4]) {
+    const float lx[4] = {w.lox.x, w.lox.y, w.lox.z, w.lox.w}, hx[4] = {w.hix.x, w.hix.y, w.hix.z, w.hix.w};
+    const float ly[4] = {w.loy.x, w.loy.y, w.loy.z, w.loy.w}, hy[4] = {w.hiy.x, w.hiy.y, w.hiy.z, w.hiy.w};
+    const float lz[4] = {w.loz.x, w.loz.y, w.loz.z, w.loz.w}, hz[4] = {w.hiz.x, w.hiz.y, w.hiz.z, w.hiz.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float x0 = fmaf(lx[k], r.inv.x, -r.oinv.x), x1 = fmaf(hx[k], r.inv.x, -r.oinv.x);
+        const float y0 = fmaf(ly[k], r.inv.y, -r.oinv.y), y1 = fmaf(hy[k], r.inv.y, -r.oinv.y);
+        const float z0 = fmaf(lz[k], r.inv.z, -r.oinv.z), z1 = fmaf(hz[k], r.inv.z, -r.oinv.z);
+        tn[k] = max3f(fminf(x0, x1), fminf(y0, y1), fminf(z0, z1));
+        tf[k] = min3f(fmaxf(x0, x1), fmaxf(y0, y1), fmaxf(z0, z1));
+    }
+}
+
 // Conservative slack on depths compared against box intervals.
 __device__ __forceinline__ float tslack(float t) { return 1e-5f * (1.0f + fabsf(t)); }
 
@@ -185,11 +224,18 @@ __host__ __device__ constexpr int trace_threads() { return K > 16 ? 64 : 128; }
 
 __device__ __forceinline__ float key_depth(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
 
+// Per-ray traversal counters of the diagnostic build (STATS = true).
+struct TraceStats {
+    int rounds, nodes, leaves, inserts;
+};
+
 // Test surfel m against the ray and insert it into the k-buffer if it lies
 // strictly after (last_key, last_m) and before the buffer's last entry.
-template <class KB>
+template <class KB, bool STATS = false>
 __device__ __forceinline__ void leaf_insert(const SceneView& S, const Ray& ray, const TraceParams& P, int32_t m,
-                                            uint64_t last_key, int32_t last_m, KB& kb, float& t_hi) {
+                                            uint64_t last_key, int32_t last_m, KB& kb, float& t_hi,
+                                            TraceStats* ts = nullptr) {
+    if (STATS) ts->leaves++;
     const float4* R = S.rec + (int64_t)m * kRecF4;
     const float4 r0 = ldg4(R), r1 = ldg4(R + 1), r2 = ldg4(R + 2), r3 = ldg4(R + 3);
     float kh, kl, a;
@@ -199,6 +245,7 @@ __device__ __forceinline__ void leaf_insert(const SceneView& S, const Ray& ray, 
     const bool after = past_min && (key > last_key || (key == last_key && m > last_m));
     const bool before = kh < P.t_max || (kh == P.t_max && kl < 0.f);
     if (after && before && kb.fits(key, m)) {
+        if (STATS) ts->inserts++;
         kb.insert(key, m, a);
         if (kb.full()) t_hi = key_depth(kb.tail_key);
     }
@@ -206,9 +253,10 @@ __device__ __forceinline__ void leaf_insert(const SceneView& S, const Ray& ray, 
 
 // One round: gather the K nearest hits strictly after (last_key, last_m).
 // Returns false if the traversal stack overflowed.
-template <class KB>
+template <class KB, bool STATS = false>
 __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray, const TraceParams& P,
-                                              uint64_t last_key, int32_t last_m, KB& kb) {
+                                              uint64_t last_key, int32_t last_m, KB& kb,
+                                              TraceStats* ts = nullptr) {
     int stack_n[kStackSize];
     float stack_t[kStackSize];
     int sp = 0;
@@ -218,43 +266,36 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
     const float lo_c = t_lo - tslack(t_lo);
     float t_hi = P.t_max;
     int ni = 0;
-    // each internal node is visited at most once per round in a valid tree
-    const int64_t max_visits = 2 * S.n + 64;
+    // each wide node is fetched at most once per round in a valid tree
+    const int64_t max_visits = S.n + 64;
     for (int64_t visits = 0;; ++visits) {
         if (visits > max_visits) {
             ok = false;
             break;
         }
-        const Node nd = load_node(S.nodes, ni);
-        float tn0, tf0, tn1, tf1;
-        slab2(nd, ray, tn0, tf0, tn1, tf1);
-        const int c0 = nd.d.x, c1 = nd.d.y;
+        const WideNode nd = load_wide(S.wide, ni);
+        if (STATS) ts->nodes++;
+        float tn[4], tf[4];
+        slab4(nd, ray, tn, tf);
+        const int c[4] = {nd.child.x, nd.child.y, nd.child.z, nd.child.w};
         float hi_c = t_hi + tslack(t_hi);
-        bool h0 = c0 != kNoChild && tn0 <= tf0 && tf0 >= lo_c && tn0 <= hi_c;
-        bool h1 = c1 != kNoChild && tn1 <= tf1 && tf1 >= lo_c && tn1 <= hi_c;
-        if (h0 && c0 < 0) leaf_insert(S, ray, P, ~c0, last_key, last_m, kb, t_hi);
-        if (h1 && c1 < 0) leaf_insert(S, ray, P, ~c1, last_key, last_m, kb, t_hi);
-        if (c0 < 0) h0 = false;
-        if (c1 < 0) h1 = false;
+        bool h[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h[k] = c[k] != kNoChild && tn[k] <= tf[k] && tf[k] >= lo_c && tn[k] <= hi_c;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (h[k] && c[k] < 0) leaf_insert<KB, STATS>(S, ray, P, ~c[k], last_key, last_m, kb, t_hi, ts);
         hi_c = t_hi + tslack(t_hi);
-        h0 = h0 && tn0 <= hi_c;
-        h1 = h1 && tn1 <= hi_c;
-        if (h0 && h1) {
-            const bool first0 = tn0 <= tn1;
-            if (sp < kStackSize) {
-                stack_n[sp] = first0 ? c1 : c0;
-                stack_t[sp] = first0 ? tn1 : tn0;
-                ++sp;
-            } else {
-                ok = false;
-            }
-            ni = first0 ? c0 : c1;
-        } else if (h0) {
-            ni = c0;
-        } else if (h1) {
-            ni = c1;
-        } else {
-            // pop the next node that can still hold a hit before t_hi
+        // internal children still in reach: descend into the nearest, push the rest far first
+        float t[4];
+        int nv = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool v = h[k] && c[k] >= 0 && tn[k] <= hi_c;
+            t[k] = v ? tn[k] : INFINITY;
+            nv += v;
+        }
+        if (nv == 0) {
             bool found = false;
             while (sp > 0) {
                 --sp;
@@ -265,7 +306,37 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
                 }
             }
             if (!found) break;
+            continue;
         }
+        // repeatedly take the farthest remaining child onto the stack
+        for (int r = 0; r < nv - 1; ++r) {
+            int far = -1;
+            float tfar = -INFINITY;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (t[k] != INFINITY && t[k] >= tfar) {
+                    tfar = t[k];
+                    far = k;
+                }
+            if (sp < kStackSize) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k == far) {
+                        stack_n[sp] = c[k];
+                        stack_t[sp] = t[k];
+                        t[k] = INFINITY;
+                    }
+                ++sp;
+            } else {
+                ok = false;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k == far) t[k] = INFINITY;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (t[k] != INFINITY) ni = c[k];
     }
     return ok;
 }
@@ -278,9 +349,10 @@ constexpr unsigned kFullWarp = 0xffffffffu;
 // each lane tests leaves with its own ray and keeps its own k-buffer, so the
 // result per ray equals the per-thread round. All 32 lanes must call this
 // together (inactive lanes pass active = false).
-template <class KB>
+template <class KB, bool STATS = false>
 __device__ __forceinline__ bool collect_round_warp(const SceneView& S, const Ray& ray, const TraceParams& P,
-                                                   uint64_t last_key, int32_t last_m, KB& kb, bool active) {
+                                                   uint64_t last_key, int32_t last_m, KB& kb, bool active,
+                                                   TraceStats* ts = nullptr) {
     kb.clear();
     const int lane = threadIdx.x & 31;
     const float t_lo = key_depth(last_key);
@@ -290,32 +362,60 @@ __device__ __forceinline__ bool collect_round_warp(const SceneView& S, const Ray
     int sp = 0;
     bool ok = true;
     int ni = 0;
-    const int64_t max_visits = 2 * S.n + 64;
+    const int64_t max_visits = S.n + 64;
     for (int64_t visits = 0;; ++visits) {
         if (visits > max_visits) {
             ok = false;
             break;
         }
-        const Node nd = load_node(S.nodes, ni);
-        float tn0, tf0, tn1, tf1;
-        slab2(nd, ray, tn0, tf0, tn1, tf1);
-        const int c0 = nd.d.x, c1 = nd.d.y;
+        const WideNode nd = load_wide(S.wide, ni);
+        if (STATS && active) ts->nodes++;
+        float tn[4], tf[4];
+        slab4(nd, ray, tn, tf);
+        const int c[4] = {nd.child.x, nd.child.y, nd.child.z, nd.child.w};
         float hi_c = t_hi + tslack(t_hi);
-        const bool h0 = active && c0 != kNoChild && tn0 <= tf0 && tf0 >= lo_c && tn0 <= hi_c;
-        const bool h1 = active && c1 != kNoChild && tn1 <= tf1 && tf1 >= lo_c && tn1 <= hi_c;
-        if (h0 && c0 < 0) leaf_insert(S, ray, P, ~c0, last_key, last_m, kb, t_hi);
-        if (h1 && c1 < 0) leaf_insert(S, ray, P, ~c1, last_key, last_m, kb, t_hi);
+        bool h[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            h[k] = active && c[k] != kNoChild && tn[k] <= tf[k] && tf[k] >= lo_c && tn[k] <= hi_c;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (h[k] && c[k] < 0) leaf_insert<KB, STATS>(S, ray, P, ~c[k], last_key, last_m, kb, t_hi, ts);
         hi_c = t_hi + tslack(t_hi);
-        const bool v0 = c0 >= 0 && h0 && tn0 <= hi_c;
-        const bool v1 = c1 >= 0 && h1 && tn1 <= hi_c;
-        const unsigned b0 = __ballot_sync(kFullWarp, v0);
-        const unsigned b1 = __ballot_sync(kFullWarp, v1);
-        if (b0 != 0u && b1 != 0u) {
-            // go first where most of the lanes that need both go first
-            const unsigned both = b0 & b1;
-            const unsigned pref1 = __ballot_sync(kFullWarp, v0 && v1 && tn1 < tn0);
-            const bool first1 = 2 * __popc(pref1) > __popc(both);
-            const int farc = first1 ? c0 : c1;
+        // internal children some lane still needs; order them by the entry
+        // depth seen by the first lane that needs each
+        float t[4];
+        int nv = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned b = __ballot_sync(kFullWarp, h[k] && c[k] >= 0 && tn[k] <= hi_c);
+            const int src = b ? __ffs(b) - 1 : 0;
+            const float tk = __shfl_sync(kFullWarp, tn[k], src);
+            t[k] = b ? tk : INFINITY;
+            nv += b ? 1 : 0;
+        }
+        if (nv == 0) {
+            if (sp == 0) break;
+            --sp;
+            ni = __shfl_sync(kFullWarp, (sp >> 5) ? st1 : st0, sp & 31);
+            continue;
+        }
+        for (int r = 0; r < nv - 1; ++r) {
+            int far = -1;
+            float tfar = -INFINITY;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (t[k] != INFINITY && t[k] >= tfar) {
+                    tfar = t[k];
+                    far = k;
+                }
+            int farc = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (k == far) {
+                    farc = c[k];
+                    t[k] = INFINITY;
+                }
             if (sp < kStackSize) {
                 if (lane == (sp & 31)) {
                     if (sp >> 5) st1 = farc; else st0 = farc;
@@ -324,17 +424,10 @@ __device__ __forceinline__ bool collect_round_warp(const SceneView& S, const Ray
             } else {
                 ok = false;
             }
-            ni = first1 ? c1 : c0;
-        } else if (b0 != 0u) {
-            ni = c0;
-        } else if (b1 != 0u) {
-            ni = c1;
-        } else {
-            if (sp == 0) break;
-            --sp;
-            const int v = __shfl_sync(kFullWarp, (sp >> 5) ? st1 : st0, sp & 31);
-            ni = v;
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (t[k] != INFINITY) ni = c[k];
     }
     return ok;
 }
@@ -350,10 +443,10 @@ struct MarchState {
 
 // WARP = true: all 32 lanes of the warp call this together (lanes without a
 // ray pass live = false) and traverse warp-coherently.
-template <int K, int FB, bool WARP>
+template <int K, int FB, bool WARP, bool STATS = false>
 __device__ __forceinline__ bool march_forward(const SceneView& S, const Ray& ray, const TraceParams& P,
                                               MarchState<K, FB>& st, int32_t* ids, int max_ids,
-                                              bool live = true) {
+                                              bool live = true, TraceStats* ts = nullptr) {
 #pragma unroll
     for (int c = 0; c < FB; ++c) st.C[c] = 0.f;
     st.D = 0.f;
@@ -367,10 +460,11 @@ __device__ __forceinline__ bool march_forward(const SceneView& S, const Ray& ray
     kb.bind();
     bool done = !live;
     while (WARP ? __any_sync(kFullWarp, !done) : !done) {
+        if (STATS && !done) ts->rounds++;
         if (WARP)
-            ok &= collect_round_warp(S, ray, P, last_key, last_m, kb, !done);
+            ok &= collect_round_warp<decltype(kb), STATS>(S, ray, P, last_key, last_m, kb, !done, ts);
         else
-            ok &= collect_round(S, ray, P, last_key, last_m, kb);
+            ok &= collect_round<decltype(kb), STATS>(S, ray, P, last_key, last_m, kb, ts);
         if (done) continue;
         for (int j = 0; j < kb.cnt && !done; ++j) {
             {

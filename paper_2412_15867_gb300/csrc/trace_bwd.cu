@@ -11,7 +11,10 @@
 // suffix comes from the forward's totals minus the replayed prefix). The
 // chain then runs alpha -> (o, rho^2) -> (u, v) -> (p - mu, tau) -> (mu, t_u,
 // t_v, n, s_u, s_v) -> raw quaternion (Eq. 6-7 and the rotation of the unit
-// quaternion). Gradients land in user order through warp-aggregated atomics.
+// quaternion). Per-hit gradients are summed across the lanes of a warp that
+// hold the same surfel, added with vector atomics into a Morton-ordered
+// scratch accumulator (stream-ordered allocation for the call), and finally
+// added once into the caller's user-order arrays.
 #include <cuda_runtime.h>
 
 #include "scene.h"
@@ -22,23 +25,26 @@ namespace {
 
 constexpr int kBwdThreads = 128;
 
-// Per-surfel gradient record: means(3) quats(4) scales(2) opacity(1) features(FB).
+// Per-surfel gradient row in the Morton-ordered scratch accumulator (16-byte
+// aligned, added with vector atomics):
+//   [g_mu.x g_mu.y g_mu.z g_o] [g_q.w g_q.x g_q.y g_q.z] [g_su g_sv 0 0]
+//   [g_f 0..3] [g_f 4..7] ...   (the traced channels, padded to 4)
 template <int FB>
-struct GradVals {
-    static constexpr int N = 10 + FB;
+struct GradRow {
+    static constexpr int FB4 = (FB + 3) / 4 * 4;
+    static constexpr int N = 12 + FB4;   // floats per row
     float v[N];
 };
 
-// Add `g` (N values) for surfel `uid`, summing over the lanes of the warp that
-// hold the same uid first (match mask + per-lane rows in shared memory).
+// Add row g for Morton slot m: lanes of the warp holding the same slot are
+// summed first (match mask + per-lane rows in shared memory), then the
+// first of them adds the row with N/4 float4 atomics.
 template <int FB>
-__device__ __forceinline__ void scatter_grad(const GradVals<FB>& g, int32_t uid, int fc, int F, int off,
-                                             float* __restrict__ g_means, float* __restrict__ g_quats,
-                                             float* __restrict__ g_scales, float* __restrict__ g_opac,
-                                             float* __restrict__ g_feat, float* rows /* [32][N+1] this warp */) {
-    constexpr int N = GradVals<FB>::N;
+__device__ __forceinline__ void accumulate_row(const GradRow<FB>& g, int32_t m, float* __restrict__ acc_rows,
+                                               float* rows /* [32][N+1] this warp */) {
+    constexpr int N = GradRow<FB>::N;
     const unsigned active = __activemask();
-    const unsigned peers = __match_any_sync(active, uid);
+    const unsigned peers = __match_any_sync(active, m);
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(peers) - 1;
     float acc[N];
@@ -62,17 +68,36 @@ __device__ __forceinline__ void scatter_grad(const GradVals<FB>& g, int32_t uid,
         __syncwarp(peers);
     }
     if (lane != leader) return;
-    const int64_t u = uid;
+    float4* dst = reinterpret_cast<float4*>(acc_rows + (int64_t)m * N);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) atomicAdd(g_means + 3 * u + k, acc[k]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) atomicAdd(g_quats + 4 * u + k, acc[3 + k]);
-    atomicAdd(g_scales + 2 * u, acc[7]);
-    atomicAdd(g_scales + 2 * u + 1, acc[8]);
-    atomicAdd(g_opac + u, acc[9]);
-#pragma unroll
-    for (int c = 0; c < FB; ++c)
-        if (c < fc) atomicAdd(g_feat + u * F + off + c, acc[10 + c]);
+    for (int q = 0; q < N / 4; ++q)
+        atomicAdd(dst + q, make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]));
+}
+
+// Add the Morton-ordered rows into the caller's user-order gradients
+// (each user index is touched by exactly one thread: no atomics).
+template <int FB>
+__global__ void k_grad_scatter(const int32_t* __restrict__ perm, int64_t n, const float* __restrict__ acc_rows,
+                               int fc, int F, int off, float* __restrict__ g_means, float* __restrict__ g_quats,
+                               float* __restrict__ g_scales, float* __restrict__ g_opac, float* __restrict__ g_feat) {
+    constexpr int N = GradRow<FB>::N;
+    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const int64_t u = perm[m];
+    const float4* r = reinterpret_cast<const float4*>(acc_rows + m * N);
+    const float4 a = r[0], q = r[1], sc = r[2];
+    g_means[3 * u] += a.x;
+    g_means[3 * u + 1] += a.y;
+    g_means[3 * u + 2] += a.z;
+    g_opac[u] += a.w;
+    g_quats[4 * u] += q.x;
+    g_quats[4 * u + 1] += q.y;
+    g_quats[4 * u + 2] += q.z;
+    g_quats[4 * u + 3] += q.w;
+    g_scales[2 * u] += sc.x;
+    g_scales[2 * u + 1] += sc.y;
+    const float* f = acc_rows + m * N + 12;
+    for (int c = 0; c < fc; ++c) g_feat[u * F + off + c] += f[c];
 }
 
 template <int K, int FB, bool WARP>
@@ -80,9 +105,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
     SceneView S, const float* __restrict__ ro, const float* __restrict__ rd, int64_t R, TraceParams P,
     const float* __restrict__ out_feat, const float* __restrict__ out_depth, const float* __restrict__ out_opac,
     const int32_t* __restrict__ out_nhits, const float* __restrict__ g_featv, const float* __restrict__ g_depthv,
-    const float* __restrict__ g_opacv, float* __restrict__ g_means, float* __restrict__ g_quats,
-    float* __restrict__ g_scales, float* __restrict__ g_opac, float* __restrict__ g_feat) {
-    constexpr int N = GradVals<FB>::N;
+    const float* __restrict__ g_opacv,
+    float* __restrict__ acc_rows) {
+    constexpr int N = GradRow<FB>::N;
     static_assert(kBwdThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
     __shared__ float rows_all[kBwdThreads * (N + 1)];
     float* rows = rows_all + (threadIdx.x & ~31) * (N + 1);
@@ -147,7 +172,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
                 const float2 sc = __ldg(&S.scale[m]);
                 const float4 q = __ldg(&S.q_raw[m]);
 
-                GradVals<FB> gv;
+                GradRow<FB> gv;
                 const bool clamped = hg.a_raw >= P.alpha_max;
                 const float g_o = clamped ? 0.f : dA * hg.G;
                 const float g_rho2 = clamped ? 0.f : -0.5f * dA * a;
@@ -172,17 +197,18 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
                                         qy * gtv.z + qx * gn.x + qy * gn.y);
                 const float proj = qw * hw + qx * hx + qy * hy + qz * hz;
                 gv.v[0] = gmu.x; gv.v[1] = gmu.y; gv.v[2] = gmu.z;
-                gv.v[3] = (hw - qw * proj) / qn;
-                gv.v[4] = (hx - qx * proj) / qn;
-                gv.v[5] = (hy - qy * proj) / qn;
-                gv.v[6] = (hz - qz * proj) / qn;
-                gv.v[7] = -gu * hg.u / sc.x;
-                gv.v[8] = -gvv * hg.v / sc.y;
-                gv.v[9] = g_o;
+                gv.v[3] = g_o;
+                gv.v[4] = (hw - qw * proj) / qn;
+                gv.v[5] = (hx - qx * proj) / qn;
+                gv.v[6] = (hy - qy * proj) / qn;
+                gv.v[7] = (hz - qz * proj) / qn;
+                gv.v[8] = -gu * hg.u / sc.x;
+                gv.v[9] = -gvv * hg.v / sc.y;
+                gv.v[10] = 0.f;
+                gv.v[11] = 0.f;
 #pragma unroll
-                for (int c = 0; c < FB; ++c) gv.v[10 + c] = w * gC[c];
-                const int32_t uid = __float_as_int(r2.w);
-                scatter_grad<FB>(gv, uid, P.fc, S.F, P.off, g_means, g_quats, g_scales, g_opac, g_feat, rows);
+                for (int c = 0; c < GradRow<FB>::FB4; ++c) gv.v[12 + c] = c < FB ? w * gC[c] : 0.f;
+                accumulate_row<FB>(gv, m, acc_rows, rows);
 
                 T = __fmul_rn(T, __fsub_rn(1.0f, a));
                 ++nh;
@@ -199,41 +225,54 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
 }
 
 template <int K, int FB, bool WARP>
-cudaError_t launch(const SceneView& S, const float* ro, const float* rd, int64_t R, const TraceParams& P,
-                   const float* feat, const float* depth, const float* opac, const int32_t* nhits,
-                   const float* gf, const float* gd, const float* go, float* gm, float* gq, float* gs,
-                   float* gop, float* gfe, cudaStream_t st) {
-    const int64_t blocks = (R + kBwdThreads - 1) / kBwdThreads;
-    k_trace_backward<K, FB, WARP><<<(unsigned)blocks, kBwdThreads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac, nhits,
-                                                                      gf, gd, go, gm, gq, gs, gop, gfe);
-    count_launches(1);
-    return cudaGetLastError();
+cudaError_t launch(const SceneView& S, const int32_t* perm, const float* ro, const float* rd, int64_t R,
+                   const TraceParams& P, const float* feat, const float* depth, const float* opac,
+                   const int32_t* nhits, const float* gf, const float* gd, const float* go, float* gm, float* gq,
+                   float* gs, float* gop, float* gfe, cudaStream_t st) {
+    constexpr int N = GradRow<FB>::N;
+    const size_t bytes = sizeof(float) * N * (size_t)(S.n > 0 ? S.n : 1);
+    float* acc_rows = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&acc_rows), bytes, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(acc_rows, 0, bytes, st);
+    if (e == cudaSuccess) {
+        const int64_t blocks = (R + kBwdThreads - 1) / kBwdThreads;
+        k_trace_backward<K, FB, WARP><<<(unsigned)blocks, kBwdThreads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac,
+                                                                              nhits, gf, gd, go, acc_rows);
+        if (S.n > 0)
+            k_grad_scatter<FB><<<(unsigned)((S.n + 255) / 256), 256, 0, st>>>(perm, S.n, acc_rows, P.fc, S.F, P.off, gm,
+                                                                             gq, gs, gop, gfe);
+        count_launches(S.n > 0 ? 2 : 1);
+        e = cudaGetLastError();
+    }
+    cudaError_t ef = cudaFreeAsync(acc_rows, st);
+    return e != cudaSuccess ? e : ef;
 }
 
 template <int K, bool WARP>
-cudaError_t launch_f(const SceneView& S, const float* ro, const float* rd, int64_t R, const TraceParams& P,
+cudaError_t launch_f(const SceneView& S, const int32_t* perm, const float* ro, const float* rd, int64_t R, const TraceParams& P,
                      const float* feat, const float* depth, const float* opac, const int32_t* nhits,
                      const float* gf, const float* gd, const float* go, float* gm, float* gq, float* gs,
                      float* gop, float* gfe, cudaStream_t st) {
     if (P.fc <= 3)
-        return launch<K, 3, WARP>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+        return launch<K, 3, WARP>(S, perm, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
     if (P.fc <= 10)
-        return launch<K, 10, WARP>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
-    return launch<K, 16, WARP>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+        return launch<K, 10, WARP>(S, perm, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+    return launch<K, 16, WARP>(S, perm, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
 }
 
 template <int K>
-cudaError_t launch_k(bool warp, const SceneView& S, const float* ro, const float* rd, int64_t R,
+cudaError_t launch_k(bool warp, const SceneView& S, const int32_t* perm, const float* ro, const float* rd, int64_t R,
                      const TraceParams& P, const float* feat, const float* depth, const float* opac,
                      const int32_t* nhits, const float* gf, const float* gd, const float* go, float* gm, float* gq,
                      float* gs, float* gop, float* gfe, cudaStream_t st) {
-    return warp ? launch_f<K, true>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st)
-                : launch_f<K, false>(S, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+    return warp ? launch_f<K, true>(S, perm, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st)
+                : launch_f<K, false>(S, perm, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
 }
 
 }  // namespace
 
-irgs_status launch_trace_backward(const SceneView& S, const float* ro, const float* rd, int64_t R,
+irgs_status launch_trace_backward(const SceneView& S, const int32_t* perm, const float* ro, const float* rd, int64_t R,
                                   const irgs_trace_params& p, const float* feat, const float* depth,
                                   const float* opac, const int32_t* nhits, const float* g_feat,
                                   const float* g_depth, const float* g_opac, float* g_means, float* g_quats,
@@ -244,15 +283,16 @@ irgs_status launch_trace_backward(const SceneView& S, const float* ro, const flo
     const bool warp = (p.flags & IRGS_FLAG_PER_THREAD) == 0u;
     switch (p.k) {
         case 8:
-            e = launch_k<8>(warp, S, ro, rd, R, P, feat, depth, opac, nhits, g_feat, g_depth, g_opac, g_means,
+            e = launch_k<8>(warp, S, perm, ro, rd, R, P, feat, depth, opac, nhits, g_feat, g_depth, g_opac, g_means,
                             g_quats, g_scales, g_opacity, g_features, st);
             break;
         case 16:
-            e = launch_k<16>(warp, S, ro, rd, R, P, feat, depth, opac, nhits, g_feat, g_depth, g_opac, g_means,
+            e = launch_k<16>(warp, S, perm, ro, rd, R, P, feat, depth, opac, nhits, g_feat, g_depth, g_opac, g_means,
                              g_quats, g_scales, g_opacity, g_features, st);
             break;
         default: return IRGS_ERR_UNSUPPORTED;
     }
+    if (e == cudaErrorMemoryAllocation) return IRGS_ERR_OOM;
     return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
 }
 

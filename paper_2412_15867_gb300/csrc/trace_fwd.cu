@@ -67,7 +67,41 @@ cudaError_t launch_k(bool warp, const SceneView& S, const float* ro, const float
                 : launch_f<K, false>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st);
 }
 
+// Diagnostic: the forward march with per-ray counters (K = 16, <= 10 channels).
+template <bool WARP>
+__global__ void __launch_bounds__(128) k_trace_stats(SceneView S, const float* __restrict__ ro,
+                                                     const float* __restrict__ rd, int64_t R, TraceParams P,
+                                                     int32_t* __restrict__ stats) {
+    const int64_t r = blockIdx.x * (int64_t)128 + threadIdx.x;
+    const bool live = r < R;
+    if (!WARP && !live) return;
+    const int64_t q = live ? r : 0;
+    const Ray ray = make_ray(mk3(ro[3 * q], ro[3 * q + 1], ro[3 * q + 2]),
+                             mk3(rd[3 * q], rd[3 * q + 1], rd[3 * q + 2]));
+    MarchState<16, 10> st;
+    TraceStats ts = {0, 0, 0, 0};
+    march_forward<16, 10, WARP, true>(S, ray, P, st, nullptr, 0, live, &ts);
+    if (!live) return;
+    stats[4 * r] = ts.rounds;
+    stats[4 * r + 1] = ts.nodes;
+    stats[4 * r + 2] = ts.leaves;
+    stats[4 * r + 3] = ts.inserts;
+}
+
 }  // namespace
+
+irgs_status launch_trace_stats(const SceneView& S, const float* ro, const float* rd, int64_t R,
+                               const irgs_trace_params& p, int32_t* stats, cudaStream_t st) {
+    if (R == 0) return IRGS_OK;
+    const TraceParams P = to_params(p);
+    const unsigned blocks = (unsigned)((R + 127) / 128);
+    if ((p.flags & IRGS_FLAG_PER_THREAD) == 0u)
+        k_trace_stats<true><<<blocks, 128, 0, st>>>(S, ro, rd, R, P, stats);
+    else
+        k_trace_stats<false><<<blocks, 128, 0, st>>>(S, ro, rd, R, P, stats);
+    count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+}
 
 irgs_status launch_trace_forward(const SceneView& S, const float* ro, const float* rd, int64_t R,
                                  const irgs_trace_params& p, float* feat, float* depth, float* opac,

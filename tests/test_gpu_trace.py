@@ -245,3 +245,53 @@ def test_traversal_modes_give_identical_results():
         irgs.trace_forward(S, dev(ro), dev(rd), irgs.TraceParams(flags=3))
     with pytest.raises(irgs.IrgsError):
         irgs.trace_forward(S, dev(ro), dev(rd), irgs.TraceParams(flags=4))
+
+
+def test_trace_stats_counters_are_consistent():
+    sc = synth.object_scene(n=20_000, seed=17)
+    ro, rd = synth.camera_batch_rays(synth.hemisphere_cameras(1, seed=17), 64, 64, tile=(8, 4))
+    S = make_scene(irgs, sc)
+    p = irgs.TraceParams(k=16, feat_count=10)
+    out = irgs.trace_forward(S, dev(ro), dev(rd), p)
+    nh = out["n_hits"].cpu().numpy()
+    sw = irgs.trace_stats(S, dev(ro), dev(rd), p).cpu().numpy()
+    st = irgs.trace_stats(S, dev(ro), dev(rd), p.with_(flags=irgs.FLAG_PER_THREAD)).cpu().numpy()
+    for s in (sw, st):
+        assert np.array_equal(s[:, 0], sw[:, 0])          # rounds depend only on the hits
+        assert np.all(s[:, 0] >= 1)
+        assert np.all(s[:, 0] >= np.ceil(nh / 16))
+        assert np.all(s[:, 3] >= nh) and np.all(s[:, 2] >= s[:, 3])
+        assert np.all(s[nh > 0, 1] > 0)
+
+
+def test_wide_hierarchy_invariants():
+    sc = synth.object_scene(n=30_000, seed=23)
+    sc = sc.subset(np.concatenate([np.arange(sc.n), np.arange(300)]))
+    S = make_scene(irgs, sc)
+    perm, keys, nodes, boxes = S.export()
+    W = S.export_wide()
+    n = sc.n
+    assert 1 <= W.shape[0] <= 2 * (n - 1) // 3 + 2
+    lo = W[:, 0:12].reshape(-1, 3, 4)       # [node, axis, child]
+    hi = W[:, 12:24].reshape(-1, 3, 4)
+    ch = W[:, 24:28].view(np.int32)
+    cnt = W[:, 28:29].view(np.int32)[:, 0]
+    seen_leaf = np.zeros(n, np.int32)
+    seen = np.zeros(W.shape[0], np.int32)
+    seen[0] = 1
+    stack = [0]
+    while stack:
+        w = stack.pop()
+        valid = ch[w] != np.iinfo(np.int32).min
+        assert valid.sum() == cnt[w] and 2 <= cnt[w] <= 4
+        for k in np.nonzero(valid)[0]:
+            c = ch[w, k]
+            if c < 0:
+                seen_leaf[~c] += 1
+                assert np.array_equal(lo[w, :, k], boxes[~c, :3]) and np.array_equal(hi[w, :, k], boxes[~c, 3:])
+            else:
+                seen[c] += 1
+                cv = ch[c] != np.iinfo(np.int32).min
+                assert np.all(lo[w, :, k][:, None] <= lo[c][:, cv]) and np.all(hi[w, :, k][:, None] >= hi[c][:, cv])
+                stack.append(c)
+    assert np.all(seen_leaf == 1) and np.all(seen == 1)
