@@ -8,8 +8,10 @@ namespace irgs {
 namespace {
 
 
+// 6 resident blocks per SM (24 warps) keep the latency-bound walk fed; the
+// k-buffers of 6 blocks take 192 KB of shared memory.
 template <int K, int FB, bool WARP>
-__global__ void __launch_bounds__(trace_threads<K>()) k_trace_forward(SceneView S, const float* __restrict__ ro,
+__global__ void __launch_bounds__(trace_threads<K>(), K <= 16 ? 6 : 4) k_trace_forward(SceneView S, const float* __restrict__ ro,
                                                                const float* __restrict__ rd, int64_t R,
                                                                TraceParams P, float* __restrict__ feat,
                                                                float* __restrict__ depth, float* __restrict__ opac,
