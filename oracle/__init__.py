@@ -103,14 +103,18 @@ def _load():
                                       P, P, P, P, P, P, P, P, P, C.c_int]
     lib.oracle_shade.restype = C.c_int
     lib.oracle_shade.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P, P, P, P, P, C.c_int64,
-                                 P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P,
+                                 P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P,
                                  P, P, P, P, P, P, C.c_int]
+    lib.oracle_shade_grad.restype = C.c_int
+    lib.oracle_shade_grad.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P, P, P, P, P, C.c_int64,
+                                      P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P,
+                                      P, P, P, P, P, P, P, P, P, P, C.c_int]
     lib.oracle_splitmix64.restype = C.c_uint64
     lib.oracle_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
     lib.oracle_env_lookup.restype = None
     lib.oracle_env_lookup.argtypes = [P, C.c_int32, C.c_int32, P, P]
     lib.oracle_sample_dirs.restype = C.c_int
-    lib.oracle_sample_dirs.argtypes = [P, P, P, C.c_int64, C.c_int32, C.c_int32, C.c_uint64, P, P]
+    lib.oracle_sample_dirs.argtypes = [P, P, P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P]
     lib.oracle_num_threads.restype = C.c_int
     lib.oracle_num_threads.argtypes = [C.c_int]
     _lib = lib
@@ -195,17 +199,28 @@ def trace_grad(scene, ray_o, ray_d, g_feat, g_depth, g_opacity, params: Params =
     return out
 
 
-def shade(scene, x, nrm, albedo, rough, wo, env, n_diffuse: int, n_spec: int, seed: int,
-          params: Params, margins: Margins | None = Margins(), n_threads: int = 0,
-          point_ids=None):
-    """Monte Carlo rendering equation per point (Eq. 13-15). Returns a dict
-    with rgb [P,3], vis [P], ind [P,3] and flags [P]. `point_ids` gives the
-    point number that keys each point's random stream (default 0..P-1)."""
-    lib = _load()
+MODE_SPLIT, MODE_UNIFORM = 0, 1
+
+
+def _shade_inputs(scene, x, nrm, albedo, rough, wo, env):
     means, quats, scales, opacity, feats = _surfel_arrays(scene)
     x, nrm, albedo, wo = (_f32(a).reshape(-1, 3) for a in (x, nrm, albedo, wo))
     rough = _f32(rough).reshape(-1)
     env = _f32(env)
+    return (means, quats, scales, opacity, feats), x, nrm, albedo, rough, wo, env
+
+
+def shade(scene, x, nrm, albedo, rough, wo, env, n_diffuse: int, n_spec: int, seed: int,
+          params: Params, margins: Margins | None = Margins(), n_threads: int = 0,
+          point_ids=None, mode: int = MODE_SPLIT):
+    """Monte Carlo rendering equation per point (Eq. 13-15). Returns a dict
+    with rgb [P,3], vis [P], ind [P,3] and flags [P]. `point_ids` gives the
+    point number that keys each point's random stream (default 0..P-1).
+    mode MODE_SPLIT: n_diffuse cosine + n_spec GGX samples per point;
+    MODE_UNIFORM: n_diffuse stratified uniform hemisphere samples (Eq. 15)."""
+    lib = _load()
+    (means, quats, scales, opacity, feats), x, nrm, albedo, rough, wo, env = _shade_inputs(
+        scene, x, nrm, albedo, rough, wo, env)
     H, W = env.shape[0], env.shape[1]
     Pn, n, F = x.shape[0], means.shape[0], feats.shape[1]
     out = {"rgb": np.zeros((Pn, 3)), "vis": np.zeros(Pn), "ind": np.zeros((Pn, 3)),
@@ -215,12 +230,41 @@ def shade(scene, x, nrm, albedo, rough, wo, env, n_diffuse: int, n_spec: int, se
     pid = None if point_ids is None else np.ascontiguousarray(point_ids, np.int64).reshape(Pn)
     rc = lib.oracle_shade(_ptr(means), _ptr(quats), _ptr(scales), _ptr(opacity), _ptr(feats), n, F,
                           _ptr(x), _ptr(nrm), _ptr(albedo), _ptr(rough), _ptr(wo), Pn, _ptr(env),
-                          H, W, int(n_diffuse), int(n_spec), C.c_uint64(seed & (2**64 - 1)),
+                          H, W, int(n_diffuse), int(n_spec), int(mode), C.c_uint64(seed & (2**64 - 1)),
                           _ptr(pid), C.byref(p), C.byref(m) if m is not None else None,
                           _ptr(out["rgb"]), _ptr(out["vis"]), _ptr(out["ind"]), _ptr(out["flags"]),
                           int(n_threads))
     if rc != 0:
         raise ValueError("oracle_shade rejected its arguments")
+    return out
+
+
+def shade_grad(scene, x, nrm, albedo, rough, wo, env, n_diffuse: int, n_spec: int, seed: int,
+               params: Params, g_rgb, n_threads: int = 0, point_ids=None, mode: int = MODE_SPLIT,
+               want_env: bool = True):
+    """Gradient of sum(g_rgb * rgb) with the sample directions held fixed:
+    dict of float64 arrays albedo [P,3], rough [P], env [H,W,3] and the
+    surfel gradients means/quats/scales/opacity/features."""
+    lib = _load()
+    (means, quats, scales, opacity, feats), x, nrm, albedo, rough, wo, env = _shade_inputs(
+        scene, x, nrm, albedo, rough, wo, env)
+    H, W = env.shape[0], env.shape[1]
+    Pn, n, F = x.shape[0], means.shape[0], feats.shape[1]
+    g = _f32(g_rgb).reshape(Pn, 3)
+    out = {"albedo": np.zeros((Pn, 3)), "rough": np.zeros(Pn),
+           "env": np.zeros((H, W, 3)) if want_env else None,
+           "means": np.zeros((n, 3)), "quats": np.zeros((n, 4)), "scales": np.zeros((n, 2)),
+           "opacity": np.zeros(n), "features": np.zeros((n, F))}
+    p = params.c()
+    pid = None if point_ids is None else np.ascontiguousarray(point_ids, np.int64).reshape(Pn)
+    rc = lib.oracle_shade_grad(_ptr(means), _ptr(quats), _ptr(scales), _ptr(opacity), _ptr(feats), n, F,
+                               _ptr(x), _ptr(nrm), _ptr(albedo), _ptr(rough), _ptr(wo), Pn, _ptr(env),
+                               H, W, int(n_diffuse), int(n_spec), int(mode), C.c_uint64(seed & (2**64 - 1)),
+                               _ptr(pid), C.byref(p), _ptr(g), _ptr(out["albedo"]), _ptr(out["rough"]),
+                               _ptr(out["env"]), _ptr(out["means"]), _ptr(out["quats"]), _ptr(out["scales"]),
+                               _ptr(out["opacity"]), _ptr(out["features"]), int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_shade_grad rejected its arguments")
     return out
 
 
@@ -241,7 +285,7 @@ def env_lookup(env, dirs):
     return out
 
 
-def sample_dirs(nrm, wo, rough, n_diffuse: int, n_spec: int, seed: int):
+def sample_dirs(nrm, wo, rough, n_diffuse: int, n_spec: int, seed: int, mode: int = 0):
     """Incident directions [P,S,3] and validity [P,S] of the shading samples."""
     lib = _load()
     nrm, wo = _f32(nrm).reshape(-1, 3), _f32(wo).reshape(-1, 3)
@@ -249,6 +293,6 @@ def sample_dirs(nrm, wo, rough, n_diffuse: int, n_spec: int, seed: int):
     Pn, S = nrm.shape[0], n_diffuse + n_spec
     dirs = np.zeros((Pn, S, 3))
     valid = np.zeros((Pn, S), np.int32)
-    lib.oracle_sample_dirs(_ptr(nrm), _ptr(wo), _ptr(rough), Pn, n_diffuse, n_spec,
+    lib.oracle_sample_dirs(_ptr(nrm), _ptr(wo), _ptr(rough), Pn, n_diffuse, n_spec, int(mode),
                            C.c_uint64(seed & (2**64 - 1)), _ptr(dirs), _ptr(valid))
     return dirs, valid.astype(bool)

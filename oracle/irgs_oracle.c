@@ -348,6 +348,71 @@ static void quat_backward(const surfel64* S, const double gu[3], const double gv
     for (int k = 0; k < 4; ++k) gq[k] = (gh[k] - qh[k] * proj) / S->qn;
 }
 
+/* Backward of one ray's blend (hits[0..nc), transmittance before each hit
+ * in Tl, final transmittance Tfin) for upstream gradients gC (feat_count
+ * channels), gD (depth), gO (opacity); adds into the surfel gradients. The
+ * suffix S_j = sum over later hits of T_m alpha_m v_m is accumulated by a
+ * reverse loop over the hit list. */
+static void ray_backward(const surfel64* s, const hit64* hits, int64_t nc, const double* Tl, double Tfin,
+                         const float* feats, int32_t F_total, const oracle_params* P, const double o[3],
+                         const double d[3], const double* gC, double gD, double gO, double* g_means,
+                         double* g_quats, double* g_scales, double* g_opacity, double* g_feats)
+{
+    const int FC = P->feat_count;
+    double S = 0.0;
+    for (int64_t j = nc - 1; j >= 0; --j) {
+        const surfel64* Sf = &s[hits[j].id];
+        cand64 c;
+        intersect(Sf, o, d, &c);
+        const float* f = feats + hits[j].id * (int64_t)F_total + P->feat_offset;
+        double a = hits[j].alpha, T = Tl[j];
+        double v = gD * c.tau;
+        for (int k = 0; k < FC; ++k) v += gC[k] * (double)f[k];
+        /* dL/dalpha_j: direct term, later hits through T, final opacity */
+        double dA = T * v - (S - gO * Tfin) / (1.0 - a);
+        S += T * a * v;
+        int64_t id = hits[j].id;
+        /* features and direct depth term */
+        for (int k = 0; k < FC; ++k) {
+            double g = T * a * gC[k];
+#pragma omp atomic
+            g_feats[id * F_total + P->feat_offset + k] += g;
+        }
+        double g_tau = T * a * gD;
+        int clamped = c.alpha_raw >= P->alpha_max;
+        double g_o = clamped ? 0.0 : dA * c.G;
+        double g_rho2 = clamped ? 0.0 : dA * (-0.5 * a);
+        double gu = g_rho2 * 2.0 * c.u, gv = g_rho2 * 2.0 * c.v;
+        /* u = e.t_u/s_u, v = e.t_v/s_v, e = o + tau d - mu, tau = n.(mu-o)/(n.d) */
+        double ge[3], gmu[3], gn[3], gtu[3], gtv[3];
+        for (int k = 0; k < 3; ++k) ge[k] = gu * Sf->tu[k] / Sf->su + gv * Sf->tv[k] / Sf->sv;
+        double gtau_tot = g_tau + dot3(ge, d);
+        for (int k = 0; k < 3; ++k) {
+            gmu[k] = -ge[k] + gtau_tot * Sf->n[k] / c.den;
+            gn[k] = -gtau_tot * c.e[k] / c.den;
+            gtu[k] = gu * c.e[k] / Sf->su;
+            gtv[k] = gv * c.e[k] / Sf->sv;
+        }
+        double gsu = -gu * c.u / Sf->su, gsv = -gv * c.v / Sf->sv;
+        double gq[4];
+        quat_backward(Sf, gtu, gtv, gn, gq);
+        for (int k = 0; k < 3; ++k) {
+#pragma omp atomic
+            g_means[id * 3 + k] += gmu[k];
+        }
+        for (int k = 0; k < 4; ++k) {
+#pragma omp atomic
+            g_quats[id * 4 + k] += gq[k];
+        }
+#pragma omp atomic
+        g_scales[id * 2] += gsu;
+#pragma omp atomic
+        g_scales[id * 2 + 1] += gsv;
+#pragma omp atomic
+        g_opacity[id] += g_o;
+    }
+}
+
 /* Gradient of L = sum_r g_feat[r].feat[r] + g_depth[r] depth[r] + g_opac[r] opacity[r]
  * with respect to means [N,3], quats [N,4], scales [N,2], opacity [N] and
  * features [N,F_total] (only the blended channels are non-zero). FP64
@@ -360,7 +425,7 @@ int oracle_trace_grad(const float* means, const float* quats, const float* scale
                       double* g_means, double* g_quats, double* g_scales, double* g_opacity,
                       double* g_feats, int n_threads)
 {
-    if (n < 0 || R < 0 || !P) return -1;
+    if (n < 0 || R < 0 || !P || P->feat_count > 64) return -1;
     if (P->feat_count > 0 && (P->feat_offset < 0 || P->feat_offset + P->feat_count > F_total)) return -1;
     surfel64* s = (surfel64*)malloc(sizeof(surfel64) * (size_t)(n > 0 ? n : 1));
     if (!s) return -1;
@@ -389,60 +454,10 @@ int oracle_trace_grad(const float* means, const float* quats, const float* scale
                 int64_t nh = collect_hits(s, n, o, d, P, NULL, hits, NULL, NULL);
                 double D, Tfin;
                 int64_t nc = composite(hits, nh, feats, F_total, P, C, &D, &Tfin, Tl);
-                const float* gC = g_feat + r * FC;
-                double gD = g_depth[r], gO = g_opac[r];
-                double S = 0.0;   /* sum over later hits of T_m alpha_m v_m */
-                for (int64_t j = nc - 1; j >= 0; --j) {
-                    const surfel64* Sf = &s[hits[j].id];
-                    cand64 c;
-                    intersect(Sf, o, d, &c);
-                    const float* f = feats + hits[j].id * (int64_t)F_total + P->feat_offset;
-                    double a = hits[j].alpha, T = Tl[j];
-                    double v = gD * c.tau;
-                    for (int k = 0; k < FC; ++k) v += (double)gC[k] * (double)f[k];
-                    /* dL/dalpha_j: direct term, later hits through T, final opacity */
-                    double dA = T * v - (S - gO * Tfin) / (1.0 - a);
-                    S += T * a * v;
-                    int64_t id = hits[j].id;
-                    /* features and direct depth term */
-                    for (int k = 0; k < FC; ++k) {
-                        double g = T * a * (double)gC[k];
-#pragma omp atomic
-                        g_feats[id * F_total + P->feat_offset + k] += g;
-                    }
-                    double g_tau = T * a * gD;
-                    int clamped = c.alpha_raw >= P->alpha_max;
-                    double g_o = clamped ? 0.0 : dA * c.G;
-                    double g_rho2 = clamped ? 0.0 : dA * (-0.5 * a);
-                    double gu = g_rho2 * 2.0 * c.u, gv = g_rho2 * 2.0 * c.v;
-                    /* u = e.t_u/s_u, v = e.t_v/s_v, e = o + tau d - mu, tau = n.(mu-o)/(n.d) */
-                    double ge[3], gmu[3], gn[3], gtu[3], gtv[3];
-                    for (int k = 0; k < 3; ++k) ge[k] = gu * Sf->tu[k] / Sf->su + gv * Sf->tv[k] / Sf->sv;
-                    double gtau_tot = g_tau + dot3(ge, d);
-                    for (int k = 0; k < 3; ++k) {
-                        gmu[k] = -ge[k] + gtau_tot * Sf->n[k] / c.den;
-                        gn[k] = -gtau_tot * c.e[k] / c.den;
-                        gtu[k] = gu * c.e[k] / Sf->su;
-                        gtv[k] = gv * c.e[k] / Sf->sv;
-                    }
-                    double gsu = -gu * c.u / Sf->su, gsv = -gv * c.v / Sf->sv;
-                    double gq[4];
-                    quat_backward(Sf, gtu, gtv, gn, gq);
-                    for (int k = 0; k < 3; ++k) {
-#pragma omp atomic
-                        g_means[id * 3 + k] += gmu[k];
-                    }
-                    for (int k = 0; k < 4; ++k) {
-#pragma omp atomic
-                        g_quats[id * 4 + k] += gq[k];
-                    }
-#pragma omp atomic
-                    g_scales[id * 2] += gsu;
-#pragma omp atomic
-                    g_scales[id * 2 + 1] += gsv;
-#pragma omp atomic
-                    g_opacity[id] += g_o;
-                }
+                double gC[64];
+                for (int k = 0; k < FC; ++k) gC[k] = (double)g_feat[r * FC + k];
+                ray_backward(s, hits, nc, Tl, Tfin, feats, F_total, P, o, d, gC, g_depth[r], g_opac[r],
+                             g_means, g_quats, g_scales, g_opacity, g_feats);
             }
         }
         free(hits); free(Tl); free(C);
@@ -509,7 +524,8 @@ void oracle_sample_ggx_h(const double n[3], double alpha_g, double u1, double u2
 /* Equirectangular lookup, z up: phi = atan2(y,x), theta = acos(z);
  * texel coords ((phi+pi)/2pi W - 0.5, theta/pi H - 0.5); bilinear with
  * wrap in phi and clamp in theta. env is [H, W, 3]. */
-void oracle_env_lookup(const float* env, int32_t H, int32_t W, const double w[3], double out[3])
+/* Texels and bilinear weights of the equirectangular lookup of direction w. */
+static void env_texels(int32_t H, int32_t W, const double w[3], int64_t idx[4], double wt[4])
 {
     double len = sqrt(dot3(w, w));
     double z = w[2] / len;
@@ -529,10 +545,20 @@ void oracle_env_lookup(const float* env, int32_t H, int32_t W, const double w[3]
     if (y0 > H - 1) y0 = H - 1;
     if (y1 < 0) y1 = 0;
     if (y1 > H - 1) y1 = H - 1;
+    idx[0] = y0 * W + x0; wt[0] = (1 - fy) * (1 - fx);
+    idx[1] = y0 * W + x1; wt[1] = (1 - fy) * fx;
+    idx[2] = y1 * W + x0; wt[2] = fy * (1 - fx);
+    idx[3] = y1 * W + x1; wt[3] = fy * fx;
+}
+
+void oracle_env_lookup(const float* env, int32_t H, int32_t W, const double w[3], double out[3])
+{
+    int64_t idx[4];
+    double wt[4];
+    env_texels(H, W, w, idx, wt);
     for (int c = 0; c < 3; ++c) {
-        double v00 = env[(y0 * W + x0) * 3 + c], v01 = env[(y0 * W + x1) * 3 + c];
-        double v10 = env[(y1 * W + x0) * 3 + c], v11 = env[(y1 * W + x1) * 3 + c];
-        out[c] = (1 - fy) * ((1 - fx) * v00 + fx * v01) + fy * ((1 - fx) * v10 + fx * v11);
+        out[c] = 0.0;
+        for (int t = 0; t < 4; ++t) out[c] += wt[t] * env[idx[t] * 3 + c];
     }
 }
 
@@ -542,14 +568,30 @@ static void normalize3(double v[3])
     v[0] /= l; v[1] /= l; v[2] /= l;
 }
 
-/* Incident direction of sample s of point p (diffuse samples first) and,
- * for a GGX sample, its half vector. Returns 0 for a GGX sample that leaves
- * below the horizon (no contribution, still counted). */
-static int sample_direction(uint64_t seed, int64_t p, int64_t s, int64_t S, int32_t n_diffuse,
+/* Sampling modes of the rendering-equation estimate. */
+enum { MODE_SPLIT = 0, MODE_UNIFORM = 1 };
+
+/* Incident direction of sample s of point p. MODE_SPLIT: samples below
+ * n_diffuse are cosine-weighted, the rest GGX (half vector in h); returns 0
+ * for a GGX sample that leaves below the horizon (no contribution, still
+ * counted). MODE_UNIFORM: stratified uniform hemisphere (Eq. 15), stratum s
+ * of S in cos(theta); returns 0 for a direction on the horizon. */
+static int sample_direction(uint64_t seed, int64_t p, int64_t s, int64_t S, int32_t n_diffuse, int mode,
                             const double n[3], const double wo[3], double rough,
                             double wi[3], double h[3])
 {
     double u1 = uniform01(seed, p, s, S, 0), u2 = uniform01(seed, p, s, S, 1);
+    if (mode == MODE_UNIFORM) {
+        double b1[3], b2[3];
+        onb(n, b1, b2);
+        double z = ((double)s + u1) / (double)S;
+        double rr = sqrt(1.0 - z * z > 0.0 ? 1.0 - z * z : 0.0), ph = 2.0 * OR_PI * u2;
+        for (int k = 0; k < 3; ++k) wi[k] = rr * cos(ph) * b1[k] + rr * sin(ph) * b2[k] + z * n[k];
+        normalize3(wi);
+        for (int k = 0; k < 3; ++k) h[k] = wi[k] + wo[k];
+        normalize3(h);
+        return z > 0.0;
+    }
     if (s < n_diffuse) {
         oracle_sample_cosine(n, u1, u2, wi);
         normalize3(wi);
@@ -567,7 +609,7 @@ static int sample_direction(uint64_t seed, int64_t p, int64_t s, int64_t S, int3
 /* Directions only (for sampler tests): [P, S, 3] incident directions and a
  * validity mask [P, S]. */
 int oracle_sample_dirs(const float* nrm, const float* wo_in, const float* rough, int64_t P,
-                       int32_t n_diffuse, int32_t n_spec, uint64_t seed, double* out_dirs,
+                       int32_t n_diffuse, int32_t n_spec, int32_t mode, uint64_t seed, double* out_dirs,
                        int32_t* out_valid)
 {
     int64_t S = (int64_t)n_diffuse + n_spec;
@@ -578,7 +620,7 @@ int oracle_sample_dirs(const float* nrm, const float* wo_in, const float* rough,
         if (dot3(n, wo) <= 0.0) { n[0] = -n[0]; n[1] = -n[1]; n[2] = -n[2]; }
         for (int64_t s = 0; s < S; ++s) {
             double wi[3], h[3];
-            int ok = sample_direction(seed, p, s, S, n_diffuse, n, wo, rough[p], wi, h);
+            int ok = sample_direction(seed, p, s, S, n_diffuse, mode, n, wo, rough[p], wi, h);
             for (int k = 0; k < 3; ++k) out_dirs[(p * S + s) * 3 + k] = wi[k];
             out_valid[p * S + s] = ok;
         }
@@ -586,30 +628,167 @@ int oracle_sample_dirs(const float* nrm, const float* wo_in, const float* rough,
     return 0;
 }
 
-/* Split-lobe Monte Carlo estimate of Eq. 15 per G-buffer point:
+/* Specular lobe pieces at one direction (Eq. 4 with the readings above):
+ * F (Schlick, on w_o.h), the two Schlick-GGX G1 factors, D (GGX) and the
+ * logarithmic derivative d ln(D G) / d roughness. */
+typedef struct { double F, G1i, G1o, D, dlnf_dr; } spec_terms;
+
+static spec_terms spec_eval(double r, double ni, double no, double nh, double oh)
+{
+    const double F0 = 0.04;
+    spec_terms t;
+    double ag = r * r, a2 = ag * ag, kk = 0.5 * ag;
+    double q = nh * nh * (a2 - 1.0) + 1.0;
+    t.F = F0 + (1.0 - F0) * pow(1.0 - oh, 5.0);
+    t.G1i = ni / (ni * (1.0 - kk) + kk);
+    t.G1o = no / (no * (1.0 - kk) + kk);
+    t.D = a2 / (OR_PI * q * q);
+    double dlnD = 4.0 / r - 8.0 * r * r * r * nh * nh / q;
+    double dlnGi = -r * (1.0 - ni) / (ni * (1.0 - kk) + kk);
+    double dlnGo = -r * (1.0 - no) / (no * (1.0 - kk) + kk);
+    t.dlnf_dr = dlnD + dlnGi + dlnGo;
+    return t;
+}
+
+/* Upstream gradients and outputs of the surfel/env gradient of shading. */
+typedef struct {
+    const float* g_rgb;     /* [P,3] */
+    double* g_albedo;       /* [P,3] */
+    double* g_rough;        /* [P]   */
+    double* g_env;          /* [H,W,3] or NULL */
+    double *g_means, *g_quats, *g_scales, *g_opacity, *g_feats;
+} shade_grads;
+
+/* Monte Carlo estimate of Eq. 15 at one point, and optionally its gradient.
+ * MODE_SPLIT (split-lobe importance sampling):
  *   diffuse lobe, cosine samples: f_d L_i cos / pdf = a L_i;
  *   specular lobe, GGX samples:   f_s L_i cos / pdf = F G (w_o.h) L_i / ((n.w_o)(n.h));
- *   L_i = V L_dir + L_ind with (L_ind, 1 - V) = Trace(x, w_i) (Eq. 13-14).
- * Outputs rgb [P,3]; vis [P] and ind [P,3] are the means of V and L_ind over
- * the cosine samples (NULL to skip); flags [P] ORs the traced rays' flags.
- * point_ids [P] (or NULL for 0..P-1) is the point number that keys the
- * random stream of each point. */
+ * MODE_UNIFORM (Eq. 15): 2 pi / N sum (f_d + f_s) L_i (w_i.n).
+ * L_i = V L_dir + L_ind with (L_ind, 1 - V) = Trace(x, w_i) (Eq. 13-14).
+ * The gradient keeps the sample directions fixed: d/dr goes through f_s
+ * only (d ln(D G)/dr), and each traced ray receives dL/dL_ind = g and
+ * dL/dO = -g.L_dir. */
+static void shade_point(const surfel64* s, int64_t n, const float* feats, int32_t F_total,
+                        const oracle_params* P, const oracle_margins* M, hit64* hits, near64* nears, double* Tl,
+                        const double x[3], const double n_raw[3], const double wo_raw[3], const double a[3],
+                        double r, int64_t key, uint64_t seed, int32_t n_diffuse, int32_t n_spec, int mode,
+                        const float* env, int32_t H, int32_t W, double rgb[3], double* vis, double ind[3],
+                        uint32_t* flags, const shade_grads* G, int64_t p)
+{
+    double nn[3] = {n_raw[0], n_raw[1], n_raw[2]}, wo[3] = {wo_raw[0], wo_raw[1], wo_raw[2]};
+    normalize3(nn); normalize3(wo);
+    if (dot3(nn, wo) <= 0.0) { nn[0] = -nn[0]; nn[1] = -nn[1]; nn[2] = -nn[2]; }
+    const int64_t S = (int64_t)n_diffuse + n_spec;
+    double no = dot3(nn, wo);
+    double acc[3] = {0, 0, 0}, sum_v = 0.0, sum_i[3] = {0, 0, 0};
+    double ga[3] = {0, 0, 0}, gr = 0.0;
+    int64_t n_aux = 0;
+    uint32_t fl = 0;
+    double grgb[3] = {0, 0, 0};
+    if (G) for (int k = 0; k < 3; ++k) grgb[k] = G->g_rgb[3 * p + k];
+    for (int64_t sI = 0; sI < S; ++sI) {
+        double wi[3], h[3];
+        if (!sample_direction(seed, key, sI, S, n_diffuse, mode, nn, wo, r, wi, h)) continue;
+        int64_t nnr = 0;
+        int64_t nh = collect_hits(s, n, x, wi, P, M, hits, nears, &nnr);
+        double C[3], D, Tfin;
+        int64_t nc = composite(hits, nh, feats, F_total, P, C, &D, &Tfin, Tl);
+        if (M) fl |= resolve_flags(hits, nh, nc, nears, nnr, P, M, Tl, Tfin);
+        double V = Tfin;                       /* 1 - V = traced opacity */
+        double Ld[3];
+        oracle_env_lookup(env, H, W, wi, Ld);
+        double Li[3] = {V * Ld[0] + C[0], V * Ld[1] + C[1], V * Ld[2] + C[2]};
+        /* per-channel factor w_c multiplying L_i in the estimate, and d w_c / d r */
+        double wc[3], dwc_dr[3] = {0, 0, 0}, dwc_da[3] = {0, 0, 0};
+        int aux = 0;
+        if (mode == MODE_UNIFORM) {
+            double ni = dot3(nn, wi), nh_ = dot3(nn, h), oh = dot3(wo, h);
+            spec_terms t = spec_eval(r, ni, no, nh_, oh);
+            double fs_cos = t.D * t.F * t.G1i * t.G1o / (4.0 * no);     /* f_s (w_i.n) */
+            for (int k = 0; k < 3; ++k) {
+                wc[k] = (2.0 * a[k] * ni + 2.0 * OR_PI * fs_cos) / (double)S;
+                dwc_da[k] = 2.0 * ni / (double)S;
+                dwc_dr[k] = 2.0 * OR_PI * fs_cos * t.dlnf_dr / (double)S;
+            }
+            aux = 1;
+        } else if (sI < n_diffuse) {
+            for (int k = 0; k < 3; ++k) { wc[k] = a[k] / n_diffuse; dwc_da[k] = 1.0 / n_diffuse; }
+            aux = 1;
+        } else {
+            double oh = dot3(wo, h), nh_ = dot3(nn, h), ni = dot3(nn, wi);
+            spec_terms t = spec_eval(r, ni, no, nh_, oh);
+            double w = t.F * t.G1i * t.G1o * oh / (no * nh_);
+            for (int k = 0; k < 3; ++k) { wc[k] = w / n_spec; dwc_dr[k] = w / n_spec * t.dlnf_dr; }
+        }
+        for (int k = 0; k < 3; ++k) acc[k] += wc[k] * Li[k];
+        if (aux) {
+            for (int k = 0; k < 3; ++k) sum_i[k] += C[k];
+            sum_v += V;
+            ++n_aux;
+        }
+        if (G) {
+            double gL[3], gO = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                gL[k] = grgb[k] * wc[k];
+                ga[k] += grgb[k] * dwc_da[k] * Li[k];
+                gr += grgb[k] * dwc_dr[k] * Li[k];
+                gO -= gL[k] * Ld[k];
+            }
+            if (G->g_env) {
+                int64_t idx[4];
+                double wt[4];
+                env_texels(H, W, wi, idx, wt);
+                for (int t4 = 0; t4 < 4; ++t4)
+                    for (int k = 0; k < 3; ++k) {
+#pragma omp atomic
+                        G->g_env[idx[t4] * 3 + k] += wt[t4] * gL[k] * V;
+                    }
+            }
+            ray_backward(s, hits, nc, Tl, Tfin, feats, F_total, P, x, wi, gL, 0.0, gO, G->g_means, G->g_quats,
+                         G->g_scales, G->g_opacity, G->g_feats);
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        rgb[k] = acc[k];
+        ind[k] = n_aux > 0 ? sum_i[k] / (double)n_aux : 0.0;
+    }
+    *vis = n_aux > 0 ? sum_v / (double)n_aux : 0.0;
+    *flags = fl;
+    if (G) {
+        for (int k = 0; k < 3; ++k) G->g_albedo[3 * p + k] = ga[k];
+        G->g_rough[p] = gr;
+    }
+}
+
+static int shade_args_ok(int64_t n, int64_t Pn, const oracle_params* P, int32_t F_total, int32_t n_diffuse,
+                         int32_t n_spec, int32_t mode)
+{
+    if (n < 0 || Pn < 0 || !P || P->feat_count != 3) return 0;
+    if (P->feat_offset < 0 || P->feat_offset + 3 > F_total) return 0;
+    if (n_diffuse < 0 || n_spec < 0 || n_diffuse + n_spec <= 0) return 0;
+    if (mode != MODE_SPLIT && mode != MODE_UNIFORM) return 0;
+    if (mode == MODE_UNIFORM && n_spec != 0) return 0;
+    return 1;
+}
+
+/* Monte Carlo rendering equation per G-buffer point (see shade_point).
+ * Outputs rgb [P,3]; vis [P] and ind [P,3] are the means of V and L_ind
+ * over the cosine samples (split mode) or over all samples (uniform mode),
+ * NULL to skip; flags [P] ORs the traced rays' flags. point_ids [P] (or NULL
+ * for 0..P-1) is the point number that keys the random stream of a point. */
 int oracle_shade(const float* means, const float* quats, const float* scales, const float* opacity,
                  const float* feats, int64_t n, int32_t F_total,
                  const float* x_in, const float* n_in, const float* albedo, const float* rough,
                  const float* wo_in, int64_t Pn, const float* env, int32_t env_h, int32_t env_w,
-                 int32_t n_diffuse, int32_t n_spec, uint64_t seed, const int64_t* point_ids,
+                 int32_t n_diffuse, int32_t n_spec, int32_t mode, uint64_t seed, const int64_t* point_ids,
                  const oracle_params* P, const oracle_margins* M, double* out_rgb, double* out_vis,
                  double* out_ind, uint32_t* out_flags, int n_threads)
 {
-    if (n < 0 || Pn < 0 || !P || P->feat_count != 3) return -1;
-    if (P->feat_offset < 0 || P->feat_offset + 3 > F_total) return -1;
+    if (!shade_args_ok(n, Pn, P, F_total, n_diffuse, n_spec, mode)) return -1;
     surfel64* s = (surfel64*)malloc(sizeof(surfel64) * (size_t)(n > 0 ? n : 1));
     if (!s) return -1;
     load_surfels(means, quats, scales, opacity, n, P->alpha_min, s);
     nthreads_set(n_threads);
-    const int64_t S = (int64_t)n_diffuse + n_spec;
-    const double F0 = 0.04;
     int err = 0;
 #pragma omp parallel
     {
@@ -623,49 +802,75 @@ int oracle_shade(const float* means, const float* quats, const float* scales, co
 #pragma omp for schedule(dynamic, 1)
             for (int64_t p = 0; p < Pn; ++p) {
                 double x[3] = {x_in[3 * p], x_in[3 * p + 1], x_in[3 * p + 2]};
-                double nn[3] = {n_in[3 * p], n_in[3 * p + 1], n_in[3 * p + 2]};
+                double nr[3] = {n_in[3 * p], n_in[3 * p + 1], n_in[3 * p + 2]};
                 double wo[3] = {wo_in[3 * p], wo_in[3 * p + 1], wo_in[3 * p + 2]};
-                normalize3(nn); normalize3(wo);
-                if (dot3(nn, wo) <= 0.0) { nn[0] = -nn[0]; nn[1] = -nn[1]; nn[2] = -nn[2]; }
                 double a[3] = {albedo[3 * p], albedo[3 * p + 1], albedo[3 * p + 2]};
-                double r = rough[p];
-                double ag = r * r, kk = ag * 0.5;
-                double sum_d[3] = {0, 0, 0}, sum_s[3] = {0, 0, 0}, sum_v = 0.0, sum_i[3] = {0, 0, 0};
-                uint32_t fl = 0;
-                double no = dot3(nn, wo);
-                for (int64_t sI = 0; sI < S; ++sI) {
-                    double wi[3], h[3];
-                    int64_t key = point_ids ? point_ids[p] : p;
-                    if (!sample_direction(seed, key, sI, S, n_diffuse, nn, wo, r, wi, h)) continue;
-                    int64_t nnr = 0;
-                    int64_t nh = collect_hits(s, n, x, wi, P, M, hits, nears, &nnr);
-                    double C[3], D, Tfin;
-                    int64_t nc = composite(hits, nh, feats, F_total, P, C, &D, &Tfin, Tl);
-                    if (M) fl |= resolve_flags(hits, nh, nc, nears, nnr, P, M, Tl, Tfin);
-                    double V = Tfin;                       /* 1 - V = traced opacity */
-                    double Ld[3];
-                    oracle_env_lookup(env, env_h, env_w, wi, Ld);
-                    double Li[3] = {V * Ld[0] + C[0], V * Ld[1] + C[1], V * Ld[2] + C[2]};
-                    if (sI < n_diffuse) {
-                        for (int k = 0; k < 3; ++k) { sum_d[k] += a[k] * Li[k]; sum_i[k] += C[k]; }
-                        sum_v += V;
-                    } else {
-                        double oh = dot3(wo, h), nh_ = dot3(nn, h), ni = dot3(nn, wi);
-                        double Fr = F0 + (1.0 - F0) * pow(1.0 - oh, 5.0);
-                        double G1i = ni / (ni * (1.0 - kk) + kk);
-                        double G1o = no / (no * (1.0 - kk) + kk);
-                        double wgt = Fr * G1i * G1o * oh / (no * nh_);
-                        for (int k = 0; k < 3; ++k) sum_s[k] += wgt * Li[k];
-                    }
-                }
+                double rgb[3], vis, ind[3];
+                uint32_t fl;
+                shade_point(s, n, feats, F_total, P, M, hits, nears, Tl, x, nr, wo, a, rough[p],
+                            point_ids ? point_ids[p] : p, seed, n_diffuse, n_spec, mode, env, env_h, env_w, rgb,
+                            &vis, ind, &fl, NULL, p);
                 for (int k = 0; k < 3; ++k) {
-                    double cd = n_diffuse > 0 ? sum_d[k] / n_diffuse : 0.0;
-                    double cs = n_spec > 0 ? sum_s[k] / n_spec : 0.0;
-                    out_rgb[3 * p + k] = cd + cs;
-                    if (out_ind) out_ind[3 * p + k] = n_diffuse > 0 ? sum_i[k] / n_diffuse : 0.0;
+                    out_rgb[3 * p + k] = rgb[k];
+                    if (out_ind) out_ind[3 * p + k] = ind[k];
                 }
-                if (out_vis) out_vis[p] = n_diffuse > 0 ? sum_v / n_diffuse : 0.0;
+                if (out_vis) out_vis[p] = vis;
                 if (out_flags) out_flags[p] = fl;
+            }
+        }
+        free(hits); free(nears); free(Tl);
+    }
+    free(s);
+    return err ? -1 : 0;
+}
+
+/* Gradient of L = sum_p g_rgb[p].rgb[p] with the sample directions fixed:
+ * outputs (overwritten) g_albedo [P,3], g_rough [P], g_env [H,W,3] (or
+ * NULL), and the surfel gradients through the traced rays: g_means [N,3],
+ * g_quats [N,4], g_scales [N,2], g_opacity [N], g_feats [N,F] (radiance
+ * channels only). */
+int oracle_shade_grad(const float* means, const float* quats, const float* scales, const float* opacity,
+                      const float* feats, int64_t n, int32_t F_total,
+                      const float* x_in, const float* n_in, const float* albedo, const float* rough,
+                      const float* wo_in, int64_t Pn, const float* env, int32_t env_h, int32_t env_w,
+                      int32_t n_diffuse, int32_t n_spec, int32_t mode, uint64_t seed, const int64_t* point_ids,
+                      const oracle_params* P, const float* g_rgb, double* g_albedo, double* g_rough,
+                      double* g_env, double* g_means, double* g_quats, double* g_scales, double* g_opacity,
+                      double* g_feats, int n_threads)
+{
+    if (!shade_args_ok(n, Pn, P, F_total, n_diffuse, n_spec, mode)) return -1;
+    surfel64* s = (surfel64*)malloc(sizeof(surfel64) * (size_t)(n > 0 ? n : 1));
+    if (!s) return -1;
+    load_surfels(means, quats, scales, opacity, n, P->alpha_min, s);
+    memset(g_means, 0, sizeof(double) * 3 * (size_t)n);
+    memset(g_quats, 0, sizeof(double) * 4 * (size_t)n);
+    memset(g_scales, 0, sizeof(double) * 2 * (size_t)n);
+    memset(g_opacity, 0, sizeof(double) * (size_t)n);
+    memset(g_feats, 0, sizeof(double) * (size_t)F_total * (size_t)n);
+    if (g_env) memset(g_env, 0, sizeof(double) * 3 * (size_t)env_h * (size_t)env_w);
+    shade_grads G = {g_rgb, g_albedo, g_rough, g_env, g_means, g_quats, g_scales, g_opacity, g_feats};
+    nthreads_set(n_threads);
+    int err = 0;
+#pragma omp parallel
+    {
+        hit64* hits = (hit64*)malloc(sizeof(hit64) * (size_t)(n > 0 ? n : 1));
+        near64* nears = (near64*)malloc(sizeof(near64) * (size_t)(n > 0 ? n : 1));
+        double* Tl = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        if (!hits || !nears || !Tl) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t p = 0; p < Pn; ++p) {
+                double x[3] = {x_in[3 * p], x_in[3 * p + 1], x_in[3 * p + 2]};
+                double nr[3] = {n_in[3 * p], n_in[3 * p + 1], n_in[3 * p + 2]};
+                double wo[3] = {wo_in[3 * p], wo_in[3 * p + 1], wo_in[3 * p + 2]};
+                double a[3] = {albedo[3 * p], albedo[3 * p + 1], albedo[3 * p + 2]};
+                double rgb[3], vis, ind[3];
+                uint32_t fl;
+                shade_point(s, n, feats, F_total, P, NULL, hits, nears, Tl, x, nr, wo, a, rough[p],
+                            point_ids ? point_ids[p] : p, seed, n_diffuse, n_spec, mode, env, env_h, env_w, rgb,
+                            &vis, ind, &fl, &G, p);
             }
         }
         free(hits); free(nears); free(Tl);
