@@ -84,6 +84,10 @@ typedef struct {
  * forces the warp-coherent walk. Setting both is invalid. */
 #define IRGS_FLAG_PER_THREAD 1u
 #define IRGS_FLAG_WARP 2u
+/* Shading only (irgs_shade_mc / irgs_shade_mc_backward): the stratified
+ * uniform hemisphere estimator of Eq. 15 instead of split-lobe importance
+ * sampling; n_spec must be 0. Rejected by the trace entry points. */
+#define IRGS_FLAG_UNIFORM 4u
 
 /* Human-readable name of a status code (static storage). */
 const char* irgs_status_string(irgs_status status);
@@ -222,15 +226,20 @@ irgs_status irgs_trace_backward(irgs_scene scene, const float* ray_o, const floa
 /*
  * Monte Carlo rendering equation at G-buffer points (Eq. 3, 15), with the
  * dielectric BRDF of Eq. 4 and incident light L_i = V L_dir + L_ind whose
- * (L_ind, 1 - V) come from tracing (x, w_i) (Eq. 13-14). Incident directions
- * are importance sampled per lobe (supplementary "Composited scene details"):
- * n_diffuse cosine-weighted samples estimate the diffuse term (estimate
- * a L_i each) and n_spec GGX samples (alpha_g = roughness^2) estimate the
- * specular term (estimate F G (w_o.h) L_i / ((n.w_o)(n.h)) each; a sample
- * below the horizon adds 0 but counts). D is GGX, F is Schlick with F0 = 0.04
- * on (w_o.h), G is separable Schlick-GGX with k = alpha_g / 2. The normal is
- * flipped when n.w_o <= 0. Random numbers: SplitMix64 stream of `seed`,
- * output index (p * (n_diffuse + n_spec) + s) * 2 + dim, top 24 bits.
+ * (L_ind, 1 - V) come from tracing (x, w_i) (Eq. 13-14). D is GGX
+ * (alpha_g = roughness^2), F is Schlick with F0 = 0.04 on (w_o.h), G is
+ * separable Schlick-GGX with k = alpha_g / 2; the normal is flipped when
+ * n.w_o <= 0. Two estimators:
+ *  - default, split-lobe importance sampling (supplementary "Composited
+ *    scene details"): n_diffuse cosine-weighted samples estimate the diffuse
+ *    term (a L_i each) and n_spec GGX samples estimate the specular term
+ *    (F G (w_o.h) L_i / ((n.w_o)(n.h)) each; a sample below the horizon adds
+ *    0 but counts);
+ *  - IRGS_FLAG_UNIFORM (n_spec = 0): S = n_diffuse directions uniform over
+ *    the hemisphere, stratified in cos(theta) (sample s has cos(theta) =
+ *    (s + u1) / S), estimate 2 pi / S sum (f_d + f_s) L_i (w_i.n) (Eq. 15).
+ * Random numbers: SplitMix64 stream of `seed`, output index
+ * (p * (n_diffuse + n_spec) + s) * 2 + dim, top 24 bits.
  *   x, n, albedo, wo : [n_points, 3]; rough : [n_points].
  *   env   : [env_h, env_w, 3] equirectangular radiance, z up, row = polar
  *           angle acos(z), column = azimuth atan2(y, x) from -pi; bilinear,
@@ -238,7 +247,8 @@ irgs_status irgs_trace_backward(irgs_scene scene, const float* ray_o, const floa
  *   params: the secondary-ray trace; feat_count must be 3 (radiance c of the
  *           surfels, Sec. 3.3) and t_min > 0 is the self-hit offset.
  *   out_rgb [n_points, 3]; out_vis [n_points] and out_ind [n_points, 3]
- *           (means of V and L_ind over the cosine samples) may be NULL.
+ *           (means of V and L_ind over the cosine samples, or over all
+ *           samples in the uniform mode) may be NULL.
  * Results do not depend on how points are batched into calls.
  */
 irgs_status irgs_shade_mc(irgs_scene scene, const float* x, const float* n, const float* albedo,
@@ -246,6 +256,30 @@ irgs_status irgs_shade_mc(irgs_scene scene, const float* x, const float* n, cons
                           int32_t env_h, int32_t env_w, int32_t n_diffuse, int32_t n_spec,
                           uint64_t seed, const irgs_trace_params* params, float* out_rgb,
                           float* out_vis, float* out_ind, void* stream);
+
+/*
+ * Gradient of irgs_shade_mc (same scene, points, sample counts, seed and
+ * params) for the loss L = sum_p g_rgb[p].rgb[p], with the sample directions
+ * held fixed (their dependence on roughness and on the normal is not
+ * differentiated: the estimate of the gradient stays unbiased for the
+ * roughness). Each sample's secondary ray is traced again and replayed
+ * backwards (as irgs_trace_backward, with upstream gradients dL/dL_ind and
+ * dL/dO = -dL/dL_ind . L_dir). All outputs are ADDED to:
+ *   g_albedo [n_points, 3], g_rough [n_points] (required);
+ *   g_env [env_h, env_w, 3] (bilinear taps, atomics; NULL to skip);
+ *   g_means [n,3], g_quats [n,4] (raw quaternion), g_scales [n,2],
+ *   g_opacity [n], g_features [n, num_features] (channels feat_offset ..
+ *   feat_offset + 2 only) (all required).
+ * Points whose g_rgb row is zero are skipped. Needs scratch of 64 bytes per
+ * surfel from the stream-ordered allocator (IRGS_ERR_OOM if it fails).
+ */
+irgs_status irgs_shade_mc_backward(irgs_scene scene, const float* x, const float* n, const float* albedo,
+                                   const float* rough, const float* wo, int64_t n_points, const float* env,
+                                   int32_t env_h, int32_t env_w, int32_t n_diffuse, int32_t n_spec,
+                                   uint64_t seed, const irgs_trace_params* params, const float* g_rgb,
+                                   float* g_albedo, float* g_rough, float* g_env, float* g_means,
+                                   float* g_quats, float* g_scales, float* g_opacity, float* g_features,
+                                   void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: several resident scenes, many requests per persistent launch. */

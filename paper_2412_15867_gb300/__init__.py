@@ -21,11 +21,12 @@ from . import _lib
 from ._lib import IrgsError
 
 __all__ = ["TraceParams", "Scene", "trace", "trace_forward", "trace_backward", "shade_mc",
-           "IrgsError", "library_path"]
+           "shade_mc_backward", "shade", "IrgsError", "library_path"]
 
 
 FLAG_PER_THREAD = 1   # one traversal stack per ray
 FLAG_WARP = 2         # one traversal stack per warp of 32 rays
+FLAG_UNIFORM = 4      # shading: stratified uniform hemisphere estimator (Eq. 15)
 
 
 def library_path() -> str:
@@ -281,10 +282,14 @@ def trace(scene: Scene, ray_o, ray_d, params: TraceParams = TraceParams()):
                           ray_o, ray_d, scene, params)
 
 
-def shade_mc(scene: Scene, x, n, albedo, rough, wo, env, n_diffuse: int, n_spec: int, seed: int,
-             params: TraceParams, want_aux: bool = False, out=None):
-    """Monte Carlo rendering equation per G-buffer point (Eq. 13-15).
-    Returns rgb [P,3] (and, with want_aux, vis [P] and ind [P,3])."""
+def _shade_params(params: TraceParams, mode: str) -> TraceParams:
+    if mode not in ("split", "uniform"):
+        raise ValueError("mode must be 'split' or 'uniform'")
+    flags = params.flags & ~FLAG_UNIFORM
+    return params.with_(flags=flags | (FLAG_UNIFORM if mode == "uniform" else 0))
+
+
+def _gbuffer(x, n, albedo, rough, wo, env):
     x = _dev_f32(x, "x", 3).reshape(-1, 3)
     P = x.shape[0]
     n = _dev_f32(n, "n", 3).reshape(P, 3)
@@ -294,13 +299,24 @@ def shade_mc(scene: Scene, x, n, albedo, rough, wo, env, n_diffuse: int, n_spec:
     env = _dev_f32(env, "env", 3)
     if env.dim() != 3:
         raise ValueError("env must be [H, W, 3]")
+    return x, n, albedo, rough, wo, env
+
+
+def shade_mc(scene: Scene, x, n, albedo, rough, wo, env, n_diffuse: int, n_spec: int, seed: int,
+             params: TraceParams, want_aux: bool = False, out=None, mode: str = "split"):
+    """Monte Carlo rendering equation per G-buffer point (Eq. 13-15).
+    mode "split": n_diffuse cosine + n_spec GGX samples; "uniform":
+    n_diffuse stratified uniform directions (n_spec = 0).
+    Returns rgb [P,3] (and, with want_aux, vis [P] and ind [P,3])."""
+    x, n, albedo, rough, wo, env = _gbuffer(x, n, albedo, rough, wo, env)
+    P = x.shape[0]
     dev = scene.device
     if out is None:
         out = {"rgb": torch.empty((P, 3), device=dev)}
         if want_aux:
             out["vis"] = torch.empty(P, device=dev)
             out["ind"] = torch.empty((P, 3), device=dev)
-    p = params.c()
+    p = _shade_params(params, mode).c()
     with torch.cuda.device(dev):
         _lib.check(_lib.lib().irgs_shade_mc(
             scene.handle, _ptr(x), _ptr(n), _ptr(albedo), _ptr(rough), _ptr(wo), P, _ptr(env),
@@ -308,3 +324,63 @@ def shade_mc(scene: Scene, x, n, albedo, rough, wo, env, n_diffuse: int, n_spec:
             C.c_uint64(int(seed) & (2 ** 64 - 1)), C.byref(p), _ptr(out["rgb"]), _ptr(out.get("vis")),
             _ptr(out.get("ind")), _stream(dev)), "irgs_shade_mc")
     return out
+
+
+def shade_mc_backward(scene: Scene, x, n, albedo, rough, wo, env, n_diffuse: int, n_spec: int, seed: int,
+                      params: TraceParams, g_rgb, mode: str = "split", want_env: bool = True, grads=None):
+    """Gradient of shade_mc for L = sum g_rgb . rgb with the sample directions
+    held fixed. Returns (or accumulates into) a dict albedo [P,3], rough [P],
+    env [H,W,3] (if want_env) and the user-order surfel gradients
+    means/quats/scales/opacity/features."""
+    x, n, albedo, rough, wo, env = _gbuffer(x, n, albedo, rough, wo, env)
+    P = x.shape[0]
+    dev = scene.device
+    ns = scene.n
+    if grads is None:
+        grads = {"albedo": torch.zeros((P, 3), device=dev), "rough": torch.zeros(P, device=dev),
+                 "means": torch.zeros((ns, 3), device=dev), "quats": torch.zeros((ns, 4), device=dev),
+                 "scales": torch.zeros((ns, 2), device=dev), "opacity": torch.zeros(ns, device=dev),
+                 "features": torch.zeros((ns, scene.num_features), device=dev)}
+        if want_env:
+            grads["env"] = torch.zeros(env.shape, device=dev)
+    g = _dev_f32(g_rgb, "g_rgb", 3).reshape(P, 3)
+    p = _shade_params(params, mode).c()
+    with torch.cuda.device(dev):
+        _lib.check(_lib.lib().irgs_shade_mc_backward(
+            scene.handle, _ptr(x), _ptr(n), _ptr(albedo), _ptr(rough), _ptr(wo), P, _ptr(env),
+            int(env.shape[0]), int(env.shape[1]), int(n_diffuse), int(n_spec),
+            C.c_uint64(int(seed) & (2 ** 64 - 1)), C.byref(p), _ptr(g), _ptr(grads["albedo"]),
+            _ptr(grads["rough"]), _ptr(grads.get("env")), _ptr(grads["means"]), _ptr(grads["quats"]),
+            _ptr(grads["scales"]), _ptr(grads["opacity"]),
+            _ptr(grads["features"]) if scene.num_features else None, _stream(dev)),
+            "irgs_shade_mc_backward")
+    return grads
+
+
+class _ShadeFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, means, quats, scales, opacity, features, albedo, rough, env, x, n, wo, scene, cfg):
+        nd, ns, seed, params, mode = cfg
+        out = shade_mc(scene, x, n, albedo, rough, wo, env, nd, ns, seed, params, mode=mode)
+        ctx.scene, ctx.cfg = scene, cfg
+        ctx.save_for_backward(albedo, rough, env, x, n, wo)
+        return out["rgb"]
+
+    @staticmethod
+    def backward(ctx, g_rgb):
+        albedo, rough, env, x, n, wo = ctx.saved_tensors
+        nd, ns, seed, params, mode = ctx.cfg
+        scene = ctx.scene
+        g = shade_mc_backward(scene, x, n, albedo, rough, wo, env, nd, ns, seed, params, g_rgb.contiguous(),
+                              mode=mode, want_env=ctx.needs_input_grad[7])
+        return (g["means"], g["quats"], g["scales"], g["opacity"].reshape(scene.opacity.shape),
+                g["features"], g["albedo"].reshape(albedo.shape), g["rough"].reshape(rough.shape),
+                g.get("env"), None, None, None, None, None)
+
+
+def shade(scene: Scene, x, n, albedo, rough, wo, env, n_diffuse: int, n_spec: int, seed: int,
+          params: TraceParams, mode: str = "split"):
+    """Differentiable shade_mc: returns rgb [P,3]; gradients flow to albedo,
+    rough, env and the tensors the scene was built from (directions fixed)."""
+    return _ShadeFn.apply(scene.means, scene.quats, scene.scales, scene.opacity, scene.features, albedo, rough,
+                          env, x, n, wo, scene, (n_diffuse, n_spec, seed, params, mode))

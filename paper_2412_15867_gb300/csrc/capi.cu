@@ -20,7 +20,7 @@ namespace {
 bool finite(float x) { return isfinite(x) != 0; }
 
 // Validate trace parameters against a scene. t_max may be +inf.
-irgs_status check_params(const irgs_scene sc, const irgs_trace_params* p) {
+irgs_status check_params(const irgs_scene sc, const irgs_trace_params* p, bool shading = false) {
     if (p == nullptr) return IRGS_ERR_INVALID_ARG;
     if (!irgs::k_supported(p->k)) return IRGS_ERR_UNSUPPORTED;
     if (!finite(p->alpha_min) || !(p->alpha_min >= sc->alpha_min) || !(p->alpha_min > 0.f))
@@ -33,13 +33,29 @@ irgs_status check_params(const irgs_scene sc, const irgs_trace_params* p) {
     if (p->feat_count < 0 || p->feat_count > IRGS_MAX_FEATURES) return IRGS_ERR_INVALID_ARG;
     if (p->feat_count > 0 && (p->feat_offset < 0 || p->feat_offset + p->feat_count > sc->F))
         return IRGS_ERR_INVALID_ARG;
-    if ((p->flags & ~(IRGS_FLAG_PER_THREAD | IRGS_FLAG_WARP)) != 0u) return IRGS_ERR_INVALID_ARG;
+    const uint32_t allowed = IRGS_FLAG_PER_THREAD | IRGS_FLAG_WARP | (shading ? IRGS_FLAG_UNIFORM : 0u);
+    if ((p->flags & ~allowed) != 0u) return IRGS_ERR_INVALID_ARG;
     if ((p->flags & IRGS_FLAG_PER_THREAD) && (p->flags & IRGS_FLAG_WARP)) return IRGS_ERR_INVALID_ARG;
     return IRGS_OK;
 }
 
 irgs_status use_device(const irgs_scene sc) {
     return cudaSetDevice(sc->device) == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+}
+
+irgs_status check_shade(const irgs_scene sc, const irgs_trace_params* params, int64_t n_points, const float* env,
+                        int32_t env_h, int32_t env_w, int32_t n_diffuse, int32_t n_spec) {
+    if (sc == nullptr || n_points < 0) return IRGS_ERR_INVALID_ARG;
+    irgs_status s = check_params(sc, params, true);
+    if (s != IRGS_OK) return s;
+    if (params->k != 8 && params->k != 16) return IRGS_ERR_UNSUPPORTED;
+    if (params->feat_count != 3 || !(params->t_min > 0.f)) return IRGS_ERR_INVALID_ARG;
+    if (n_diffuse < 0 || n_spec < 0 || n_diffuse + n_spec <= 0 || n_diffuse + n_spec > (1 << 24))
+        return IRGS_ERR_INVALID_ARG;
+    if ((params->flags & IRGS_FLAG_UNIFORM) && n_spec != 0) return IRGS_ERR_INVALID_ARG;
+    if (env_h <= 0 || env_w <= 0 || !env) return IRGS_ERR_INVALID_ARG;
+    if (n_points >= (int64_t)UINT32_MAX * 4) return IRGS_ERR_INVALID_ARG;
+    return IRGS_OK;
 }
 
 }  // namespace
@@ -210,19 +226,30 @@ irgs_status irgs_shade_mc(irgs_scene sc, const float* x, const float* n, const f
                           const float* wo, int64_t n_points, const float* env, int32_t env_h, int32_t env_w,
                           int32_t n_diffuse, int32_t n_spec, uint64_t seed, const irgs_trace_params* params,
                           float* out_rgb, float* out_vis, float* out_ind, void* stream) {
-    if (sc == nullptr || n_points < 0) return IRGS_ERR_INVALID_ARG;
-    irgs_status s = check_params(sc, params);
+    irgs_status s = check_shade(sc, params, n_points, env, env_h, env_w, n_diffuse, n_spec);
     if (s != IRGS_OK) return s;
-    if (params->k != 8 && params->k != 16) return IRGS_ERR_UNSUPPORTED;
-    if (params->feat_count != 3 || !(params->t_min > 0.f)) return IRGS_ERR_INVALID_ARG;
-    if (n_diffuse < 0 || n_spec < 0 || n_diffuse + n_spec <= 0 || n_diffuse + n_spec > (1 << 24))
-        return IRGS_ERR_INVALID_ARG;
-    if (env_h <= 0 || env_w <= 0 || !env) return IRGS_ERR_INVALID_ARG;
     if (n_points > 0 && (!x || !n || !albedo || !rough || !wo || !out_rgb)) return IRGS_ERR_INVALID_ARG;
-    if (n_points >= (int64_t)UINT32_MAX * 4) return IRGS_ERR_INVALID_ARG;
     if ((s = use_device(sc)) != IRGS_OK) return s;
     return irgs::launch_shade_mc(sc->view(), x, n, albedo, rough, wo, n_points, env, env_h, env_w, n_diffuse, n_spec,
                                  seed, *params, out_rgb, out_vis, out_ind, static_cast<cudaStream_t>(stream));
+}
+
+irgs_status irgs_shade_mc_backward(irgs_scene sc, const float* x, const float* n, const float* albedo,
+                                   const float* rough, const float* wo, int64_t n_points, const float* env,
+                                   int32_t env_h, int32_t env_w, int32_t n_diffuse, int32_t n_spec, uint64_t seed,
+                                   const irgs_trace_params* params, const float* g_rgb, float* g_albedo,
+                                   float* g_rough, float* g_env, float* g_means, float* g_quats, float* g_scales,
+                                   float* g_opacity, float* g_features, void* stream) {
+    irgs_status s = check_shade(sc, params, n_points, env, env_h, env_w, n_diffuse, n_spec);
+    if (s != IRGS_OK) return s;
+    if (n_points > 0 && (!x || !n || !albedo || !rough || !wo || !g_rgb || !g_albedo || !g_rough))
+        return IRGS_ERR_INVALID_ARG;
+    if (sc->n > 0 && (!g_means || !g_quats || !g_scales || !g_opacity || !g_features)) return IRGS_ERR_INVALID_ARG;
+    if ((s = use_device(sc)) != IRGS_OK) return s;
+    return irgs::launch_shade_mc_backward(sc->view(), sc->perm, x, n, albedo, rough, wo, n_points, env, env_h, env_w,
+                                          n_diffuse, n_spec, seed, *params, g_rgb, g_albedo, g_rough, g_env, g_means,
+                                          g_quats, g_scales, g_opacity, g_features,
+                                          static_cast<cudaStream_t>(stream));
 }
 
 irgs_status irgs_build_lbvh_noalloc(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,

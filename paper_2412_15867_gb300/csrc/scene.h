@@ -83,6 +83,12 @@ irgs_status launch_shade_mc(const SceneView& sv, const float* x, const float* n,
                             int32_t W, int32_t n_diffuse, int32_t n_spec, uint64_t seed,
                             const irgs_trace_params& p, float* rgb, float* vis, float* ind,
                             cudaStream_t st);
+irgs_status launch_shade_mc_backward(const SceneView& sv, const int32_t* perm, const float* x, const float* n,
+                                     const float* albedo, const float* rough, const float* wo, int64_t P,
+                                     const float* env, int32_t H, int32_t W, int32_t n_diffuse, int32_t n_spec,
+                                     uint64_t seed, const irgs_trace_params& p, const float* g_rgb,
+                                     float* g_albedo, float* g_rough, float* g_env, float* g_means, float* g_quats,
+                                     float* g_scales, float* g_opacity, float* g_features, cudaStream_t st);
 
 // k-buffer sizes that are compiled in
 inline bool k_supported(int k) { return k == 1 || k == 4 || k == 8 || k == 16 || k == 32; }

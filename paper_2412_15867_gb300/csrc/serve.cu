@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kServeThreads) k_serve(ServeArgs A) {
                     ShadeSums sums;
                     shade_point_warp<kServeK, false>(S, mk3(g[0], g[1], g[2]), mk3(g[3], g[4], g[5]),
                                                      mk3(g[10], g[11], g[12]), mk3(g[6], g[7], g[8]), g[9],
-                                                     (uint64_t)p, job.n_diffuse, job.n_spec, job.seed, job.env,
+                                                     (uint64_t)p, job.n_diffuse, job.n_spec, kModeSplit, job.seed, job.env,
                                                      job.env_h, job.env_w, A.shade, sums);
                     out[0] = sums.rgb[0]; out[1] = sums.rgb[1]; out[2] = sums.rgb[2];
                 }

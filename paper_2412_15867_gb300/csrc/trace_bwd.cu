@@ -1,112 +1,22 @@
-// Backward trace kernel: the gradient of Trace(r_o, r_d) (IRGS Eq. 8; the
-// tracer is differentiable, Sec. 3.3) with respect to every surfel parameter.
-//
-// Each ray's k-buffer march is replayed exactly (same traversal, same
-// arithmetic), capped at the forward's hit count, and no hit list is stored.
-// For the loss L = g_C.C + g_D D + g_O O and hits j = 0..J-1 in depth order,
-// with w_j = T_j alpha_j and v_j = g_C.f_j + g_D tau_j:
-//   dL/dalpha_j = T_j v_j - (S_j - g_O T_J) / (1 - alpha_j),
-//   S_j = sum_{m>j} w_m v_m = g_C.(C - C_<=j) + g_D (D - D_<=j),
-// where C_<=j, D_<=j are the running sums up to and including hit j (the
-// suffix comes from the forward's totals minus the replayed prefix). The
-// chain then runs alpha -> (o, rho^2) -> (u, v) -> (p - mu, tau) -> (mu, t_u,
-// t_v, n, s_u, s_v) -> raw quaternion (Eq. 6-7 and the rotation of the unit
-// quaternion). Per-hit gradients are summed across the lanes of a warp that
-// hold the same surfel, added with vector atomics into a Morton-ordered
-// scratch accumulator (stream-ordered allocation for the call), and finally
-// added once into the caller's user-order arrays.
+// Backward trace kernel: replays each ray's march (trace_bwd.cuh) and adds
+// the surfel gradients into the caller's user-order arrays.
 #include <cuda_runtime.h>
 
 #include "scene.h"
 #include "trace.cuh"
+#include "trace_bwd.cuh"
 
 namespace irgs {
 namespace {
 
 constexpr int kBwdThreads = 128;
 
-// Per-surfel gradient row in the Morton-ordered scratch accumulator (16-byte
-// aligned, added with vector atomics):
-//   [g_mu.x g_mu.y g_mu.z g_o] [g_q.w g_q.x g_q.y g_q.z] [g_su g_sv 0 0]
-//   [g_f 0..3] [g_f 4..7] ...   (the traced channels, padded to 4)
-template <int FB>
-struct GradRow {
-    static constexpr int FB4 = (FB + 3) / 4 * 4;
-    static constexpr int N = 12 + FB4;   // floats per row
-    float v[N];
-};
-
-// Add row g for Morton slot m: lanes of the warp holding the same slot are
-// summed first (match mask + per-lane rows in shared memory), then the
-// first of them adds the row with N/4 float4 atomics.
-template <int FB>
-__device__ __forceinline__ void accumulate_row(const GradRow<FB>& g, int32_t m, float* __restrict__ acc_rows,
-                                               float* rows /* [32][N+1] this warp */) {
-    constexpr int N = GradRow<FB>::N;
-    const unsigned active = __activemask();
-    const unsigned peers = __match_any_sync(active, m);
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    float acc[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) acc[k] = g.v[k];
-    if (peers != (1u << lane)) {
-        float* mine = rows + lane * (N + 1);
-#pragma unroll
-        for (int k = 0; k < N; ++k) mine[k] = g.v[k];
-        __syncwarp(peers);
-        if (lane == leader) {
-            unsigned rest = peers & ~(1u << lane);
-            while (rest) {
-                const int l = __ffs(rest) - 1;
-                rest &= rest - 1;
-                const float* other = rows + l * (N + 1);
-#pragma unroll
-                for (int k = 0; k < N; ++k) acc[k] += other[k];
-            }
-        }
-        __syncwarp(peers);
-    }
-    if (lane != leader) return;
-    float4* dst = reinterpret_cast<float4*>(acc_rows + (int64_t)m * N);
-#pragma unroll
-    for (int q = 0; q < N / 4; ++q)
-        atomicAdd(dst + q, make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]));
-}
-
-// Add the Morton-ordered rows into the caller's user-order gradients
-// (each user index is touched by exactly one thread: no atomics).
-template <int FB>
-__global__ void k_grad_scatter(const int32_t* __restrict__ perm, int64_t n, const float* __restrict__ acc_rows,
-                               int fc, int F, int off, float* __restrict__ g_means, float* __restrict__ g_quats,
-                               float* __restrict__ g_scales, float* __restrict__ g_opac, float* __restrict__ g_feat) {
-    constexpr int N = GradRow<FB>::N;
-    const int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (m >= n) return;
-    const int64_t u = perm[m];
-    const float4* r = reinterpret_cast<const float4*>(acc_rows + m * N);
-    const float4 a = r[0], q = r[1], sc = r[2];
-    g_means[3 * u] += a.x;
-    g_means[3 * u + 1] += a.y;
-    g_means[3 * u + 2] += a.z;
-    g_opac[u] += a.w;
-    g_quats[4 * u] += q.x;
-    g_quats[4 * u + 1] += q.y;
-    g_quats[4 * u + 2] += q.z;
-    g_quats[4 * u + 3] += q.w;
-    g_scales[2 * u] += sc.x;
-    g_scales[2 * u + 1] += sc.y;
-    const float* f = acc_rows + m * N + 12;
-    for (int c = 0; c < fc; ++c) g_feat[u * F + off + c] += f[c];
-}
-
 template <int K, int FB, bool WARP>
 __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
     SceneView S, const float* __restrict__ ro, const float* __restrict__ rd, int64_t R, TraceParams P,
     const float* __restrict__ out_feat, const float* __restrict__ out_depth, const float* __restrict__ out_opac,
     const int32_t* __restrict__ out_nhits, const float* __restrict__ g_featv, const float* __restrict__ g_depthv,
-    const float* __restrict__ g_opacv,
-    float* __restrict__ acc_rows) {
+    const float* __restrict__ g_opacv, float* __restrict__ acc_rows) {
     constexpr int N = GradRow<FB>::N;
     static_assert(kBwdThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
     __shared__ float rows_all[kBwdThreads * (N + 1)];
@@ -119,108 +29,16 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
     const int64_t q = live ? r : 0;   // lanes without work follow the warp with a dummy ray
     const Ray ray = make_ray(mk3(ro[3 * q], ro[3 * q + 1], ro[3 * q + 2]),
                              mk3(rd[3 * q], rd[3 * q + 1], rd[3 * q + 2]));
-    float gC[FB], Cf[FB], Cacc[FB];
+    float gC[FB], Cf[FB];
 #pragma unroll
     for (int c = 0; c < FB; ++c) {
         gC[c] = c < P.fc ? g_featv[q * P.fc + c] : 0.f;
         Cf[c] = c < P.fc ? out_feat[q * P.fc + c] : 0.f;
-        Cacc[c] = 0.f;
     }
     const float gD = g_depthv != nullptr ? g_depthv[q] : 0.f;
     const float gO = g_opacv != nullptr ? g_opacv[q] : 0.f;
-    const float Df = out_depth[q];
-    const float Tfin = 1.0f - out_opac[q];
-    float Dacc = 0.f, T = 1.f;
-    int nh = 0;
-    uint64_t last_key = depth_key(P.t_min, 0.f);
-    int32_t last_m = INT32_MAX;
-    KBuffer<K, kBwdThreads> kb;
-    kb.bind();
-    bool ok = true, done = !live;
-    while (WARP ? __any_sync(kFullWarp, !done) : !done) {
-        if (WARP)
-            ok &= collect_round_warp(S, ray, P, last_key, last_m, kb, !done);
-        else
-            ok &= collect_round(S, ray, P, last_key, last_m, kb);
-        if (done) continue;
-        for (int j = 0; j < kb.cnt && nh < nh_total; ++j) {
-            {
-                const float a = kb.a_at(j);
-                const int32_t m = kb.m_at(j);
-                const float tau = key_depth(kb.key_at(j));
-                const float w = __fmul_rn(T, a);
-                const float* f = S.feat + (int64_t)m * S.F + P.off;
-                float fv[FB];
-                float v = __fmul_rn(gD, tau), Sj = 0.f;
-#pragma unroll
-                for (int c = 0; c < FB; ++c) {
-                    fv[c] = c < P.fc ? __ldg(f + c) : 0.f;
-                    Cacc[c] = c < P.fc ? __fmaf_rn(w, fv[c], Cacc[c]) : 0.f;
-                    v = fmaf(gC[c], fv[c], v);
-                    Sj = fmaf(gC[c], Cf[c] - Cacc[c], Sj);
-                }
-                Dacc = __fmaf_rn(w, tau, Dacc);
-                Sj = fmaf(gD, Df - Dacc, Sj);
-                const float dA = T * v - (Sj - gO * Tfin) / (1.0f - a);
-
-                // recompute the hit geometry (bitwise identical to the march)
-                const float4* Rp = S.rec + (int64_t)m * kRecF4;
-                const float4 r0 = ldg4(Rp), r1 = ldg4(Rp + 1), r2 = ldg4(Rp + 2), r3 = ldg4(Rp + 3);
-                float kh, kl, a2;
-                HitGeom hg;
-                surfel_hit<true>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a2, &hg);
-                const float2 sc = __ldg(&S.scale[m]);
-                const float4 q = __ldg(&S.q_raw[m]);
-
-                GradRow<FB> gv;
-                const bool clamped = hg.a_raw >= P.alpha_max;
-                const float g_o = clamped ? 0.f : dA * hg.G;
-                const float g_rho2 = clamped ? 0.f : -0.5f * dA * a;
-                const float gu = 2.f * g_rho2 * hg.u, gvv = 2.f * g_rho2 * hg.v;
-                const f3 tus = mk3(r1.x, r1.y, r1.z), tvs = mk3(r2.x, r2.y, r2.z), nn = mk3(r3.x, r3.y, r3.z);
-                const f3 ge = add3(mul3(tus, gu), mul3(tvs, gvv));
-                const float gtau = w * gD + dot3(ge, ray.d);
-                const float s_t = gtau / hg.den;
-                const f3 gmu = sub3(mul3(nn, s_t), ge);
-                const f3 gn = mul3(hg.e, -s_t);
-                const f3 gtu = mul3(hg.e, gu / sc.x);
-                const f3 gtv = mul3(hg.e, gvv / sc.y);
-                // raw quaternion: derivative of the rotation columns, then of q / |q|
-                const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-                const float qw = q.x / qn, qx = q.y / qn, qy = q.z / qn, qz = q.w / qn;
-                const float hw = 2.f * (qz * gtu.y - qy * gtu.z - qz * gtv.x + qx * gtv.z + qy * gn.x - qx * gn.y);
-                const float hx = 2.f * (qy * gtu.y + qz * gtu.z + qy * gtv.x - 2.f * qx * gtv.y + qw * gtv.z +
-                                        qz * gn.x - qw * gn.y - 2.f * qx * gn.z);
-                const float hy = 2.f * (-2.f * qy * gtu.x + qx * gtu.y - qw * gtu.z + qx * gtv.x + qz * gtv.z +
-                                        qw * gn.x + qz * gn.y - 2.f * qy * gn.z);
-                const float hz = 2.f * (-2.f * qz * gtu.x + qw * gtu.y + qx * gtu.z - qw * gtv.x - 2.f * qz * gtv.y +
-                                        qy * gtv.z + qx * gn.x + qy * gn.y);
-                const float proj = qw * hw + qx * hx + qy * hy + qz * hz;
-                gv.v[0] = gmu.x; gv.v[1] = gmu.y; gv.v[2] = gmu.z;
-                gv.v[3] = g_o;
-                gv.v[4] = (hw - qw * proj) / qn;
-                gv.v[5] = (hx - qx * proj) / qn;
-                gv.v[6] = (hy - qy * proj) / qn;
-                gv.v[7] = (hz - qz * proj) / qn;
-                gv.v[8] = -gu * hg.u / sc.x;
-                gv.v[9] = -gvv * hg.v / sc.y;
-                gv.v[10] = 0.f;
-                gv.v[11] = 0.f;
-#pragma unroll
-                for (int c = 0; c < GradRow<FB>::FB4; ++c) gv.v[12 + c] = c < FB ? w * gC[c] : 0.f;
-                accumulate_row<FB>(gv, m, acc_rows, rows);
-
-                T = __fmul_rn(T, __fsub_rn(1.0f, a));
-                ++nh;
-            }
-        }
-        if (nh >= nh_total || kb.cnt < K) {
-            done = true;
-        } else {
-            last_key = kb.tail_key;
-            last_m = kb.tail_m;
-        }
-    }
+    const bool ok = march_backward<K, FB, WARP>(S, ray, P, live, nh_total, Cf, out_depth[q], 1.0f - out_opac[q], gC,
+                                                gD, gO, acc_rows, rows);
     if (live && !ok) atomicOr(S.status, kErrStackOverflow);
 }
 
