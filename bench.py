@@ -68,10 +68,16 @@ def parse():
     ap.add_argument("--res", type=int, default=800)
     ap.add_argument("--surfels", type=int, default=300_000)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--saved-hits", type=int, default=96,
+                    help="hit-list length the forward saves for the backward (0: the backward replays)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
+    ap.add_argument("--mc-only", action="store_true", help="run only the Monte Carlo shading leg")
+    ap.add_argument("--mc-points", type=int, default=640_000)
+    ap.add_argument("--mc-surfels", type=int, default=1_000_000)
+    ap.add_argument("--mc-reps", type=int, default=2)
     ap.add_argument("--serve-seconds", type=float, default=8.0)
     ap.add_argument("--serve-warmup", type=float, default=2.0)
     ap.add_argument("--cpu-rays", type=int, default=20480, help="oracle sample for cpu_baseline")
@@ -135,16 +141,19 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
-def algorithmic_flops(nh, k, n_surfels, F, backward=False):
+def algorithmic_flops(nh, k, n_surfels, F, backward=False, saved_hits=0):
     """Algorithmic FP32 flops of one launch: per composited hit one Eq. 6-7
     intersection (45, exp counted as 1) plus blending (2(F+2) + 3); per
     k-buffer round one root-to-leaf descent of ceil(log2 N) nodes with two
-    slab tests (40). The backward costs about 3x per hit."""
+    slab tests (40). The backward costs about 3x per hit and descends only
+    for rays whose hit list was not saved (n_hits > saved_hits)."""
     import torch
     nh = nh.to(torch.float64)
     rounds = torch.floor(nh / k) + 1
     per_hit = 45 + 2 * (F + 2) + 3
     depth = math.ceil(math.log2(max(n_surfels, 2)))
+    if backward and saved_hits > 0:
+        rounds = torch.where(nh > saved_hits, rounds, torch.zeros_like(rounds))
     f = nh * per_hit * (3 if backward else 1) + rounds * depth * 40
     return float(f.sum())
 
@@ -182,7 +191,9 @@ def run_ours(args):
     gf, gd, go = T(gf_np), T(gd_np), T(go_np)
     p = irgs.TraceParams(k=16, feat_count=F)
     scene = irgs.Scene(*surf, alpha_min=1 / 255)
-    out = irgs.trace_forward(scene, ro, rd, p)
+    # the forward keeps each ray's hit list (4 B per blended hit) so that the
+    # backward needs no second traversal; rays with more hits replay it
+    out = irgs.trace_forward(scene, ro, rd, p, max_hit_ids=args.saved_hits)
     grads = {"means": torch.zeros((sc.n, 3), device=dev), "quats": torch.zeros((sc.n, 4), device=dev),
              "scales": torch.zeros((sc.n, 2), device=dev), "opacity": torch.zeros(sc.n, device=dev),
              "features": torch.zeros((sc.n, F), device=dev)}
@@ -194,7 +205,7 @@ def run_ours(args):
         scene.update()
         if evs:
             evs[1].record(stream)
-        irgs.trace_forward(scene, ro, rd, p, out=out)
+        irgs.trace_forward(scene, ro, rd, p, max_hit_ids=args.saved_hits, out=out)
         if evs:
             evs[2].record(stream)
         for g in grads.values():
@@ -246,7 +257,7 @@ def run_ours(args):
     nh = out["n_hits"]
     if bwd_ms >= fwd_ms:
         kname, kms = "k_trace_backward<16,10>", bwd_ms
-        flops = algorithmic_flops(nh, 16, sc.n, F, backward=True)
+        flops = algorithmic_flops(nh, 16, sc.n, F, backward=True, saved_hits=args.saved_hits)
         src = ["trace.cuh", "trace_bwd.cu", "common.cuh"]
     else:
         kname, kms = "k_trace_forward<16,10>", fwd_ms
@@ -271,7 +282,8 @@ def run_ours(args):
                         "gf": torch.from_numpy(gf_np).pin_memory(), "gd": torch.from_numpy(gd_np).pin_memory(),
                         "go": torch.from_numpy(go_np).pin_memory()})
         dev_in = {k: torch.empty_like(v, device=dev) for k, v in host_in.items()}
-        host_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in out.items()}
+        # the rendered outputs and the gradients come back; the hit lists stay on the device
+        host_out = {k: torch.empty_like(v, device="cpu").pin_memory() for k, v in out.items() if k != "hit_ids"}
         host_out.update({("g_" + k): torch.empty_like(v, device="cpu").pin_memory() for k, v in grads.items()})
         h2d = sum(v.numel() * v.element_size() for v in host_in.values())
         d2h = sum(v.numel() * v.element_size() for v in host_out.values())
@@ -282,13 +294,13 @@ def run_ours(args):
             for k, v in host_in.items():
                 dev_in[k].copy_(v, non_blocking=True)
             scene_e2e.update()
-            o_ = irgs.trace_forward(scene_e2e, dev_in["ro"], dev_in["rd"], p, out=out)
+            o_ = irgs.trace_forward(scene_e2e, dev_in["ro"], dev_in["rd"], p, max_hit_ids=args.saved_hits, out=out)
             for g in grads.values():
                 g.zero_()
             irgs.trace_backward(scene_e2e, dev_in["ro"], dev_in["rd"], p, o_, dev_in["gf"], dev_in["gd"],
                                 dev_in["go"], grads=grads)
-            for k, v in out.items():
-                host_out[k].copy_(v, non_blocking=True)
+            for k in ("feat", "depth", "opacity", "n_hits"):
+                host_out[k].copy_(out[k], non_blocking=True)
             for k, v in grads.items():
                 host_out["g_" + k].copy_(v, non_blocking=True)
 
@@ -309,29 +321,7 @@ def run_ours(args):
     # ---- Monte Carlo rendering equation configuration
     mc = None
     if not args.no_mc and rank == 0:
-        sc2 = synth.object_scene(1_000_000, seed=1002)
-        gb = synth.gbuffer_points(640_000, seed=1002)
-        env = T(synth.env_map(seed=1003))
-        S2 = irgs.Scene(*(T(a) for a in sc2.arrays()))
-        g2 = [T(a) for a in gb]
-        ps = irgs.TraceParams(k=16, feat_count=3, t_min=1e-3)
-        o2 = irgs.shade_mc(S2, *g2, env, 32, 32, 2024, ps)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 2
-        a.record(stream)
-        for _ in range(reps):
-            irgs.shade_mc(S2, *g2, env, 32, 32, 2024, ps, out=o2)
-        b.record(stream)
-        torch.cuda.synchronize()
-        mms = a.elapsed_time(b) / reps
-        rays = 640_000 * 64
-        mc = {"workload": "1M surfels, 640k G-buffer points x (32 cosine + 32 GGX) = 41M secondary rays, "
-                          "512x256 env, k=16", "ms": mms, "mrays_s": rays / (mms * 1e-3) / 1e6,
-              "points_per_s": 640_000 / (mms * 1e-3)}
-        if S2.status() != 0:
-            raise RuntimeError("device error in the MC leg")
-        S2.close()
+        mc = mc_leg(args, dev)
 
     # ---- serving mix (continuous batching vs one request at a time)
     serving = None
@@ -354,18 +344,67 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "surfels": sc.n, "rays_per_step_per_gpu": R,
                        "cameras": args.cams, "resolution": args.res, "k": 16, "feat_count": F,
                        "alpha_min": 1 / 255, "T_min": 1e-4,
-                       "step": "LBVH rebuild + forward trace + backward trace",
+                       "step": "LBVH rebuild + forward trace (saving hit lists) + backward trace from the lists",
+                       "saved_hits": args.saved_hits,
                        "ray_order": "8x4 pixel tiles per camera", "traversal": "warp-coherent",
                        "l2": "inputs larger than L2 (1.5 GB of rays per step)"},
             "fwd_mrays_s": R / (fwd_ms * 1e-3) / 1e6, "bwd_mrays_s": R / (bwd_ms * 1e-3) / 1e6,
             "build_ms": build_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
-            "mean_hits_per_ray": float(nh.float().mean()),
+            "mean_hits_per_ray": float(nh.float().mean()), "max_hits_per_ray": int(nh.max()),
+            "replayed_ray_frac": float((nh > args.saved_hits).float().mean()) if args.saved_hits > 0 else 1.0,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "mc": mc, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def mc_leg(args, dev):
+    """Monte Carlo rendering equation at G-buffer points (Eq. 13-15): object
+    scene of --mc-surfels surfels (1M), --mc-points points (640k) x (32
+    cosine + 32 GGX) secondary rays, 512x256 environment, k=16. Times the
+    shading forward and its gradient (surfels, albedo, roughness, env)."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2412_15867_gb300 as irgs
+
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    Pn = args.mc_points
+    sc2 = synth.object_scene(args.mc_surfels, seed=1002)
+    gb = synth.gbuffer_points(Pn, seed=1002)
+    env = T(synth.env_map(seed=1003))
+    S2 = irgs.Scene(*(T(a) for a in sc2.arrays()))
+    g2 = [T(a) for a in gb]
+    ps = irgs.TraceParams(k=16, feat_count=3, t_min=1e-3)
+    g_rgb = T(np.random.default_rng(1004).normal(size=(Pn, 3)).astype(np.float32))
+    o2 = irgs.shade_mc(S2, *g2, env, 32, 32, 2024, ps)
+    gr = irgs.shade_mc_backward(S2, *g2, env, 32, 32, 2024, ps, g_rgb)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    reps = args.mc_reps
+    ev[0].record(stream)
+    for _ in range(reps):
+        irgs.shade_mc(S2, *g2, env, 32, 32, 2024, ps, out=o2)
+    ev[1].record(stream)
+    for _ in range(reps):
+        for g in gr.values():
+            g.zero_()
+        irgs.shade_mc_backward(S2, *g2, env, 32, 32, 2024, ps, g_rgb, grads=gr)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    fms = ev[0].elapsed_time(ev[1]) / reps
+    bms = ev[1].elapsed_time(ev[2]) / reps
+    rays = Pn * 64
+    if S2.status() != 0:
+        raise RuntimeError("device error in the MC leg")
+    S2.close()
+    return {"workload": f"{args.mc_surfels} surfels, {Pn} G-buffer points x (32 cosine + 32 GGX) = "
+                        f"{rays / 1e6:.1f}M secondary rays, 512x256 env, k=16",
+            "ms": fms, "mrays_s": rays / (fms * 1e-3) / 1e6, "points_per_s": Pn / (fms * 1e-3),
+            "bwd_ms": bms, "bwd_mrays_s": rays / (bms * 1e-3) / 1e6}
 
 
 def serve_leg(args, dev):
@@ -507,6 +546,10 @@ def main():
     if args.serve_only:
         import torch
         print(json.dumps({"serving": serve_leg(args, torch.device("cuda", 0))}), flush=True)
+        return
+    if args.mc_only:
+        import torch
+        print(json.dumps({"mc": mc_leg(args, torch.device("cuda", 0))}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define IRGS_ABI_VERSION 1
+#define IRGS_ABI_VERSION 2
 #define IRGS_MAX_FEATURES 16   /* blended channels per trace call */
 
 typedef enum {
@@ -139,7 +139,9 @@ irgs_status irgs_scene_info(irgs_scene scene, int64_t* n, int32_t* num_features,
 /* Synchronise `stream`, then read and clear the scene's device error word.
  * Returns IRGS_OK or IRGS_ERR_DEVICE; *bits (may be NULL) receives the raw
  * word (bit 0: a traversal stack overflowed and that ray's result is
- * incomplete). */
+ * incomplete; bit 1: the hierarchy failed a consistency bound; bit 2: a hit
+ * list given to irgs_trace_backward held an index outside the scene, and
+ * that ray's gradient is incomplete). */
 irgs_status irgs_scene_status(irgs_scene scene, void* stream, uint32_t* bits);
 
 /*
@@ -181,7 +183,10 @@ irgs_status irgs_scene_export_wide(irgs_scene scene, float* nodes, int64_t cap, 
  *   out_opacity   : [n_rays] 1 - T_final (o_rt of Eq. 8).
  *   out_nhits     : [n_rays] int32 blended hits, or NULL.
  *   out_hit_ids   : [n_rays, max_hit_ids] int32 user indices of the first
- *                   blended hits in order, -1 padded, or NULL (debugging).
+ *                   min(n_hits, max_hit_ids) blended hits in blend order,
+ *                   followed by -1 if n_hits < max_hit_ids; later entries
+ *                   are not written. NULL to skip. irgs_trace_backward can
+ *                   take this list instead of replaying the traversal.
  * Outputs are overwritten. n_rays may be 0.
  */
 irgs_status irgs_trace_forward(irgs_scene scene, const float* ray_o, const float* ray_d,
@@ -203,11 +208,15 @@ irgs_status irgs_trace_stats(irgs_scene scene, const float* ray_o, const float* 
 /*
  * Backward of irgs_trace_forward for the loss
  *   L = sum_r g_feat[r].feat[r] + g_depth[r] depth[r] + g_opacity[r] opacity[r].
- * The kernel replays each ray's k-buffer march, recomputing the hits (no hit
- * list is stored), and ADDS dL/d(parameter) into the user-order gradient
- * arrays with atomics (the caller zeroes them first).
+ * Each ray's blended hits are taken from the forward's hit list when one is
+ * given and holds them all (n_hits <= max_hit_ids), else found again by
+ * replaying the k-buffer march; each hit is recomputed with the forward's
+ * arithmetic. dL/d(parameter) is ADDED into the user-order gradient arrays
+ * (the caller zeroes them first).
  *   out_feat, out_depth, out_opacity, out_nhits: the forward's outputs for
  *                   the same scene, rays and params (required).
+ *   hit_ids, max_hit_ids: the out_hit_ids list of that forward call, or
+ *                   NULL (then max_hit_ids is ignored); max_hit_ids > 0.
  *   g_feat [n_rays, feat_count], g_depth [n_rays], g_opacity [n_rays]:
  *                   upstream gradients; g_depth / g_opacity may be NULL (0).
  *   g_means [n,3], g_quats [n,4] (w.r.t. the raw, unnormalised quaternion),
@@ -219,6 +228,7 @@ irgs_status irgs_trace_backward(irgs_scene scene, const float* ray_o, const floa
                                 int64_t n_rays, const irgs_trace_params* params,
                                 const float* out_feat, const float* out_depth,
                                 const float* out_opacity, const int32_t* out_nhits,
+                                const int32_t* hit_ids, int32_t max_hit_ids,
                                 const float* g_feat, const float* g_depth, const float* g_opacity,
                                 float* g_means, float* g_quats, float* g_scales,
                                 float* g_opacity_param, float* g_features, void* stream);

@@ -191,7 +191,9 @@ def _rays(scene: Scene, ray_o, ray_d):
 def trace_forward(scene: Scene, ray_o, ray_d, params: TraceParams = TraceParams(), max_hit_ids: int = 0,
                   out=None):
     """Forward trace (Eq. 8). Returns dict feat [R,Fc], depth [R], opacity [R],
-    n_hits [R] int32 and, if max_hit_ids > 0, hit_ids [R,max_hit_ids]."""
+    n_hits [R] int32 and, if max_hit_ids > 0, hit_ids [R,max_hit_ids] (user
+    indices in blend order, -1 after the last one when it fits; a fresh
+    array is -1 filled). trace_backward uses hit_ids when present."""
     o, d = _rays(scene, ray_o, ray_d)
     R = o.shape[0]
     dev = scene.device
@@ -200,9 +202,9 @@ def trace_forward(scene: Scene, ray_o, ray_d, params: TraceParams = TraceParams(
                "depth": torch.empty(R, device=dev, dtype=torch.float32),
                "opacity": torch.empty(R, device=dev, dtype=torch.float32),
                "n_hits": torch.empty(R, device=dev, dtype=torch.int32)}
-    ids = None
-    if max_hit_ids > 0:
-        ids = torch.empty((R, max_hit_ids), device=dev, dtype=torch.int32)
+    ids = out.get("hit_ids") if max_hit_ids > 0 else None
+    if max_hit_ids > 0 and ids is None:
+        ids = torch.full((R, max_hit_ids), -1, device=dev, dtype=torch.int32)
         out["hit_ids"] = ids
     p = params.c()
     with torch.cuda.device(dev):
@@ -229,7 +231,8 @@ def trace_stats(scene: Scene, ray_o, ray_d, params: TraceParams = TraceParams())
 def trace_backward(scene: Scene, ray_o, ray_d, params: TraceParams, fwd: dict, g_feat, g_depth=None,
                    g_opacity=None, grads=None):
     """Backward of trace_forward; returns (or accumulates into) a dict of
-    user-order gradients means/quats/scales/opacity/features."""
+    user-order gradients means/quats/scales/opacity/features. If fwd holds
+    hit_ids, rays whose whole hit list is there skip the traversal."""
     o, d = _rays(scene, ray_o, ray_d)
     R = o.shape[0]
     dev = scene.device
@@ -239,13 +242,18 @@ def trace_backward(scene: Scene, ray_o, ray_d, params: TraceParams, fwd: dict, g
                  "scales": torch.zeros((n, 2), device=dev), "opacity": torch.zeros(n, device=dev),
                  "features": torch.zeros((n, scene.num_features), device=dev)}
     gf = _dev_f32(g_feat, "g_feat").reshape(R, params.feat_count)
+    ids = fwd.get("hit_ids")
+    if ids is not None and (ids.dtype != torch.int32 or ids.dim() != 2 or ids.shape[0] != R
+                            or not ids.is_contiguous()):
+        raise ValueError("hit_ids must be a contiguous int32 [R, max_hit_ids] tensor")
     gd = None if g_depth is None else _dev_f32(g_depth, "g_depth").reshape(R)
     go = None if g_opacity is None else _dev_f32(g_opacity, "g_opacity").reshape(R)
     p = params.c()
     with torch.cuda.device(dev):
         _lib.check(_lib.lib().irgs_trace_backward(
             scene.handle, _ptr(o), _ptr(d), R, C.byref(p), _ptr(fwd["feat"]), _ptr(fwd["depth"]),
-            _ptr(fwd["opacity"]), _ptr(fwd["n_hits"]), _ptr(gf), _ptr(gd), _ptr(go),
+            _ptr(fwd["opacity"]), _ptr(fwd["n_hits"]), _ptr(ids), int(ids.shape[1]) if ids is not None else 0,
+            _ptr(gf), _ptr(gd), _ptr(go),
             _ptr(grads["means"]), _ptr(grads["quats"]), _ptr(grads["scales"]), _ptr(grads["opacity"]),
             _ptr(grads["features"]) if scene.num_features else None, _stream(dev)),
             "irgs_trace_backward")
@@ -254,9 +262,10 @@ def trace_backward(scene: Scene, ray_o, ray_d, params: TraceParams, fwd: dict, g
 
 class _TraceFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, means, quats, scales, opacity, features, ray_o, ray_d, scene, params):
-        out = trace_forward(scene, ray_o, ray_d, params)
+    def forward(ctx, means, quats, scales, opacity, features, ray_o, ray_d, scene, params, max_saved_hits):
+        out = trace_forward(scene, ray_o, ray_d, params, max_hit_ids=max_saved_hits)
         ctx.scene, ctx.params = scene, params
+        ctx.hit_ids = out.get("hit_ids")
         ctx.save_for_backward(ray_o, ray_d, out["feat"], out["depth"], out["opacity"], out["n_hits"])
         ctx.mark_non_differentiable(out["n_hits"])
         return out["feat"], out["depth"], out["opacity"], out["n_hits"]
@@ -269,17 +278,22 @@ class _TraceFn(torch.autograd.Function):
         dev = scene.device
         zf = lambda: torch.zeros((R, params.feat_count), device=dev)
         g_feat = zf() if g_feat is None else g_feat
-        g = trace_backward(scene, ro, rd, params, {"feat": feat, "depth": depth, "opacity": opac, "n_hits": nh},
-                           g_feat, g_depth, g_opac)
+        fwd = {"feat": feat, "depth": depth, "opacity": opac, "n_hits": nh}
+        if ctx.hit_ids is not None:
+            fwd["hit_ids"] = ctx.hit_ids
+        g = trace_backward(scene, ro, rd, params, fwd, g_feat, g_depth, g_opac)
+        ctx.hit_ids = None
         return (g["means"], g["quats"], g["scales"], g["opacity"].reshape(scene.opacity.shape),
-                g["features"], None, None, None, None)
+                g["features"], None, None, None, None, None)
 
 
-def trace(scene: Scene, ray_o, ray_d, params: TraceParams = TraceParams()):
+def trace(scene: Scene, ray_o, ray_d, params: TraceParams = TraceParams(), max_saved_hits: int = 0):
     """Differentiable Trace(r_o, r_d): returns (feat, depth, opacity, n_hits);
-    gradients flow to the tensors the scene was built from."""
+    gradients flow to the tensors the scene was built from. With
+    max_saved_hits > 0 the forward keeps each ray's hit list (4 bytes per
+    entry) and the backward skips the traversal for rays that fit in it."""
     return _TraceFn.apply(scene.means, scene.quats, scene.scales, scene.opacity, scene.features,
-                          ray_o, ray_d, scene, params)
+                          ray_o, ray_d, scene, params, int(max_saved_hits))
 
 
 def _shade_params(params: TraceParams, mode: str) -> TraceParams:

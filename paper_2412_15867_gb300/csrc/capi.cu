@@ -204,9 +204,10 @@ irgs_status irgs_trace_stats(irgs_scene sc, const float* ray_o, const float* ray
 
 irgs_status irgs_trace_backward(irgs_scene sc, const float* ray_o, const float* ray_d, int64_t n_rays,
                                 const irgs_trace_params* params, const float* out_feat, const float* out_depth,
-                                const float* out_opacity, const int32_t* out_nhits, const float* g_feat,
-                                const float* g_depth, const float* g_opacity, float* g_means, float* g_quats,
-                                float* g_scales, float* g_opacity_param, float* g_features, void* stream) {
+                                const float* out_opacity, const int32_t* out_nhits, const int32_t* hit_ids,
+                                int32_t max_hit_ids, const float* g_feat, const float* g_depth,
+                                const float* g_opacity, float* g_means, float* g_quats, float* g_scales,
+                                float* g_opacity_param, float* g_features, void* stream) {
     if (sc == nullptr || n_rays < 0) return IRGS_ERR_INVALID_ARG;
     irgs_status s = check_params(sc, params);
     if (s != IRGS_OK) return s;
@@ -215,11 +216,13 @@ irgs_status irgs_trace_backward(irgs_scene sc, const float* ray_o, const float* 
     if (n_rays > 0 && params->feat_count > 0 && (!out_feat || !g_feat)) return IRGS_ERR_INVALID_ARG;
     if (sc->n > 0 && (!g_means || !g_quats || !g_scales || !g_opacity_param)) return IRGS_ERR_INVALID_ARG;
     if (sc->n > 0 && sc->F > 0 && params->feat_count > 0 && !g_features) return IRGS_ERR_INVALID_ARG;
+    if (hit_ids != nullptr && max_hit_ids <= 0) return IRGS_ERR_INVALID_ARG;
     if (n_rays >= (int64_t)UINT32_MAX * 128) return IRGS_ERR_INVALID_ARG;
     if ((s = use_device(sc)) != IRGS_OK) return s;
-    return irgs::launch_trace_backward(sc->view(), sc->perm, ray_o, ray_d, n_rays, *params, out_feat, out_depth, out_opacity,
-                                       out_nhits, g_feat, g_depth, g_opacity, g_means, g_quats, g_scales,
-                                       g_opacity_param, g_features, static_cast<cudaStream_t>(stream));
+    return irgs::launch_trace_backward(sc->view(), sc->perm, ray_o, ray_d, n_rays, *params, out_feat, out_depth,
+                                       out_opacity, out_nhits, hit_ids, max_hit_ids, g_feat, g_depth, g_opacity,
+                                       g_means, g_quats, g_scales, g_opacity_param, g_features,
+                                       static_cast<cudaStream_t>(stream));
 }
 
 irgs_status irgs_shade_mc(irgs_scene sc, const float* x, const float* n, const float* albedo, const float* rough,

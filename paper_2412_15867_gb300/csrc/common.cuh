@@ -14,6 +14,7 @@ namespace irgs {
 // Error bits of the per-scene device status word.
 constexpr uint32_t kErrStackOverflow = 1u;   // a ray's traversal stack overflowed
 constexpr uint32_t kErrBadTree = 2u;         // the hierarchy failed a consistency bound
+constexpr uint32_t kErrBadHitList = 4u;      // a saved hit list held an index outside the scene
 
 // Traversal stack depth. Karras trees over 30-bit keys with index tie-breaks
 // are at most 30 + 31 levels deep; the stack holds deferred siblings only.
@@ -123,6 +124,7 @@ struct SceneView {
     const float* feat;     // [n, F] Morton order
     const float4* q_raw;   // [n] raw quaternion (w,x,y,z), Morton order
     const float2* scale;   // [n] (s_u, s_v), Morton order
+    const int32_t* inv_perm;  // [n] Morton slot of user index u
     uint32_t* status;      // device error word
     int64_t n;
     int32_t F;

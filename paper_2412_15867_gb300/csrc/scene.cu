@@ -234,10 +234,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
 __global__ void k_gather(const int32_t* __restrict__ perm, int64_t n, const float4* __restrict__ rec_user,
                          const float* __restrict__ box_user, const float* __restrict__ quats,
                          const float* __restrict__ scales, float4* __restrict__ rec, float* __restrict__ leaf_box,
-                         float4* __restrict__ q_raw, float2* __restrict__ scale) {
+                         float4* __restrict__ q_raw, float2* __restrict__ scale, int32_t* __restrict__ inv_perm) {
     int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (m >= n) return;
     int64_t u = perm[m];
+    if (inv_perm != nullptr) inv_perm[u] = (int32_t)m;
     for (int k = 0; k < 4; ++k) rec[4 * m + k] = rec_user[4 * u + k];
     for (int k = 0; k < 6; ++k) leaf_box[6 * m + k] = box_user[6 * u + k];
     q_raw[m] = make_float4(quats[4 * u], quats[4 * u + 1], quats[4 * u + 2], quats[4 * u + 3]);
@@ -453,7 +454,7 @@ inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 void free_scene(irgs_scene sc) {
     if (!sc) return;
     void* ptrs[] = {sc->nodes, sc->rec, sc->feat, sc->q_raw, sc->scale, sc->leaf_box, sc->keys,
-                    sc->perm, sc->status, sc->rec_user, sc->box_user, sc->keys_tmp, sc->vals_tmp,
+                    sc->perm, sc->inv_perm, sc->status, sc->rec_user, sc->box_user, sc->keys_tmp, sc->vals_tmp,
                     sc->hist, sc->bounds, sc->leaf_parent, sc->node_parent, sc->refit_flag, sc->wide,
                     sc->wide_rank};
     for (void* p : ptrs)
@@ -491,7 +492,7 @@ static irgs_status enqueue_build(irgs_scene sc, const irgs_surfels* s, cudaStrea
         }
         // after an even number of passes the sorted data is back in keys/perm
         k_gather<<<blocks_for(n, T), T, 0, st>>>(sc->perm, n, sc->rec_user, sc->box_user, s->quats, s->scales,
-                                                 sc->rec, sc->leaf_box, sc->q_raw, sc->scale);
+                                                 sc->rec, sc->leaf_box, sc->q_raw, sc->scale, sc->inv_perm);
         if (F > 0)
             k_gather_feat<<<blocks_for(n * F, T), T, 0, st>>>(sc->perm, n, F, s->features, sc->feat);
         if (n > 1) {
@@ -543,6 +544,7 @@ irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_
     A(dalloc(&sc->leaf_box, 6 * n, B));
     A(dalloc(&sc->keys, n, B));
     A(dalloc(&sc->perm, n, B));
+    A(dalloc(&sc->inv_perm, n, B));
     A(dalloc(&sc->status, 1, B));
     A(dalloc(&sc->rec_user, 4 * n, B));
     A(dalloc(&sc->box_user, 6 * n, B));

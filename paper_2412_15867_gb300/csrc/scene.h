@@ -23,6 +23,7 @@ struct irgs_scene_s {
     float* leaf_box = nullptr;        // [n*6]
     uint32_t* keys = nullptr;         // [n] sorted Morton codes
     int32_t* perm = nullptr;          // [n] user index of Morton slot
+    int32_t* inv_perm = nullptr;      // [n] Morton slot of user index
     uint32_t* status = nullptr;       // device error word
     irgs::WideNode* wide = nullptr;   // [max_wide] 4-wide hierarchy
     int64_t max_wide = 0;
@@ -47,6 +48,7 @@ struct irgs_scene_s {
         v.feat = feat;
         v.q_raw = q_raw;
         v.scale = scale;
+        v.inv_perm = inv_perm;
         v.status = status;
         v.n = n;
         v.F = F;
@@ -73,7 +75,8 @@ irgs_status launch_trace_stats(const SceneView& S, const float* ro, const float*
 // trace_bwd.cu
 irgs_status launch_trace_backward(const SceneView& sv, const int32_t* perm, const float* ro, const float* rd, int64_t R,
                                   const irgs_trace_params& p, const float* feat, const float* depth,
-                                  const float* opac, const int32_t* nhits, const float* g_feat,
+                                  const float* opac, const int32_t* nhits, const int32_t* hit_ids,
+                                  int32_t max_hit_ids, const float* g_feat,
                                   const float* g_depth, const float* g_opac, float* g_means,
                                   float* g_quats, float* g_scales, float* g_opacity, float* g_features,
                                   cudaStream_t st);

@@ -15,8 +15,9 @@ template <int K, int FB, bool WARP>
 __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
     SceneView S, const float* __restrict__ ro, const float* __restrict__ rd, int64_t R, TraceParams P,
     const float* __restrict__ out_feat, const float* __restrict__ out_depth, const float* __restrict__ out_opac,
-    const int32_t* __restrict__ out_nhits, const float* __restrict__ g_featv, const float* __restrict__ g_depthv,
-    const float* __restrict__ g_opacv, float* __restrict__ acc_rows) {
+    const int32_t* __restrict__ out_nhits, const int32_t* __restrict__ hit_ids, int max_ids,
+    const float* __restrict__ g_featv, const float* __restrict__ g_depthv, const float* __restrict__ g_opacv,
+    float* __restrict__ acc_rows) {
     constexpr int N = GradRow<FB>::N;
     static_assert(kBwdThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
     __shared__ float rows_all[kBwdThreads * (N + 1)];
@@ -37,16 +38,35 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
     }
     const float gD = g_depthv != nullptr ? g_depthv[q] : 0.f;
     const float gO = g_opacv != nullptr ? g_opacv[q] : 0.f;
-    const bool ok = march_backward<K, FB, WARP>(S, ray, P, live, nh_total, Cf, out_depth[q], 1.0f - out_opac[q], gC,
-                                                gD, gO, acc_rows, rows);
-    if (live && !ok) atomicOr(S.status, kErrStackOverflow);
+    const float Df = out_depth[q], Tfin = 1.0f - out_opac[q];
+    // rays whose whole hit list was saved skip the traversal; the others
+    // (list absent or longer than max_ids) replay the march
+    const bool listed = live && hit_ids != nullptr && nh_total <= max_ids;
+    if (listed)
+        listed_backward<FB>(S, ray, P, hit_ids + q * (int64_t)max_ids, nh_total, Cf, Df, Tfin, gC, gD, gO, acc_rows,
+                            rows);
+    const bool replay = live && !listed;
+    if (WARP ? __any_sync(kFullWarp, replay) : replay) {
+        const bool ok = march_backward<K, FB, WARP>(S, ray, P, replay, nh_total, Cf, Df, Tfin, gC, gD, gO, acc_rows,
+                                                    rows);
+        if (replay && !ok) atomicOr(S.status, kErrStackOverflow);
+    }
 }
 
+// Pointers of one backward call (see irgs_trace_backward).
+struct BwdArgs {
+    const int32_t* perm;
+    const float *ro, *rd;
+    int64_t R;
+    const float *feat, *depth, *opac;
+    const int32_t *nhits, *ids;
+    int max_ids;
+    const float *gf, *gd, *go;
+    float *gm, *gq, *gs, *gop, *gfe;
+};
+
 template <int K, int FB, bool WARP>
-cudaError_t launch(const SceneView& S, const int32_t* perm, const float* ro, const float* rd, int64_t R,
-                   const TraceParams& P, const float* feat, const float* depth, const float* opac,
-                   const int32_t* nhits, const float* gf, const float* gd, const float* go, float* gm, float* gq,
-                   float* gs, float* gop, float* gfe, cudaStream_t st) {
+cudaError_t launch(const SceneView& S, const TraceParams& P, const BwdArgs& a, cudaStream_t st) {
     constexpr int N = GradRow<FB>::N;
     const size_t bytes = sizeof(float) * N * (size_t)(S.n > 0 ? S.n : 1);
     float* acc_rows = nullptr;
@@ -54,12 +74,12 @@ cudaError_t launch(const SceneView& S, const int32_t* perm, const float* ro, con
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(acc_rows, 0, bytes, st);
     if (e == cudaSuccess) {
-        const int64_t blocks = (R + kBwdThreads - 1) / kBwdThreads;
-        k_trace_backward<K, FB, WARP><<<(unsigned)blocks, kBwdThreads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac,
-                                                                              nhits, gf, gd, go, acc_rows);
+        const int64_t blocks = (a.R + kBwdThreads - 1) / kBwdThreads;
+        k_trace_backward<K, FB, WARP><<<(unsigned)blocks, kBwdThreads, 0, st>>>(
+            S, a.ro, a.rd, a.R, P, a.feat, a.depth, a.opac, a.nhits, a.ids, a.max_ids, a.gf, a.gd, a.go, acc_rows);
         if (S.n > 0)
-            k_grad_scatter<FB><<<(unsigned)((S.n + 255) / 256), 256, 0, st>>>(perm, S.n, acc_rows, P.fc, S.F, P.off, gm,
-                                                                             gq, gs, gop, gfe);
+            k_grad_scatter<FB><<<(unsigned)((S.n + 255) / 256), 256, 0, st>>>(a.perm, S.n, acc_rows, P.fc, S.F, P.off,
+                                                                             a.gm, a.gq, a.gs, a.gop, a.gfe);
         count_launches(S.n > 0 ? 2 : 1);
         e = cudaGetLastError();
     }
@@ -68,46 +88,35 @@ cudaError_t launch(const SceneView& S, const int32_t* perm, const float* ro, con
 }
 
 template <int K, bool WARP>
-cudaError_t launch_f(const SceneView& S, const int32_t* perm, const float* ro, const float* rd, int64_t R, const TraceParams& P,
-                     const float* feat, const float* depth, const float* opac, const int32_t* nhits,
-                     const float* gf, const float* gd, const float* go, float* gm, float* gq, float* gs,
-                     float* gop, float* gfe, cudaStream_t st) {
-    if (P.fc <= 3)
-        return launch<K, 3, WARP>(S, perm, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
-    if (P.fc <= 10)
-        return launch<K, 10, WARP>(S, perm, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
-    return launch<K, 16, WARP>(S, perm, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+cudaError_t launch_f(const SceneView& S, const TraceParams& P, const BwdArgs& a, cudaStream_t st) {
+    if (P.fc <= 3) return launch<K, 3, WARP>(S, P, a, st);
+    if (P.fc <= 10) return launch<K, 10, WARP>(S, P, a, st);
+    return launch<K, 16, WARP>(S, P, a, st);
 }
 
 template <int K>
-cudaError_t launch_k(bool warp, const SceneView& S, const int32_t* perm, const float* ro, const float* rd, int64_t R,
-                     const TraceParams& P, const float* feat, const float* depth, const float* opac,
-                     const int32_t* nhits, const float* gf, const float* gd, const float* go, float* gm, float* gq,
-                     float* gs, float* gop, float* gfe, cudaStream_t st) {
-    return warp ? launch_f<K, true>(S, perm, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st)
-                : launch_f<K, false>(S, perm, ro, rd, R, P, feat, depth, opac, nhits, gf, gd, go, gm, gq, gs, gop, gfe, st);
+cudaError_t launch_k(bool warp, const SceneView& S, const TraceParams& P, const BwdArgs& a, cudaStream_t st) {
+    return warp ? launch_f<K, true>(S, P, a, st) : launch_f<K, false>(S, P, a, st);
 }
 
 }  // namespace
 
 irgs_status launch_trace_backward(const SceneView& S, const int32_t* perm, const float* ro, const float* rd, int64_t R,
                                   const irgs_trace_params& p, const float* feat, const float* depth,
-                                  const float* opac, const int32_t* nhits, const float* g_feat,
-                                  const float* g_depth, const float* g_opac, float* g_means, float* g_quats,
-                                  float* g_scales, float* g_opacity, float* g_features, cudaStream_t st) {
+                                  const float* opac, const int32_t* nhits, const int32_t* hit_ids,
+                                  int32_t max_hit_ids, const float* g_feat, const float* g_depth, const float* g_opac,
+                                  float* g_means, float* g_quats, float* g_scales, float* g_opacity,
+                                  float* g_features, cudaStream_t st) {
     if (R == 0) return IRGS_OK;
     const TraceParams P = to_params(p);
-    cudaError_t e;
+    const BwdArgs a{perm,  ro,     rd,      R,       feat,     depth,     opac,      nhits,     hit_ids,
+                    hit_ids != nullptr ? max_hit_ids : 0, g_feat, g_depth, g_opac, g_means, g_quats, g_scales,
+                    g_opacity, g_features};
     const bool warp = (p.flags & IRGS_FLAG_PER_THREAD) == 0u;
+    cudaError_t e;
     switch (p.k) {
-        case 8:
-            e = launch_k<8>(warp, S, perm, ro, rd, R, P, feat, depth, opac, nhits, g_feat, g_depth, g_opac, g_means,
-                            g_quats, g_scales, g_opacity, g_features, st);
-            break;
-        case 16:
-            e = launch_k<16>(warp, S, perm, ro, rd, R, P, feat, depth, opac, nhits, g_feat, g_depth, g_opac, g_means,
-                             g_quats, g_scales, g_opacity, g_features, st);
-            break;
+        case 8: e = launch_k<8>(warp, S, P, a, st); break;
+        case 16: e = launch_k<16>(warp, S, P, a, st); break;
         default: return IRGS_ERR_UNSUPPORTED;
     }
     if (e == cudaErrorMemoryAllocation) return IRGS_ERR_OOM;

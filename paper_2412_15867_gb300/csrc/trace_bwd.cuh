@@ -1,6 +1,6 @@
-// Backward replay of one ray's k-buffer march (the gradient of Trace, IRGS
-// Eq. 8; the tracer is differentiable, Sec. 3.3), shared by the trace
-// backward and the shading backward kernels.
+// Backward of one ray's blend (the gradient of Trace, IRGS Eq. 8; the
+// tracer is differentiable, Sec. 3.3), shared by the trace backward and the
+// shading backward kernels.
 //
 // For the loss L = g_C.C + g_D D + g_O O and hits j = 0..J-1 in depth order,
 // with w_j = T_j alpha_j and v_j = g_C.f_j + g_D tau_j:
@@ -10,9 +10,11 @@
 // suffix comes from the forward's totals minus the replayed prefix). The
 // chain then runs alpha -> (o, rho^2) -> (u, v) -> (p - mu, tau) -> (mu, t_u,
 // t_v, n, s_u, s_v) -> raw quaternion (Eq. 6-7 and the rotation of the unit
-// quaternion). Per-hit gradients are summed across the lanes of a warp that
-// hold the same surfel and added with vector atomics into a Morton-ordered
-// scratch accumulator, which k_grad_scatter finally adds into the caller's
+// quaternion). The hits come either from replaying the march (same traversal
+// and arithmetic as the forward) or from the hit list the forward saved.
+// Per-hit gradients are summed across the lanes of a warp that hold the same
+// surfel and added with vector atomics into a Morton-ordered scratch
+// accumulator, which k_grad_scatter finally adds into the caller's
 // user-order arrays.
 #pragma once
 
@@ -97,6 +99,91 @@ __global__ void k_grad_scatter(const int32_t* __restrict__ perm, int64_t n, cons
     for (int c = 0; c < fc; ++c) g_feat[u * F + off + c] += f[c];
 }
 
+// Running state of one ray's backward: the blended prefix sums C_<=j, D_<=j
+// and the transmittance T_j in front of the next hit.
+template <int FB>
+struct BwdAcc {
+    float C[FB];
+    float D, T;
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int c = 0; c < FB; ++c) C[c] = 0.f;
+        D = 0.f;
+        T = 1.f;
+    }
+};
+
+// Gradient of the next blended hit, surfel m (Morton slot), given the
+// forward's outputs (Cf, Df, Tfin) and the upstream gradients: recomputes
+// the hit with the forward's arithmetic (bitwise the same alpha and depth),
+// adds its row to the accumulator and advances the running state.
+template <int FB>
+__device__ __forceinline__ void backward_hit(const SceneView& S, const Ray& ray, const TraceParams& P, int32_t m,
+                                             BwdAcc<FB>& st, const float (&Cf)[FB], float Df, float Tfin,
+                                             const float (&gC)[FB], float gD, float gO,
+                                             float* __restrict__ acc_rows, float* rows) {
+    const float4* Rp = S.rec + (int64_t)m * kRecF4;
+    const float4 r0 = ldg4(Rp), r1 = ldg4(Rp + 1), r2 = ldg4(Rp + 2), r3 = ldg4(Rp + 3);
+    float kh, kl, a;
+    HitGeom hg;
+    surfel_hit<true>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a, &hg);
+    const float tau = kh + 0.0f;
+    const float w = __fmul_rn(st.T, a);
+    const float* f = S.feat + (int64_t)m * S.F + P.off;
+    float v = __fmul_rn(gD, tau), Sj = 0.f;
+#pragma unroll
+    for (int c = 0; c < FB; ++c) {
+        const float fv = c < P.fc ? __ldg(f + c) : 0.f;
+        st.C[c] = c < P.fc ? __fmaf_rn(w, fv, st.C[c]) : 0.f;
+        v = fmaf(gC[c], fv, v);
+        Sj = fmaf(gC[c], Cf[c] - st.C[c], Sj);
+    }
+    st.D = __fmaf_rn(w, tau, st.D);
+    Sj = fmaf(gD, Df - st.D, Sj);
+    const float dA = st.T * v - (Sj - gO * Tfin) / (1.0f - a);
+
+    const float2 sc = __ldg(&S.scale[m]);
+    const float4 q = __ldg(&S.q_raw[m]);
+    GradRow<FB> gv;
+    const bool clamped = hg.a_raw >= P.alpha_max;
+    const float g_o = clamped ? 0.f : dA * hg.G;
+    const float g_rho2 = clamped ? 0.f : -0.5f * dA * a;
+    const float gu = 2.f * g_rho2 * hg.u, gvv = 2.f * g_rho2 * hg.v;
+    const f3 tus = mk3(r1.x, r1.y, r1.z), tvs = mk3(r2.x, r2.y, r2.z), nn = mk3(r3.x, r3.y, r3.z);
+    const f3 ge = add3(mul3(tus, gu), mul3(tvs, gvv));
+    const float gtau = w * gD + dot3(ge, ray.d);
+    const float s_t = gtau / hg.den;
+    const f3 gmu = sub3(mul3(nn, s_t), ge);
+    const f3 gn = mul3(hg.e, -s_t);
+    const f3 gtu = mul3(hg.e, gu / sc.x);
+    const f3 gtv = mul3(hg.e, gvv / sc.y);
+    // raw quaternion: derivative of the rotation columns, then of q / |q|
+    const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    const float qw = q.x / qn, qx = q.y / qn, qy = q.z / qn, qz = q.w / qn;
+    const float hw = 2.f * (qz * gtu.y - qy * gtu.z - qz * gtv.x + qx * gtv.z + qy * gn.x - qx * gn.y);
+    const float hx = 2.f * (qy * gtu.y + qz * gtu.z + qy * gtv.x - 2.f * qx * gtv.y + qw * gtv.z + qz * gn.x -
+                            qw * gn.y - 2.f * qx * gn.z);
+    const float hy = 2.f * (-2.f * qy * gtu.x + qx * gtu.y - qw * gtu.z + qx * gtv.x + qz * gtv.z + qw * gn.x +
+                            qz * gn.y - 2.f * qy * gn.z);
+    const float hz = 2.f * (-2.f * qz * gtu.x + qw * gtu.y + qx * gtu.z - qw * gtv.x - 2.f * qz * gtv.y +
+                            qy * gtv.z + qx * gn.x + qy * gn.y);
+    const float proj = qw * hw + qx * hx + qy * hy + qz * hz;
+    gv.v[0] = gmu.x; gv.v[1] = gmu.y; gv.v[2] = gmu.z;
+    gv.v[3] = g_o;
+    gv.v[4] = (hw - qw * proj) / qn;
+    gv.v[5] = (hx - qx * proj) / qn;
+    gv.v[6] = (hy - qy * proj) / qn;
+    gv.v[7] = (hz - qz * proj) / qn;
+    gv.v[8] = -gu * hg.u / sc.x;
+    gv.v[9] = -gvv * hg.v / sc.y;
+    gv.v[10] = 0.f;
+    gv.v[11] = 0.f;
+#pragma unroll
+    for (int c = 0; c < GradRow<FB>::FB4; ++c) gv.v[12 + c] = c < FB ? w * gC[c] : 0.f;
+    accumulate_row<FB>(gv, m, acc_rows, rows);
+    st.T = __fmul_rn(st.T, __fsub_rn(1.0f, a));
+}
+
 // Replay of one ray (all 32 lanes together when WARP): the march is repeated
 // with the same traversal and arithmetic as the forward, capped at nh_total
 // composited hits; Cf, Df, Tfin are the forward's outputs and gC, gD, gO the
@@ -107,10 +194,8 @@ __device__ __forceinline__ bool march_backward(const SceneView& S, const Ray& ra
                                                int nh_total, const float (&Cf)[FB], float Df, float Tfin,
                                                const float (&gC)[FB], float gD, float gO,
                                                float* __restrict__ acc_rows, float* rows) {
-    float Cacc[FB];
-#pragma unroll
-    for (int c = 0; c < FB; ++c) Cacc[c] = 0.f;
-    float Dacc = 0.f, T = 1.f;
+    BwdAcc<FB> st;
+    st.init();
     int nh = 0;
     uint64_t last_key = depth_key(P.t_min, 0.f);
     int32_t last_m = INT32_MAX;
@@ -123,77 +208,8 @@ __device__ __forceinline__ bool march_backward(const SceneView& S, const Ray& ra
         else
             ok &= collect_round(S, ray, P, last_key, last_m, kb);
         if (done) continue;
-        for (int j = 0; j < kb.cnt && nh < nh_total; ++j) {
-            {
-                const float a = kb.a_at(j);
-                const int32_t m = kb.m_at(j);
-                const float tau = key_depth(kb.key_at(j));
-                const float w = __fmul_rn(T, a);
-                const float* f = S.feat + (int64_t)m * S.F + P.off;
-                float fv[FB];
-                float v = __fmul_rn(gD, tau), Sj = 0.f;
-#pragma unroll
-                for (int c = 0; c < FB; ++c) {
-                    fv[c] = c < P.fc ? __ldg(f + c) : 0.f;
-                    Cacc[c] = c < P.fc ? __fmaf_rn(w, fv[c], Cacc[c]) : 0.f;
-                    v = fmaf(gC[c], fv[c], v);
-                    Sj = fmaf(gC[c], Cf[c] - Cacc[c], Sj);
-                }
-                Dacc = __fmaf_rn(w, tau, Dacc);
-                Sj = fmaf(gD, Df - Dacc, Sj);
-                const float dA = T * v - (Sj - gO * Tfin) / (1.0f - a);
-
-                // recompute the hit geometry (bitwise identical to the march)
-                const float4* Rp = S.rec + (int64_t)m * kRecF4;
-                const float4 r0 = ldg4(Rp), r1 = ldg4(Rp + 1), r2 = ldg4(Rp + 2), r3 = ldg4(Rp + 3);
-                float kh, kl, a2;
-                HitGeom hg;
-                surfel_hit<true>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a2, &hg);
-                const float2 sc = __ldg(&S.scale[m]);
-                const float4 q = __ldg(&S.q_raw[m]);
-
-                GradRow<FB> gv;
-                const bool clamped = hg.a_raw >= P.alpha_max;
-                const float g_o = clamped ? 0.f : dA * hg.G;
-                const float g_rho2 = clamped ? 0.f : -0.5f * dA * a;
-                const float gu = 2.f * g_rho2 * hg.u, gvv = 2.f * g_rho2 * hg.v;
-                const f3 tus = mk3(r1.x, r1.y, r1.z), tvs = mk3(r2.x, r2.y, r2.z), nn = mk3(r3.x, r3.y, r3.z);
-                const f3 ge = add3(mul3(tus, gu), mul3(tvs, gvv));
-                const float gtau = w * gD + dot3(ge, ray.d);
-                const float s_t = gtau / hg.den;
-                const f3 gmu = sub3(mul3(nn, s_t), ge);
-                const f3 gn = mul3(hg.e, -s_t);
-                const f3 gtu = mul3(hg.e, gu / sc.x);
-                const f3 gtv = mul3(hg.e, gvv / sc.y);
-                // raw quaternion: derivative of the rotation columns, then of q / |q|
-                const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-                const float qw = q.x / qn, qx = q.y / qn, qy = q.z / qn, qz = q.w / qn;
-                const float hw = 2.f * (qz * gtu.y - qy * gtu.z - qz * gtv.x + qx * gtv.z + qy * gn.x - qx * gn.y);
-                const float hx = 2.f * (qy * gtu.y + qz * gtu.z + qy * gtv.x - 2.f * qx * gtv.y + qw * gtv.z +
-                                        qz * gn.x - qw * gn.y - 2.f * qx * gn.z);
-                const float hy = 2.f * (-2.f * qy * gtu.x + qx * gtu.y - qw * gtu.z + qx * gtv.x + qz * gtv.z +
-                                        qw * gn.x + qz * gn.y - 2.f * qy * gn.z);
-                const float hz = 2.f * (-2.f * qz * gtu.x + qw * gtu.y + qx * gtu.z - qw * gtv.x - 2.f * qz * gtv.y +
-                                        qy * gtv.z + qx * gn.x + qy * gn.y);
-                const float proj = qw * hw + qx * hx + qy * hy + qz * hz;
-                gv.v[0] = gmu.x; gv.v[1] = gmu.y; gv.v[2] = gmu.z;
-                gv.v[3] = g_o;
-                gv.v[4] = (hw - qw * proj) / qn;
-                gv.v[5] = (hx - qx * proj) / qn;
-                gv.v[6] = (hy - qy * proj) / qn;
-                gv.v[7] = (hz - qz * proj) / qn;
-                gv.v[8] = -gu * hg.u / sc.x;
-                gv.v[9] = -gvv * hg.v / sc.y;
-                gv.v[10] = 0.f;
-                gv.v[11] = 0.f;
-#pragma unroll
-                for (int c = 0; c < GradRow<FB>::FB4; ++c) gv.v[12 + c] = c < FB ? w * gC[c] : 0.f;
-                accumulate_row<FB>(gv, m, acc_rows, rows);
-
-                T = __fmul_rn(T, __fsub_rn(1.0f, a));
-                ++nh;
-            }
-        }
+        for (int j = 0; j < kb.cnt && nh < nh_total; ++j, ++nh)
+            backward_hit<FB>(S, ray, P, kb.m_at(j), st, Cf, Df, Tfin, gC, gD, gO, acc_rows, rows);
         if (nh >= nh_total || kb.cnt < K) {
             done = true;
         } else {
@@ -202,6 +218,25 @@ __device__ __forceinline__ bool march_backward(const SceneView& S, const Ray& ra
         }
     }
     return ok;
+}
+
+// Backward from the forward's saved hit list (user indices in blend order,
+// as irgs_trace_forward writes them): no traversal.
+template <int FB>
+__device__ __forceinline__ void listed_backward(const SceneView& S, const Ray& ray, const TraceParams& P,
+                                                const int32_t* __restrict__ ids, int nh_total, const float (&Cf)[FB],
+                                                float Df, float Tfin, const float (&gC)[FB], float gD, float gO,
+                                                float* __restrict__ acc_rows, float* rows) {
+    BwdAcc<FB> st;
+    st.init();
+    for (int j = 0; j < nh_total; ++j) {
+        const int32_t u = __ldg(ids + j);
+        if (u < 0 || u >= S.n) {   // not a list the forward wrote for this scene
+            atomicOr(S.status, kErrBadHitList);
+            return;
+        }
+        backward_hit<FB>(S, ray, P, __ldg(&S.inv_perm[u]), st, Cf, Df, Tfin, gC, gD, gO, acc_rows, rows);
+    }
 }
 
 }  // namespace irgs

@@ -23,14 +23,11 @@ __global__ void __launch_bounds__(trace_threads<K>(), K <= 16 ? 6 : 4) k_trace_f
     const int64_t q = live ? r : 0;   // lanes without a ray follow the warp with a dummy ray
     const Ray ray = make_ray(mk3(ro[3 * q], ro[3 * q + 1], ro[3 * q + 2]),
                              mk3(rd[3 * q], rd[3 * q + 1], rd[3 * q + 2]));
-    int32_t* my_ids = nullptr;
-    if (ids != nullptr && live) {
-        my_ids = ids + r * (int64_t)max_ids;
-        for (int j = 0; j < max_ids; ++j) my_ids[j] = -1;
-    }
+    int32_t* my_ids = (ids != nullptr && live) ? ids + r * (int64_t)max_ids : nullptr;
     MarchState<K, FB> st;
     const bool ok = march_forward<K, FB, WARP>(S, ray, P, st, my_ids, max_ids, live);
     if (!live) return;
+    if (my_ids != nullptr && st.nh < max_ids) my_ids[st.nh] = -1;   // terminator
     if (!ok) atomicOr(S.status, kErrStackOverflow);
 #pragma unroll
     for (int c = 0; c < FB; ++c)

@@ -19,7 +19,7 @@ def test_exports_every_declared_symbol(L):
     assert len(names) >= 10
     for n in names:
         assert hasattr(L, n), n
-    assert L.irgs_abi_version() == 1
+    assert L.irgs_abi_version() == 2
 
 
 def test_status_strings(L):
@@ -40,7 +40,8 @@ def test_null_arguments_rejected_without_gpu(L):
     assert L.irgs_build_scene(C.byref(s), 0.0, None, C.byref(h)) == 1     # alpha_min must be > 0
     p = _lib.TraceParamsC(16, 1 / 255, 0.99, 1e-4, 0.0, math.inf, 0, 3, 0)
     assert L.irgs_trace_forward(None, None, None, 0, C.byref(p), None, None, None, None, None, 0, None) == 1
-    assert L.irgs_trace_backward(None, None, None, 0, C.byref(p), *([None] * 13)) == 1
+    assert L.irgs_trace_backward(None, None, None, 0, C.byref(p), None, None, None, None, None, 0,
+                                 *([None] * 9)) == 1
     assert L.irgs_shade_mc(None, None, None, None, None, None, 0, None, 1, 1, 1, 1, 0, C.byref(p),
                            None, None, None, None) == 1
     assert L.irgs_destroy_scene(None) == 0

@@ -136,3 +136,87 @@ def test_gradient_scatter_under_heavy_contention():
     g = gpu_grads(sc, ro, rd, p, gf, gd, go)
     gref = oracle.trace_grad(sc, ro, rd, gf, gd, go, opar(p))
     compare_grads(g, gref)
+
+
+def _grads_close(a, b, rel=1e-5):
+    for k in NAMES:
+        x, y = a[k].reshape(-1), b[k].reshape(-1)
+        if y.numel() == 0:
+            continue
+        scale = float(y.abs().max())
+        assert float((x - y).abs().max()) <= rel * scale + 1e-30, k
+
+
+@pytest.mark.parametrize("flags", [0, irgs.FLAG_PER_THREAD])
+@pytest.mark.parametrize("max_ids", [128, 8])
+def test_saved_hit_lists_match_replay_and_oracle(flags, max_ids):
+    """Backward from the forward's saved hit lists (max_ids = 128: every ray
+    listed; 8: rays with more hits replay the march inside the same warps)
+    equals the replaying backward up to the order of the atomic sums, and
+    the oracle's gradient within the usual bar."""
+    sc = synth.object_scene(n=20_000, seed=45)
+    ro, rd = synth.camera_batch_rays(synth.hemisphere_cameras(2, seed=45), 48, 40, tile=(8, 4))
+    p = irgs.TraceParams(k=16, feat_count=10, flags=flags)
+    ro, rd = clean_rays(sc, ro, rd, p)
+    gf, gd, go = synth.upstream_grads(ro.shape[0], 10, seed=46)
+    S = make_scene(irgs, sc)
+    fwd = irgs.trace_forward(S, dev(ro), dev(rd), p, max_hit_ids=max_ids)
+    nh = fwd["n_hits"].cpu().numpy()
+    assert (nh <= max_ids).any() and (max_ids == 128 or (nh > max_ids).any())
+    listed = irgs.trace_backward(S, dev(ro), dev(rd), p, fwd, dev(gf), dev(gd), dev(go))
+    plain = {k: v for k, v in fwd.items() if k != "hit_ids"}
+    replay = irgs.trace_backward(S, dev(ro), dev(rd), p, plain, dev(gf), dev(gd), dev(go))
+    torch.cuda.synchronize()
+    assert S.status() == 0
+    _grads_close(listed, replay)
+    compare_grads(listed, oracle.trace_grad(sc, ro, rd, gf, gd, go, opar(p)))
+
+
+def test_hit_list_layout_terminator():
+    sc = synth.object_scene(n=5_000, seed=47)
+    ro, rd = synth.camera_batch_rays(synth.hemisphere_cameras(1, seed=47), 32, 32)
+    p = irgs.TraceParams(k=16, feat_count=3)
+    S = make_scene(irgs, sc)
+    ids = torch.full((ro.shape[0], 40), -7, device="cuda", dtype=torch.int32)
+    out = irgs.trace_forward(S, dev(ro), dev(rd), p, max_hit_ids=40, out={
+        "feat": torch.empty((ro.shape[0], 3), device="cuda"), "depth": torch.empty(ro.shape[0], device="cuda"),
+        "opacity": torch.empty(ro.shape[0], device="cuda"),
+        "n_hits": torch.empty(ro.shape[0], device="cuda", dtype=torch.int32), "hit_ids": ids})
+    nh = out["n_hits"].cpu().numpy()
+    h = ids.cpu().numpy()
+    ref = oracle.trace(sc, ro, rd, opar(p), max_ids=40)
+    assert (nh > 0).sum() > 100
+    for r in np.nonzero((ref["flags"] & oracle.FORWARD_FLAGS) == 0)[0][:300]:
+        k = min(nh[r], 40)
+        assert np.array_equal(h[r, :k], ref["ids"][r, :k])
+        if nh[r] < 40:
+            assert h[r, nh[r]] == -1 and np.all(h[r, nh[r] + 1:] == -7)
+
+
+def test_out_of_range_hit_list_sets_status_bit():
+    sc = synth.object_scene(n=2_000, seed=48)
+    ro, rd = synth.camera_batch_rays(synth.hemisphere_cameras(1, seed=48), 16, 16)
+    p = irgs.TraceParams(k=8, feat_count=3)
+    S = make_scene(irgs, sc)
+    fwd = irgs.trace_forward(S, dev(ro), dev(rd), p, max_hit_ids=64)
+    nh = fwd["n_hits"]
+    r = int(torch.nonzero(nh > 0)[0])
+    fwd["hit_ids"][r, 0] = sc.means.shape[0]          # one past the last surfel
+    gf = torch.ones((ro.shape[0], 3), device="cuda")
+    irgs.trace_backward(S, dev(ro), dev(rd), p, fwd, gf)
+    assert S.status() & 4
+
+
+def test_autograd_with_saved_hits_equals_replay():
+    sc = synth.object_scene(n=6_000, seed=49)
+    ro, rd = synth.camera_batch_rays(synth.hemisphere_cameras(1, seed=49), 48, 48, tile=(8, 4))
+    p = irgs.TraceParams(k=16, feat_count=10)
+    gf, gd, go = (dev(a) for a in synth.upstream_grads(ro.shape[0], 10, seed=50))
+    grads = []
+    for saved in (0, 96):
+        leaves = [dev(a).requires_grad_(True) for a in sc.arrays()]
+        S = irgs.Scene(*leaves)
+        feat, depth, opac, _ = irgs.trace(S, dev(ro), dev(rd), p, max_saved_hits=saved)
+        ((feat * gf).sum() + (depth * gd).sum() + (opac * go).sum()).backward()
+        grads.append({k: l.grad for k, l in zip(NAMES, leaves)})
+    _grads_close(grads[1], grads[0])
