@@ -1,5 +1,7 @@
-// Backward trace kernel: replays each ray's march (trace_bwd.cuh) and adds
-// the surfel gradients into the caller's user-order arrays.
+// Backward trace kernels: each ray's hits come from the forward's saved hit
+// list or from a replay of its march (trace_bwd.cuh); the surfel gradients
+// are accumulated in Morton order and then added into the caller's
+// user-order arrays.
 #include <cuda_runtime.h>
 
 #include "scene.h"
@@ -11,7 +13,38 @@ namespace {
 
 constexpr int kBwdThreads = 128;
 
-template <int K, int FB, bool WARP>
+// Which rays a launch handles.
+enum BwdMode {
+    kReplayAll = 0,    // every ray replays the march (no hit lists)
+    kListed = 1,       // rays whose whole hit list was saved; no traversal code
+    kReplayLong = 2,   // rays whose hit list did not fit replay the march
+};
+
+// Per-ray inputs of the backward (forward outputs and upstream gradients).
+template <int FB>
+struct RayGrad {
+    float gC[FB], Cf[FB];
+    float gD, gO, Df, Tfin;
+};
+
+template <int FB>
+__device__ __forceinline__ void load_ray_grad(RayGrad<FB>& g, int64_t q, const TraceParams& P,
+                                              const float* __restrict__ out_feat, const float* __restrict__ out_depth,
+                                              const float* __restrict__ out_opac, const float* __restrict__ g_featv,
+                                              const float* __restrict__ g_depthv,
+                                              const float* __restrict__ g_opacv) {
+#pragma unroll
+    for (int c = 0; c < FB; ++c) {
+        g.gC[c] = c < P.fc ? g_featv[q * P.fc + c] : 0.f;
+        g.Cf[c] = c < P.fc ? out_feat[q * P.fc + c] : 0.f;
+    }
+    g.gD = g_depthv != nullptr ? g_depthv[q] : 0.f;
+    g.gO = g_opacv != nullptr ? g_opacv[q] : 0.f;
+    g.Df = out_depth[q];
+    g.Tfin = 1.0f - out_opac[q];
+}
+
+template <int K, int FB, bool WARP, int MODE>
 __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
     SceneView S, const float* __restrict__ ro, const float* __restrict__ rd, int64_t R, TraceParams P,
     const float* __restrict__ out_feat, const float* __restrict__ out_depth, const float* __restrict__ out_opac,
@@ -25,31 +58,24 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
     const int64_t r = blockIdx.x * (int64_t)kBwdThreads + threadIdx.x;
     if (S.n == 0) return;
     const int nh_total = r < R ? out_nhits[r] : 0;
-    const bool live = nh_total > 0;
-    if (!WARP && !live) return;
-    const int64_t q = live ? r : 0;   // lanes without work follow the warp with a dummy ray
+    const bool mine = nh_total > 0 && (MODE == kReplayAll || (MODE == kListed) == (nh_total <= max_ids));
+    if (MODE == kListed || !WARP) {
+        if (!mine) return;
+    } else if (!__any_sync(kFullWarp, mine)) {
+        return;   // the whole warp has nothing to replay
+    }
+    const int64_t q = mine ? r : 0;   // lanes without work follow the warp with a dummy ray
     const Ray ray = make_ray(mk3(ro[3 * q], ro[3 * q + 1], ro[3 * q + 2]),
                              mk3(rd[3 * q], rd[3 * q + 1], rd[3 * q + 2]));
-    float gC[FB], Cf[FB];
-#pragma unroll
-    for (int c = 0; c < FB; ++c) {
-        gC[c] = c < P.fc ? g_featv[q * P.fc + c] : 0.f;
-        Cf[c] = c < P.fc ? out_feat[q * P.fc + c] : 0.f;
-    }
-    const float gD = g_depthv != nullptr ? g_depthv[q] : 0.f;
-    const float gO = g_opacv != nullptr ? g_opacv[q] : 0.f;
-    const float Df = out_depth[q], Tfin = 1.0f - out_opac[q];
-    // rays whose whole hit list was saved skip the traversal; the others
-    // (list absent or longer than max_ids) replay the march
-    const bool listed = live && hit_ids != nullptr && nh_total <= max_ids;
-    if (listed)
-        listed_backward<FB>(S, ray, P, hit_ids + q * (int64_t)max_ids, nh_total, Cf, Df, Tfin, gC, gD, gO, acc_rows,
-                            rows);
-    const bool replay = live && !listed;
-    if (WARP ? __any_sync(kFullWarp, replay) : replay) {
-        const bool ok = march_backward<K, FB, WARP>(S, ray, P, replay, nh_total, Cf, Df, Tfin, gC, gD, gO, acc_rows,
-                                                    rows);
-        if (replay && !ok) atomicOr(S.status, kErrStackOverflow);
+    RayGrad<FB> g;
+    load_ray_grad<FB>(g, q, P, out_feat, out_depth, out_opac, g_featv, g_depthv, g_opacv);
+    if (MODE == kListed) {
+        listed_backward<FB>(S, ray, P, hit_ids + q * (int64_t)max_ids, nh_total, g.Cf, g.Df, g.Tfin, g.gC, g.gD,
+                            g.gO, acc_rows, rows);
+    } else {
+        const bool ok = march_backward<K, FB, WARP>(S, ray, P, mine, nh_total, g.Cf, g.Df, g.Tfin, g.gC, g.gD, g.gO,
+                                                    acc_rows, rows);
+        if (mine && !ok) atomicOr(S.status, kErrStackOverflow);
     }
 }
 
@@ -75,8 +101,19 @@ cudaError_t launch(const SceneView& S, const TraceParams& P, const BwdArgs& a, c
     e = cudaMemsetAsync(acc_rows, 0, bytes, st);
     if (e == cudaSuccess) {
         const int64_t blocks = (a.R + kBwdThreads - 1) / kBwdThreads;
-        k_trace_backward<K, FB, WARP><<<(unsigned)blocks, kBwdThreads, 0, st>>>(
-            S, a.ro, a.rd, a.R, P, a.feat, a.depth, a.opac, a.nhits, a.ids, a.max_ids, a.gf, a.gd, a.go, acc_rows);
+        const unsigned grid = (unsigned)blocks;
+#define IRGS_BWD(MODE)                                                                                  \
+    k_trace_backward<K, FB, WARP, MODE><<<grid, kBwdThreads, 0, st>>>(S, a.ro, a.rd, a.R, P, a.feat, a.depth, \
+                                                                      a.opac, a.nhits, a.ids, a.max_ids, a.gf, \
+                                                                      a.gd, a.go, acc_rows)
+        if (a.ids != nullptr) {
+            IRGS_BWD(kListed);
+            IRGS_BWD(kReplayLong);
+            count_launches(1);
+        } else {
+            IRGS_BWD(kReplayAll);
+        }
+#undef IRGS_BWD
         if (S.n > 0)
             k_grad_scatter<FB><<<(unsigned)((S.n + 255) / 256), 256, 0, st>>>(a.perm, S.n, acc_rows, P.fc, S.F, P.off,
                                                                              a.gm, a.gq, a.gs, a.gop, a.gfe);
