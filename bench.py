@@ -47,7 +47,12 @@ FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM traffic per launch of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) scaled per ray; keyed by
 # the hash of the sources it was measured on (null once they change).
-TRAFFIC = {}
+# Captured on the 10-camera case (6.4M rays; the ~90 MB scene read is ~5% of
+# it, so the per-ray figure slightly overstates a 64M-ray launch).
+TRAFFIC = {
+    "k_trace_forward<16,10>": {"bytes_per_ray": (719.0e6 + 1012.6e6) / 6.4e6, "src_hash": "a016fbfbf5f8"},
+    "k_trace_backward<16,10>": {"bytes_per_ray": (1948.3e6 + 187.7e6) / 6.4e6, "src_hash": "bafef88a9786"},
+}
 
 
 def _kernel_hash(files):
@@ -258,7 +263,7 @@ def run_ours(args):
     if bwd_ms >= fwd_ms:
         kname, kms = "k_trace_backward<16,10>", bwd_ms
         flops = algorithmic_flops(nh, 16, sc.n, F, backward=True, saved_hits=args.saved_hits)
-        src = ["trace.cuh", "trace_bwd.cu", "common.cuh"]
+        src = ["trace.cuh", "trace_bwd.cuh", "trace_bwd.cu", "common.cuh"]
     else:
         kname, kms = "k_trace_forward<16,10>", fwd_ms
         flops = algorithmic_flops(nh, 16, sc.n, F)
