@@ -402,6 +402,13 @@ def mc_leg(args, dev):
     torch.cuda.synchronize()
     fms = ev[0].elapsed_time(ev[1]) / reps
     bms = ev[1].elapsed_time(ev[2]) / reps
+    # the fused kernel (a warp per point tracing its own samples), for reference
+    pf = ps.with_(flags=irgs.FLAG_PER_THREAD)
+    ev[0].record(stream)
+    irgs.shade_mc(S2, *g2, env, 32, 32, 2024, pf, out=o2)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    fused_ms = ev[0].elapsed_time(ev[1])
     rays = Pn * 64
     if S2.status() != 0:
         raise RuntimeError("device error in the MC leg")
@@ -409,7 +416,9 @@ def mc_leg(args, dev):
     return {"workload": f"{args.mc_surfels} surfels, {Pn} G-buffer points x (32 cosine + 32 GGX) = "
                         f"{rays / 1e6:.1f}M secondary rays, 512x256 env, k=16",
             "ms": fms, "mrays_s": rays / (fms * 1e-3) / 1e6, "points_per_s": Pn / (fms * 1e-3),
-            "bwd_ms": bms, "bwd_mrays_s": rays / (bms * 1e-3) / 1e6}
+            "bwd_ms": bms, "bwd_mrays_s": rays / (bms * 1e-3) / 1e6,
+            "path": "secondary rays regrouped by direction bin and origin Morton code, one stack per ray",
+            "fused_per_lane_ms": fused_ms}
 
 
 def serve_leg(args, dev):

@@ -43,6 +43,14 @@ irgs_status use_device(const irgs_scene sc) {
     return cudaSetDevice(sc->device) == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
 }
 
+// Shading runs as one fused kernel (a warp per point tracing its own
+// samples) when a traversal flag is given, else as the regrouped wavefront.
+bool fused_shading(const irgs_trace_params* p) {
+    return (p->flags & (IRGS_FLAG_PER_THREAD | IRGS_FLAG_WARP)) != 0u;
+}
+
+int shade_mode(const irgs_trace_params* p) { return (p->flags & IRGS_FLAG_UNIFORM) ? 1 : 0; }
+
 irgs_status check_shade(const irgs_scene sc, const irgs_trace_params* params, int64_t n_points, const float* env,
                         int32_t env_h, int32_t env_w, int32_t n_diffuse, int32_t n_spec) {
     if (sc == nullptr || n_points < 0) return IRGS_ERR_INVALID_ARG;
@@ -233,8 +241,13 @@ irgs_status irgs_shade_mc(irgs_scene sc, const float* x, const float* n, const f
     if (s != IRGS_OK) return s;
     if (n_points > 0 && (!x || !n || !albedo || !rough || !wo || !out_rgb)) return IRGS_ERR_INVALID_ARG;
     if ((s = use_device(sc)) != IRGS_OK) return s;
-    return irgs::launch_shade_mc(sc->view(), x, n, albedo, rough, wo, n_points, env, env_h, env_w, n_diffuse, n_spec,
-                                 seed, *params, out_rgb, out_vis, out_ind, static_cast<cudaStream_t>(stream));
+    if (fused_shading(params))
+        return irgs::launch_shade_mc(sc->view(), x, n, albedo, rough, wo, n_points, env, env_h, env_w, n_diffuse,
+                                     n_spec, seed, *params, out_rgb, out_vis, out_ind,
+                                     static_cast<cudaStream_t>(stream));
+    return irgs::launch_shade_wave(sc->view(), sc->bounds, x, n, albedo, rough, wo, n_points, env, env_h, env_w,
+                                   n_diffuse, n_spec, seed, shade_mode(params), *params, out_rgb, out_vis, out_ind,
+                                   static_cast<cudaStream_t>(stream));
 }
 
 irgs_status irgs_shade_mc_backward(irgs_scene sc, const float* x, const float* n, const float* albedo,
@@ -249,10 +262,15 @@ irgs_status irgs_shade_mc_backward(irgs_scene sc, const float* x, const float* n
         return IRGS_ERR_INVALID_ARG;
     if (sc->n > 0 && (!g_means || !g_quats || !g_scales || !g_opacity || !g_features)) return IRGS_ERR_INVALID_ARG;
     if ((s = use_device(sc)) != IRGS_OK) return s;
-    return irgs::launch_shade_mc_backward(sc->view(), sc->perm, x, n, albedo, rough, wo, n_points, env, env_h, env_w,
-                                          n_diffuse, n_spec, seed, *params, g_rgb, g_albedo, g_rough, g_env, g_means,
-                                          g_quats, g_scales, g_opacity, g_features,
-                                          static_cast<cudaStream_t>(stream));
+    if (fused_shading(params))
+        return irgs::launch_shade_mc_backward(sc->view(), sc->perm, x, n, albedo, rough, wo, n_points, env, env_h,
+                                              env_w, n_diffuse, n_spec, seed, *params, g_rgb, g_albedo, g_rough,
+                                              g_env, g_means, g_quats, g_scales, g_opacity, g_features,
+                                              static_cast<cudaStream_t>(stream));
+    return irgs::launch_shade_wave_backward(sc->view(), sc->perm, sc->bounds, x, n, albedo, rough, wo, n_points, env,
+                                            env_h, env_w, n_diffuse, n_spec, seed, shade_mode(params), *params,
+                                            g_rgb, g_albedo, g_rough, g_env, g_means, g_quats, g_scales, g_opacity,
+                                            g_features, static_cast<cudaStream_t>(stream));
 }
 
 irgs_status irgs_build_lbvh_noalloc(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,

@@ -522,6 +522,28 @@ static irgs_status enqueue_build(irgs_scene sc, const irgs_surfels* s, cudaStrea
     return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
 }
 
+int64_t sort_hist_words(int64_t n) {
+    const int64_t tiles = (n + kTile - 1) / kTile;
+    return 256 * (tiles > 0 ? tiles : 1);
+}
+
+cudaError_t sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp, int32_t* vals_tmp, uint32_t* hist,
+                       int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t tiles = (n + kTile - 1) / kTile;
+    uint32_t* ka = keys; int32_t* va = vals;
+    uint32_t* kb = keys_tmp; int32_t* vb = vals_tmp;
+    for (int shift = 0; shift < 32; shift += 8) {
+        k_sort_hist<<<(unsigned)tiles, 256, 0, st>>>(ka, n, shift, (int)tiles, hist);
+        k_scan_exclusive<<<1, 1024, 0, st>>>(hist, 256 * tiles);
+        k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(ka, va, n, shift, (int)tiles, hist, kb, vb);
+        uint32_t* tk = ka; ka = kb; kb = tk;
+        int32_t* tv = va; va = vb; vb = tv;
+    }
+    count_launches(12);
+    return cudaGetLastError();
+}
+
 irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_t st, irgs_scene* out) {
     const int64_t n = s->n;
     const int32_t F = s->num_features;

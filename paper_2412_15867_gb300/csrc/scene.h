@@ -65,6 +65,12 @@ irgs_status update_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t
 irgs_status build_lbvh_noalloc_impl(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,
                                     float* nodes, float* leaf_boxes, cudaStream_t st);
 void free_scene(irgs_scene sc);
+// Stable LSD radix sort of (keys, vals) pairs by all 32 key bits (four 8-bit
+// passes; the result ends in keys/vals). keys_tmp/vals_tmp hold n entries,
+// hist sort_hist_words(n) words.
+int64_t sort_hist_words(int64_t n);
+cudaError_t sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp, int32_t* vals_tmp, uint32_t* hist,
+                       int64_t n, cudaStream_t st);
 
 // trace_fwd.cu
 irgs_status launch_trace_forward(const SceneView& sv, const float* ro, const float* rd, int64_t R,
@@ -86,6 +92,20 @@ irgs_status launch_shade_mc(const SceneView& sv, const float* x, const float* n,
                             int32_t W, int32_t n_diffuse, int32_t n_spec, uint64_t seed,
                             const irgs_trace_params& p, float* rgb, float* vis, float* ind,
                             cudaStream_t st);
+// shade_wave.cu: the same estimates and gradients with the secondary rays
+// regrouped by direction and origin (bounds: the scene's ordered-bit centre
+// bounds)
+irgs_status launch_shade_wave(const SceneView& sv, const uint32_t* bounds, const float* x, const float* n,
+                              const float* albedo, const float* rough, const float* wo, int64_t P, const float* env,
+                              int32_t H, int32_t W, int32_t n_diffuse, int32_t n_spec, uint64_t seed, int mode,
+                              const irgs_trace_params& p, float* rgb, float* vis, float* ind, cudaStream_t st);
+irgs_status launch_shade_wave_backward(const SceneView& sv, const int32_t* perm, const uint32_t* bounds,
+                                       const float* x, const float* n, const float* albedo, const float* rough,
+                                       const float* wo, int64_t P, const float* env, int32_t H, int32_t W,
+                                       int32_t n_diffuse, int32_t n_spec, uint64_t seed, int mode,
+                                       const irgs_trace_params& p, const float* g_rgb, float* g_albedo,
+                                       float* g_rough, float* g_env, float* g_means, float* g_quats, float* g_scales,
+                                       float* g_opacity, float* g_features, cudaStream_t st);
 irgs_status launch_shade_mc_backward(const SceneView& sv, const int32_t* perm, const float* x, const float* n,
                                      const float* albedo, const float* rough, const float* wo, int64_t P,
                                      const float* env, int32_t H, int32_t W, int32_t n_diffuse, int32_t n_spec,

@@ -87,24 +87,7 @@ __global__ void __launch_bounds__(kShadeThreads) k_shade_backward(
         MarchState<K, 3> st;
         ok &= march_forward<K, 3, WARP>(S, ray, TP, st, nullptr, 0, d.valid);
         float gL[3] = {0.f, 0.f, 0.f}, gO = 0.f;
-        if (d.valid) {
-            const float V = st.T;
-            const f3 Ld = env_lookup(env, H, W, d.wi);
-            const float Ldv[3] = {Ld.x, Ld.y, Ld.z};
-            const SampleWeight w = sample_weight(F, d, mode, nd, ns, St, true);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float Li = V * Ldv[c] + st.C[c];
-                gL[c] = g[c] * (w.wa * av[c] + w.ws);
-                ga[c] += g[c] * w.wa * Li;
-                gr += g[c] * w.ws * w.dln * Li;
-                gO -= gL[c] * Ldv[c];
-            }
-            if (g_env != nullptr) {
-                const float ge[3] = {gL[0] * V, gL[1] * V, gL[2] * V};
-                env_lookup_grad(g_env, H, W, d.wi, ge);
-            }
-        }
+        if (d.valid) sample_grad(F, d, mode, nd, ns, St, av, g, st.C, st.T, env, H, W, g_env, ga, gr, gL, gO);
         const bool live = d.valid && st.nh > 0;
         if (!WARP && !live) continue;
         ok &= march_backward<K, 3, WARP>(S, ray, TP, live, st.nh, st.C, st.D, st.T, gL, 0.f, gO, acc_rows, rows);

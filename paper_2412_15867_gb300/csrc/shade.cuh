@@ -231,6 +231,34 @@ __device__ __forceinline__ SampleWeight sample_weight(const ShadeFrame& F, const
     return w;
 }
 
+// Gradient of one valid sample's estimate term (directions held fixed),
+// given its trace (L_ind = C, visibility V) and the point's upstream g:
+// adds g_c w_a L_i,c to ga, sum_c g_c w_s (d ln f_s/dr) L_i,c to gr, the
+// bilinear taps of gL_c V to g_env (if not NULL), and returns the upstream
+// gradient of the trace: gL_c = g_c (w_a a_c + w_s), gO = -gL.L_dir.
+__device__ __forceinline__ void sample_grad(const ShadeFrame& F, const ShadeSample& d, int mode, int nd, int ns,
+                                            int St, const float (&av)[3], const float (&g)[3], const float (&C)[3],
+                                            float V, const float* __restrict__ env, int H, int W,
+                                            float* __restrict__ g_env, float (&ga)[3], float& gr, float (&gL)[3],
+                                            float& gO) {
+    const f3 Ld = env_lookup(env, H, W, d.wi);
+    const float Ldv[3] = {Ld.x, Ld.y, Ld.z};
+    const SampleWeight w = sample_weight(F, d, mode, nd, ns, St, true);
+    gO = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float Li = V * Ldv[c] + C[c];
+        gL[c] = g[c] * (w.wa * av[c] + w.ws);
+        ga[c] += g[c] * w.wa * Li;
+        gr += g[c] * w.ws * w.dln * Li;
+        gO -= gL[c] * Ldv[c];
+    }
+    if (g_env != nullptr) {
+        const float ge[3] = {gL[0] * V, gL[1] * V, gL[2] * V};
+        env_lookup_grad(g_env, H, W, d.wi, ge);
+    }
+}
+
 struct ShadeSums {
     float rgb[3];   // the estimate of Eq. 15
     float vis;      // mean V over the cosine samples (split) or all samples (uniform)
@@ -238,12 +266,14 @@ struct ShadeSums {
 };
 
 // All 32 lanes of a warp call this with the same point; every lane returns
-// the point's sums. WARP selects the warp-coherent traversal.
-template <int K, bool WARP>
+// the point's sums. WARP selects the warp-coherent traversal. With TRACED the
+// samples' traces were made beforehand: traced[s] = (L_ind, V) of sample s
+// of this point (the same values the march gives), and nothing is traced.
+template <int K, bool WARP, bool TRACED = false>
 __device__ __forceinline__ void shade_point_warp(const SceneView& S, f3 x, f3 n_in, f3 wo_in, f3 a, float rough,
                                                  uint64_t p, int nd, int ns, int mode, uint64_t seed,
                                                  const float* __restrict__ env, int H, int W, const TraceParams& TP,
-                                                 ShadeSums& out) {
+                                                 ShadeSums& out, const float4* __restrict__ traced = nullptr) {
     const int lane = threadIdx.x & 31;
     const ShadeFrame F = shade_frame(n_in, wo_in, rough);
     const int St = nd + ns;
@@ -252,12 +282,20 @@ __device__ __forceinline__ void shade_point_warp(const SceneView& S, f3 x, f3 n_
     // whole warp so the warp-coherent walk keeps every lane in the loop
     for (int base = 0; base < St; base += 32) {
         const ShadeSample d = draw_sample(F, mode, p, base + lane, St, nd, seed);
-        if (!WARP && !d.valid) continue;
-        const Ray ray = make_ray(x, d.wi);
+        if ((TRACED || !WARP) && !d.valid) continue;
         MarchState<K, 3> st;
-        const bool ok = march_forward<K, 3, WARP>(S, ray, TP, st, nullptr, 0, d.valid);
-        if (!d.valid) continue;
-        if (!ok) atomicOr(S.status, kErrStackOverflow);
+        if (TRACED) {
+            const float4 t = __ldg(traced + base + lane);
+            st.C[0] = t.x;
+            st.C[1] = t.y;
+            st.C[2] = t.z;
+            st.T = t.w;
+        } else {
+            const Ray ray = make_ray(x, d.wi);
+            const bool ok = march_forward<K, 3, WARP>(S, ray, TP, st, nullptr, 0, d.valid);
+            if (!d.valid) continue;
+            if (!ok) atomicOr(S.status, kErrStackOverflow);
+        }
         const float V = st.T;
         const f3 Ld = env_lookup(env, H, W, d.wi);
         const float Li[3] = {V * Ld.x + st.C[0], V * Ld.y + st.C[1], V * Ld.z + st.C[2]};

@@ -121,16 +121,36 @@ def test_mc_config_full_size_sampled():
     print(check(sub, ref, frac=0.95))
 
 
-def test_shading_traversal_modes_identical():
+@pytest.mark.parametrize("mode", ["split", "uniform"])
+def test_shading_paths_agree(mode):
+    """The regrouped wavefront (default) and the fused kernels (per-lane or
+    warp-coherent walk) trace the same rays; the kernels may round the
+    estimator arithmetic differently."""
     sc = synth.object_scene(n=10_000, seed=91)
     x, n, a, r, wo = synth.gbuffer_points(50, seed=92)
     env = synth.env_map(seed=93, height=32, width=64)
     S = make_scene(irgs, sc)
     p = irgs.TraceParams(k=16, feat_count=3, t_min=1e-3)
-    args = (dev(x), dev(n), dev(a), dev(r), dev(wo), dev(env), 21, 19, 5)
-    o1 = irgs.shade_mc(S, *args, p, want_aux=True)
-    o2 = irgs.shade_mc(S, *args, p.with_(flags=irgs.FLAG_WARP), want_aux=True)
-    # the traces are identical; the two kernel instantiations may round the
-    # estimator arithmetic differently
-    for k in o1:
-        assert torch.allclose(o1[k], o2[k], rtol=1e-6, atol=1e-6), k
+    nd, ns = (21, 19) if mode == "split" else (40, 0)
+    args = (dev(x), dev(n), dev(a), dev(r), dev(wo), dev(env), nd, ns, 5)
+    o1 = irgs.shade_mc(S, *args, p, want_aux=True, mode=mode)
+    for fl in (irgs.FLAG_WARP, irgs.FLAG_PER_THREAD):
+        o2 = irgs.shade_mc(S, *args, p.with_(flags=fl), want_aux=True, mode=mode)
+        for k in o1:
+            assert torch.allclose(o1[k], o2[k], rtol=1e-6, atol=1e-6), (fl, k)
+    torch.cuda.synchronize()
+    assert S.status() == 0
+
+
+def test_wavefront_handles_invalid_samples_and_ragged_points():
+    """GGX samples below the horizon (grazing w_o, rough lobes) and a point
+    count that leaves a partial warp: every point still matches the oracle."""
+    sc = synth.object_scene(n=5_000, seed=94)
+    x, n, a, r, wo = synth.gbuffer_points(37, seed=95)
+    r[:] = np.float32(0.95)
+    wo = (wo + 3.0 * n).astype(np.float32)          # mostly fine; make a few grazing:
+    wo[::5] = (n[::5] * 0.02 + np.cross(n[::5], [0, 0, 1.0]) + 1e-3).astype(np.float32)
+    env = synth.env_map(seed=96, height=32, width=64)
+    p = irgs.TraceParams(k=8, feat_count=3, t_min=1e-3)
+    out, ref = shade_both(sc, (x, n, a, r, wo), env, 5, 27, 13, p)
+    check(out, ref, frac=0.97)

@@ -67,12 +67,13 @@ def grads_both(sc, gb, env, nd, ns, seed, p, mode, flags_seed=11):
     return {k: v.detach().cpu().numpy() for k, v in out.items()}, ref, keep
 
 
-@pytest.mark.parametrize("mode,nd,ns,k", [("split", 24, 24, 16), ("uniform", 40, 0, 16), ("split", 9, 7, 8)])
-def test_shading_gradient_matches_oracle(mode, nd, ns, k):
+@pytest.mark.parametrize("mode,nd,ns,k,flags", [("split", 24, 24, 16, 0), ("uniform", 40, 0, 16, 0),
+                                                ("split", 9, 7, 8, 0), ("split", 24, 24, 16, 1)])
+def test_shading_gradient_matches_oracle(mode, nd, ns, k, flags):
     sc = synth.object_scene(n=8_000, seed=201)
     gb = synth.gbuffer_points(48, seed=202)
     env = synth.env_map(seed=203, height=32, width=64)
-    p = irgs.TraceParams(k=k, feat_count=3, t_min=1e-3)
+    p = irgs.TraceParams(k=k, feat_count=3, t_min=1e-3, flags=flags)
     got, ref, keep = grads_both(sc, gb, env, nd, ns, 77, p, mode)
     worst = {}
     for name in SURFEL + ("env",):
@@ -97,12 +98,13 @@ def test_shading_gradient_traversal_modes_agree():
     p = irgs.TraceParams(k=16, feat_count=3, t_min=1e-3)
     args = (dev(x), dev(n), dev(a), dev(r), dev(wo), dev(env), 17, 15, 3)
     g1 = irgs.shade_mc_backward(S, *args, p, g)
-    g2 = irgs.shade_mc_backward(S, *args, p.with_(flags=irgs.FLAG_WARP), g)
-    torch.cuda.synchronize()
-    # same traces and per-sample arithmetic; atomics reorder the sums
-    for k in g1:
-        scale = max(float(g1[k].abs().max()), 1e-30)
-        assert float((g1[k] - g2[k]).abs().max()) <= 1e-5 * scale, k
+    for fl in (irgs.FLAG_WARP, irgs.FLAG_PER_THREAD):
+        g2 = irgs.shade_mc_backward(S, *args, p.with_(flags=fl), g)
+        torch.cuda.synchronize()
+        # same traces and per-sample arithmetic; atomics reorder the sums
+        for k in g1:
+            scale = max(float(g1[k].abs().max()), 1e-30)
+            assert float((g1[k] - g2[k]).abs().max()) <= 1e-5 * scale, (fl, k)
 
 
 def test_zero_upstream_gradient_adds_nothing():
