@@ -79,9 +79,12 @@ typedef struct {
 /* Traversal policy (results are identical either way, only speed differs).
  * Default for irgs_trace_forward / irgs_trace_backward: warp-coherent -- the
  * 32 rays of a warp walk one shared stack, best for coherent batches such as
- * camera rays in image order. Default for irgs_shade_mc: per ray.
- * IRGS_FLAG_PER_THREAD forces an independent stack per ray; IRGS_FLAG_WARP
- * forces the warp-coherent walk. Setting both is invalid. */
+ * camera rays in image order. Default for irgs_shade_mc / _backward: the
+ * secondary rays of all points are regrouped by direction and origin and
+ * traced with one stack per ray. IRGS_FLAG_PER_THREAD forces an independent
+ * stack per ray (for shading: the fused kernel, a warp per point tracing its
+ * own samples); IRGS_FLAG_WARP forces the warp-coherent walk (for shading:
+ * the fused kernel with a warp-shared stack). Setting both is invalid. */
 #define IRGS_FLAG_PER_THREAD 1u
 #define IRGS_FLAG_WARP 2u
 /* Shading only (irgs_shade_mc / irgs_shade_mc_backward): the stratified
