@@ -130,6 +130,18 @@ irgs_status irgs_build_scene(const irgs_surfels* surfels, float alpha_min, void*
  */
 irgs_status irgs_update_scene(irgs_scene scene, const irgs_surfels* surfels, void* stream);
 
+/*
+ * Refit an existing scene to new surfel values (same n and num_features)
+ * without rebuilding it: records, boxes and features are recomputed in the
+ * Morton order of the last build, and the boxes of its hierarchy are
+ * refitted bottom-up (the per-iteration BVH update of Sec. 4 done as a
+ * refit). Traces stay exact (every box bounds its subtree); only traversal
+ * speed can degrade as surfels drift from the order the tree was built for,
+ * so callers rebuild with irgs_update_scene now and then. Allocates nothing;
+ * enqueued on `stream`. IRGS_ERR_INVALID_ARG if n or num_features differ.
+ */
+irgs_status irgs_refit_scene(irgs_scene scene, const irgs_surfels* surfels, void* stream);
+
 /* Free a scene and all its device memory (synchronises the device first).
  * NULL is accepted and ignored. */
 irgs_status irgs_destroy_scene(irgs_scene scene);

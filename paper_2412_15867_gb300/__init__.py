@@ -112,9 +112,7 @@ class Scene:
                             self.features.data_ptr() if (n and self.num_features) else None,
                             n, self.num_features)
 
-    def update(self, means=None, quats=None, scales=None, opacity=None, features=None) -> None:
-        """Rebuild the BVH in place after the surfel values changed (same count).
-        Tensors given here replace the stored ones (same shapes)."""
+    def _replace(self, means, quats, scales, opacity, features):
         for name, t in (("means", means), ("quats", quats), ("scales", scales), ("opacity", opacity),
                         ("features", features)):
             if t is not None:
@@ -122,10 +120,24 @@ class Scene:
                 if t.numel() != getattr(self, name).numel():
                     raise ValueError(f"{name} must keep its shape")
                 setattr(self, name, t.reshape(getattr(self, name).shape))
+
+    def update(self, means=None, quats=None, scales=None, opacity=None, features=None) -> None:
+        """Rebuild the BVH in place after the surfel values changed (same count).
+        Tensors given here replace the stored ones (same shapes)."""
+        self._replace(means, quats, scales, opacity, features)
         s = self._surfels()
         with torch.cuda.device(self.device):
             _lib.check(_lib.lib().irgs_update_scene(self.handle, C.byref(s), _stream(self.device)),
                        "irgs_update_scene")
+
+    def refit(self, means=None, quats=None, scales=None, opacity=None, features=None) -> None:
+        """Refit the BVH to changed surfel values, keeping its Morton order and
+        topology (cheaper than update; traces stay exact)."""
+        self._replace(means, quats, scales, opacity, features)
+        s = self._surfels()
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.lib().irgs_refit_scene(self.handle, C.byref(s), _stream(self.device)),
+                       "irgs_refit_scene")
 
     @property
     def handle(self) -> C.c_void_p:

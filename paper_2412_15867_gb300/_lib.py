@@ -41,6 +41,7 @@ P = C.c_void_p
 _SIGS = {
     "irgs_status_string": (C.c_char_p, [C.c_int]),
     "irgs_abi_version": (C.c_int32, []),
+    "irgs_refit_scene": (C.c_int, [P, C.POINTER(Surfels), P]),
     "irgs_kernel_launches": (C.c_uint64, []),
     "irgs_build_scene": (C.c_int, [C.POINTER(Surfels), C.c_float, P, C.POINTER(P)]),
     "irgs_update_scene": (C.c_int, [P, C.POINTER(Surfels), P]),

@@ -117,6 +117,16 @@ irgs_status irgs_update_scene(irgs_scene sc, const irgs_surfels* s, void* stream
     return irgs::update_scene_impl(sc, s, static_cast<cudaStream_t>(stream));
 }
 
+irgs_status irgs_refit_scene(irgs_scene sc, const irgs_surfels* s, void* stream) {
+    if (sc == nullptr || s == nullptr) return IRGS_ERR_INVALID_ARG;
+    if (s->n != sc->n || s->num_features != sc->F) return IRGS_ERR_INVALID_ARG;
+    if (s->n > 0 && (!s->means || !s->quats || !s->scales || !s->opacity)) return IRGS_ERR_INVALID_ARG;
+    if (s->n > 0 && s->num_features > 0 && !s->features) return IRGS_ERR_INVALID_ARG;
+    irgs_status st = use_device(sc);
+    if (st != IRGS_OK) return st;
+    return irgs::refit_scene_impl(sc, s, static_cast<cudaStream_t>(stream));
+}
+
 irgs_status irgs_destroy_scene(irgs_scene sc) {
     if (sc == nullptr) return IRGS_OK;
     cudaSetDevice(sc->device);

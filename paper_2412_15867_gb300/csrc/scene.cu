@@ -604,6 +604,47 @@ irgs_status update_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t
     return enqueue_build(sc, s, st);
 }
 
+// Refit: new surfel values in the Morton order and hierarchy of the last
+// build. Records, leaf boxes and features are recomputed and gathered with
+// the kept permutation, the binary boxes are refitted bottom-up and the
+// 4-wide nodes re-emitted from them (their layout depends only on the
+// topology). Every box still bounds its subtree, so traces stay exact; only
+// the quality of the tree can degrade as surfels move.
+irgs_status refit_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t st) {
+    const int64_t n = sc->n;
+    const int32_t F = sc->F;
+    const int64_t nn = n > 1 ? n - 1 : 1;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(cudaMemsetAsync(sc->refit_flag, 0, sizeof(uint32_t) * nn, st));
+    A(cudaMemsetAsync(sc->bounds, 0xff, 3 * sizeof(uint32_t), st));
+    A(cudaMemsetAsync(sc->bounds + 3, 0x00, 3 * sizeof(uint32_t), st));
+    const int T = 256;
+    if (n > 0) {
+        k_surfel_boxes<<<blocks_for(n, T), T, 0, st>>>(s->means, s->quats, s->scales, s->opacity, n,
+                                                       (double)sc->alpha_min, sc->rec_user, sc->box_user, sc->bounds);
+        k_gather<<<blocks_for(n, T), T, 0, st>>>(sc->perm, n, sc->rec_user, sc->box_user, s->quats, s->scales,
+                                                 sc->rec, sc->leaf_box, sc->q_raw, sc->scale, sc->inv_perm);
+        if (F > 0)
+            k_gather_feat<<<blocks_for(n * F, T), T, 0, st>>>(sc->perm, n, F, s->features, sc->feat);
+        if (n > 1)
+            k_refit<<<blocks_for(n, T), T, 0, st>>>(n, sc->leaf_box, sc->leaf_parent, sc->node_parent, sc->nodes,
+                                                    sc->refit_flag, sc->status);
+    }
+    if (n <= 1) k_tiny_root<<<1, 1, 0, st>>>(n, sc->leaf_box, sc->nodes);
+    if (n > 1) {
+        k_wide_mark<<<blocks_for(n - 1, T), T, 0, st>>>(n, sc->node_parent, sc->refit_flag, sc->status);
+        k_wide_emit<<<blocks_for(n - 1, T), T, 0, st>>>(n, sc->nodes, sc->refit_flag, sc->wide_rank, sc->max_wide,
+                                                       sc->wide, sc->status);
+    } else {
+        k_wide_tiny<<<1, 1, 0, st>>>(n, sc->leaf_box, sc->wide);
+    }
+    // boxes, gather, features, refit, mark, emit (or the tiny root and tiny wide node)
+    count_launches(n == 0 ? 2 : (n == 1 ? 4 + (F > 0) : 5 + (F > 0)));
+    A(cudaGetLastError());
+    return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free build: all working memory of the build comes from one
 // file-scope device array; the caller provides the outputs.

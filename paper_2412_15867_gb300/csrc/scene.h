@@ -62,6 +62,7 @@ namespace irgs {
 // scene.cu
 irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_t st, irgs_scene* out);
 irgs_status update_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t st);
+irgs_status refit_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t st);
 irgs_status build_lbvh_noalloc_impl(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,
                                     float* nodes, float* leaf_boxes, cudaStream_t st);
 void free_scene(irgs_scene sc);
