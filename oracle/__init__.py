@@ -117,6 +117,13 @@ def _load():
     lib.oracle_sample_dirs.argtypes = [P, P, P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P]
     lib.oracle_num_threads.restype = C.c_int
     lib.oracle_num_threads.argtypes = [C.c_int]
+    lib.oracle_relight_maps.restype = C.c_int
+    lib.oracle_relight_maps.argtypes = [P, C.c_int32, C.c_int32, C.c_int, P, P, P, P, P]
+    lib.oracle_env_samples.restype = C.c_int
+    lib.oracle_env_samples.argtypes = [P, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_uint64, P, P]
+    lib.oracle_relight.restype = C.c_int
+    lib.oracle_relight.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P, P, P, P, P, C.c_int64,
+                                   P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P, P, P, P, P, P, C.c_int]
     _lib = lib
     return lib
 
@@ -296,3 +303,63 @@ def sample_dirs(nrm, wo, rough, n_diffuse: int, n_spec: int, seed: int, mode: in
     lib.oracle_sample_dirs(_ptr(nrm), _ptr(wo), _ptr(rough), Pn, n_diffuse, n_spec, int(mode),
                            C.c_uint64(seed & (2**64 - 1)), _ptr(dirs), _ptr(valid))
     return dirs, valid.astype(bool)
+
+
+# Sizes of the relighting maps (supplementary "Relighting details").
+RL_IRR = (32, 64)
+RL_LEVELS = 6
+RL_PREF = (64, 128)
+RL_LUT_N = 32
+
+
+def relight_maps(env, n_threads: int = 0):
+    """Pre-integrated maps of an environment [H,W,3]: irr [32,64,3] (diffuse
+    irradiance), pref [5,64,128,3] (split-sum prefiltered radiance at
+    roughness 0.2..1.0; level 0 is the environment), lut [32,32,2] (split-sum
+    BRDF factors A, B over (n.v, roughness) cell centres), row_cdf [H+1] and
+    col_cdf [H,W+1] (importance-sampling tables)."""
+    env = _f32(env)
+    H, W = env.shape[0], env.shape[1]
+    out = {"irr": np.zeros(RL_IRR + (3,)), "pref": np.zeros((RL_LEVELS - 1,) + RL_PREF + (3,)),
+           "lut": np.zeros((RL_LUT_N, RL_LUT_N, 2)), "row_cdf": np.zeros(H + 1), "col_cdf": np.zeros((H, W + 1))}
+    rc = _load().oracle_relight_maps(_ptr(env), H, W, int(n_threads), _ptr(out["irr"]), _ptr(out["pref"]),
+                                     _ptr(out["lut"]), _ptr(out["row_cdf"]), _ptr(out["col_cdf"]))
+    if rc != 0:
+        raise ValueError("oracle_relight_maps rejected its arguments")
+    return out
+
+
+def env_samples(env, P: int, S: int, seed: int):
+    """Environment importance samples: directions [P,S,3] and pdf [P,S]."""
+    env = _f32(env)
+    dirs = np.zeros((P, S, 3))
+    pdf = np.zeros((P, S))
+    _load().oracle_env_samples(_ptr(env), env.shape[0], env.shape[1], P, S, C.c_uint64(seed & (2**64 - 1)),
+                               _ptr(dirs), _ptr(pdf))
+    return dirs, pdf
+
+
+def relight(scene, x, nrm, albedo, rough, wo, env, n_samples: int, seed: int, params: Params,
+            margins: Margins | None = Margins(), n_threads: int = 0, point_ids=None):
+    """Relighting estimate per point under environment `env` (supplementary
+    "Relighting details"): params.feat_offset / feat_count = 7 select the
+    traced [albedo (3), roughness, normal (3)] channels. Returns rgb [P,3],
+    vis [P], ind [P,3] and flags [P]."""
+    lib = _load()
+    (means, quats, scales, opacity, feats), x, nrm, albedo, rough, wo, env = _shade_inputs(
+        scene, x, nrm, albedo, rough, wo, env)
+    H, W = env.shape[0], env.shape[1]
+    Pn, n, F = x.shape[0], means.shape[0], feats.shape[1]
+    out = {"rgb": np.zeros((Pn, 3)), "vis": np.zeros(Pn), "ind": np.zeros((Pn, 3)),
+           "flags": np.zeros(Pn, np.uint32)}
+    p = params.c()
+    m = margins.c() if margins is not None else None
+    pid = None if point_ids is None else np.ascontiguousarray(point_ids, np.int64).reshape(Pn)
+    rc = lib.oracle_relight(_ptr(means), _ptr(quats), _ptr(scales), _ptr(opacity), _ptr(feats), n, F,
+                            _ptr(x), _ptr(nrm), _ptr(albedo), _ptr(rough), _ptr(wo), Pn, _ptr(env), H, W,
+                            int(n_samples), C.c_uint64(seed & (2**64 - 1)), _ptr(pid), C.byref(p),
+                            C.byref(m) if m is not None else None, _ptr(out["rgb"]), _ptr(out["vis"]),
+                            _ptr(out["ind"]), _ptr(out["flags"]), int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_relight rejected its arguments")
+    return out

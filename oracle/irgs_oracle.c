@@ -878,3 +878,429 @@ int oracle_shade_grad(const float* means, const float* quats, const float* scale
     free(s);
     return err ? -1 : 0;
 }
+
+/* ====================================================================== */
+/* Relighting query (supplementary "Relighting details", Eq. 18; Sec. 4,   */
+/* relighting paragraph): each incident ray blends the albedo, roughness   */
+/* and normal of the surfels it crosses; that aggregate surface is shaded  */
+/* under the new environment with pre-integrated maps (a diffuse           */
+/* irradiance map and the two split-sum factors: a roughness-prefiltered   */
+/* environment and a 2D lookup table of the BRDF integral); directions are */
+/* drawn by importance sampling the environment's intensity.               */
+/* ====================================================================== */
+
+/* Sizes of the pre-integrated maps. */
+enum {
+    RL_IRR_H = 32, RL_IRR_W = 64,             /* irradiance map                      */
+    RL_LEVELS = 6,                            /* prefilter levels, roughness l / 5   */
+    RL_PREF_H = 64, RL_PREF_W = 128,          /* prefiltered levels 1..5             */
+    RL_LUT_N = 32,                            /* LUT cells over (n.v, roughness)     */
+    RL_LUT_SAMPLES = 1024                     /* Hammersley points per LUT cell      */
+};
+
+/* Direction of the centre of texel (row, col) of an H x W equirect map. */
+static void texel_dir(int64_t H, int64_t W, double row, double col, double w[3])
+{
+    double th = (row + 0.5) * OR_PI / (double)H;
+    double ph = (col + 0.5) * 2.0 * OR_PI / (double)W - OR_PI;
+    w[0] = sin(th) * cos(ph);
+    w[1] = sin(th) * sin(ph);
+    w[2] = cos(th);
+}
+
+/* Solid angle of any texel of row `row` (exact band area / W). */
+static double texel_solid_angle(int64_t H, int64_t W, int64_t row)
+{
+    double t0 = row * OR_PI / (double)H, t1 = (row + 1) * OR_PI / (double)H;
+    return (cos(t0) - cos(t1)) * 2.0 * OR_PI / (double)W;
+}
+
+/* Diffuse irradiance map: for each map texel centre N,
+ *   Irr(N) = (1/pi) sum_t E_t max(0, w_t.N) dOmega_t
+ * over all environment texels t (each of constant radiance over its solid
+ * angle, seen from its centre direction w_t). out [RL_IRR_H, RL_IRR_W, 3]. */
+static void relight_irradiance(const float* env, int32_t H, int32_t W, double* out)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < (int64_t)RL_IRR_H * RL_IRR_W; ++i) {
+        double N[3];
+        texel_dir(RL_IRR_H, RL_IRR_W, (double)(i / RL_IRR_W), (double)(i % RL_IRR_W), N);
+        double acc[3] = {0, 0, 0};
+        for (int64_t r = 0; r < H; ++r) {
+            double dO = texel_solid_angle(H, W, r);
+            for (int64_t c = 0; c < W; ++c) {
+                double w[3];
+                texel_dir(H, W, (double)r, (double)c, w);
+                double cs = dot3(w, N);
+                if (cs <= 0.0) continue;
+                const float* e = env + (r * W + c) * 3;
+                for (int k = 0; k < 3; ++k) acc[k] += e[k] * cs * dO;
+            }
+        }
+        for (int k = 0; k < 3; ++k) out[i * 3 + k] = acc[k] / OR_PI;
+    }
+}
+
+/* GGX distribution with alpha_g = r^2 at cos(theta_h) = nh. */
+static double ggx_d(double r, double nh)
+{
+    double a2 = r * r * r * r;
+    double q = nh * nh * (a2 - 1.0) + 1.0;
+    return a2 / (OR_PI * q * q);
+}
+
+/* Prefiltered environment of level l (roughness rho = l / 5, l = 1..5), the
+ * radiance factor of the split sum with n = v = R: for each map texel centre R,
+ *   Pref(R) = sum_t E_t D(R.h_t) max(0, w_t.R) dOmega_t
+ *             / sum_t D(R.h_t) max(0, w_t.R) dOmega_t,   h_t = (w_t + R)/|w_t + R|.
+ * Level 0 is the environment itself. out [RL_PREF_H, RL_PREF_W, 3]. */
+static void relight_prefilter(const float* env, int32_t H, int32_t W, int level, double* out)
+{
+    double rho = (double)level / (double)(RL_LEVELS - 1);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < (int64_t)RL_PREF_H * RL_PREF_W; ++i) {
+        double R[3];
+        texel_dir(RL_PREF_H, RL_PREF_W, (double)(i / RL_PREF_W), (double)(i % RL_PREF_W), R);
+        double acc[3] = {0, 0, 0}, wsum = 0.0;
+        for (int64_t r = 0; r < H; ++r) {
+            double dO = texel_solid_angle(H, W, r);
+            for (int64_t c = 0; c < W; ++c) {
+                double w[3];
+                texel_dir(H, W, (double)r, (double)c, w);
+                double cs = dot3(w, R);
+                if (cs <= 0.0) continue;
+                double h[3] = {w[0] + R[0], w[1] + R[1], w[2] + R[2]};
+                normalize3(h);
+                double wt = ggx_d(rho, dot3(R, h)) * cs * dO;
+                const float* e = env + (r * W + c) * 3;
+                for (int k = 0; k < 3; ++k) acc[k] += e[k] * wt;
+                wsum += wt;
+            }
+        }
+        for (int k = 0; k < 3; ++k) out[i * 3 + k] = wsum > 0.0 ? acc[k] / wsum : 0.0;
+    }
+}
+
+/* Radical inverse in base 2 of i (van der Corput), for Hammersley points. */
+static double radical_inverse2(uint32_t i)
+{
+    double r = 0.0, f = 0.5;
+    while (i) {
+        if (i & 1u) r += f;
+        i >>= 1;
+        f *= 0.5;
+    }
+    return r;
+}
+
+/* Split-sum BRDF table over cell centres mu = (i + 0.5)/N (= n.v) and
+ * rho = (j + 0.5)/N (roughness): the BRDF-times-cosine integral
+ *   int f_s (w.n) dw = F0 A(mu, rho) + B(mu, rho)
+ * with Schlick F = F0 + (1 - F0)(1 - v.h)^5, split as
+ *   A = int (f_s/F)(1 - (1 - v.h)^5)(w.n) dw,  B = int (f_s/F)(1 - v.h)^5 (w.n) dw,
+ * estimated with RL_LUT_SAMPLES Hammersley points ((k + 0.5)/M, radical
+ * inverse of k) mapped to GGX half vectors (pdf D(h) n.h), i.e. per sample
+ * G (v.h)/((n.h)(n.v)) times the Fresnel part, for w = reflect(v, h) above
+ * the surface. out [RL_LUT_N (mu), RL_LUT_N (rho), 2]. */
+static void relight_lut(double* out)
+{
+    for (int i = 0; i < RL_LUT_N; ++i) {
+        for (int j = 0; j < RL_LUT_N; ++j) {
+            double mu = (i + 0.5) / RL_LUT_N, rho = (j + 0.5) / RL_LUT_N;
+            double ag = rho * rho, a2 = ag * ag, kk = 0.5 * ag;
+            double v[3] = {sqrt(1.0 - mu * mu), 0.0, mu};
+            double A = 0.0, B = 0.0;
+            for (int s = 0; s < RL_LUT_SAMPLES; ++s) {
+                double u1 = (s + 0.5) / RL_LUT_SAMPLES, u2 = radical_inverse2((uint32_t)s);
+                double c2 = (1.0 - u1) / (1.0 + (a2 - 1.0) * u1);
+                double ct = sqrt(c2), st = sqrt(1.0 - c2 > 0.0 ? 1.0 - c2 : 0.0);
+                double ph = 2.0 * OR_PI * u2;
+                double h[3] = {st * cos(ph), st * sin(ph), ct};
+                double vh = dot3(v, h);
+                double l[3] = {2.0 * vh * h[0] - v[0], 2.0 * vh * h[1] - v[1], 2.0 * vh * h[2] - v[2]};
+                if (l[2] <= 0.0 || vh <= 0.0) continue;
+                double G = (l[2] / (l[2] * (1.0 - kk) + kk)) * (mu / (mu * (1.0 - kk) + kk));
+                double gv = G * vh / (h[2] * mu);
+                double fc = pow(1.0 - vh, 5.0);
+                A += (1.0 - fc) * gv;
+                B += fc * gv;
+            }
+            out[(i * RL_LUT_N + j) * 2] = A / RL_LUT_SAMPLES;
+            out[(i * RL_LUT_N + j) * 2 + 1] = B / RL_LUT_SAMPLES;
+        }
+    }
+}
+
+/* Importance-sampling tables of the environment: texel weight
+ * w_t = lum(E_t) sin(theta of the row centre), lum = 0.2126 r + 0.7152 g +
+ * 0.0722 b. row_cdf[r] = sum of the weights of rows < r (H + 1 entries);
+ * col_cdf[r (W+1) + c] = sum of the weights of texels (r, < c). */
+static void relight_cdf(const float* env, int32_t H, int32_t W, double* row_cdf, double* col_cdf)
+{
+    row_cdf[0] = 0.0;
+    for (int64_t r = 0; r < H; ++r) {
+        double s = sin((r + 0.5) * OR_PI / (double)H);
+        double* cc = col_cdf + r * (W + 1);
+        cc[0] = 0.0;
+        for (int64_t c = 0; c < W; ++c) {
+            const float* e = env + (r * W + c) * 3;
+            double lum = 0.2126 * e[0] + 0.7152 * e[1] + 0.0722 * e[2];
+            cc[c + 1] = cc[c] + lum * s;
+        }
+        row_cdf[r + 1] = row_cdf[r] + cc[W];
+    }
+}
+
+/* Largest index k in [0, n) with cdf[k] <= t and cdf[k+1] > cdf[k]
+ * (cdf has n + 1 non-decreasing entries, cdf[0] <= t < cdf[n]). */
+static int64_t cdf_find(const double* cdf, int64_t n, double t)
+{
+    int64_t lo = 0, hi = n;   /* invariant: cdf[lo] <= t < cdf[hi] */
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) / 2;
+        if (cdf[mid] <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/* Environment sample from (u1, u2): row by the row cdf at u1 total, column
+ * by that row's cdf at u2 (row total); the fractions left over place the
+ * direction inside the texel uniformly in (phi, theta):
+ *   theta = (row + f_v) pi / H, phi = (col + f_u) 2 pi / W - pi,
+ * pdf (solid angle) = (w_t / total) W H / (2 pi^2 sin theta).
+ * Returns 0 if the environment has no weight. */
+static int env_sample(const double* row_cdf, const double* col_cdf, int32_t H, int32_t W, double u1, double u2,
+                      double w[3], double* pdf)
+{
+    double total = row_cdf[H];
+    if (!(total > 0.0)) return 0;
+    double t1 = u1 * total;
+    int64_t r = cdf_find(row_cdf, H, t1);
+    const double* cc = col_cdf + r * (W + 1);
+    double rw = cc[W];
+    double fv = (t1 - row_cdf[r]) / rw;
+    double t2 = u2 * rw;
+    int64_t c = cdf_find(cc, W, t2);
+    double wt = cc[c + 1] - cc[c];
+    double fu = (t2 - cc[c]) / wt;
+    double th = (r + fv) * OR_PI / (double)H;
+    double ph = (c + fu) * 2.0 * OR_PI / (double)W - OR_PI;
+    double sth = sin(th);
+    w[0] = sth * cos(ph);
+    w[1] = sth * sin(ph);
+    w[2] = cos(th);
+    *pdf = sth > 0.0 ? (wt / total) * (double)W * (double)H / (2.0 * OR_PI * OR_PI * sth) : 0.0;
+    return *pdf > 0.0;
+}
+
+/* Bilinear lookup of an h x w x 3 double map at direction d (same equirect
+ * convention as the environment). */
+static void map_lookup(const double* map, int32_t h, int32_t w, const double d[3], double out[3])
+{
+    int64_t idx[4];
+    double wt[4];
+    env_texels(h, w, d, idx, wt);
+    for (int k = 0; k < 3; ++k) {
+        out[k] = 0.0;
+        for (int t = 0; t < 4; ++t) out[k] += wt[t] * map[idx[t] * 3 + k];
+    }
+}
+
+/* Bilinear lookup of the LUT at (mu, rho), coordinates clamped to the cell
+ * centres. */
+static void lut_lookup(const double* lut, double mu, double rho, double* A, double* B)
+{
+    double x = mu * RL_LUT_N - 0.5, y = rho * RL_LUT_N - 0.5;
+    if (x < 0.0) x = 0.0;
+    if (x > RL_LUT_N - 1) x = RL_LUT_N - 1;
+    if (y < 0.0) y = 0.0;
+    if (y > RL_LUT_N - 1) y = RL_LUT_N - 1;
+    int i0 = (int)floor(x), j0 = (int)floor(y);
+    if (i0 > RL_LUT_N - 2) i0 = RL_LUT_N - 2;
+    if (j0 > RL_LUT_N - 2) j0 = RL_LUT_N - 2;
+    double fx = x - i0, fy = y - j0;
+    double v[2];
+    for (int k = 0; k < 2; ++k) {
+        double a = lut[(i0 * RL_LUT_N + j0) * 2 + k], b = lut[(i0 * RL_LUT_N + j0 + 1) * 2 + k];
+        double c = lut[((i0 + 1) * RL_LUT_N + j0) * 2 + k], d = lut[((i0 + 1) * RL_LUT_N + j0 + 1) * 2 + k];
+        v[k] = (1 - fx) * ((1 - fy) * a + fy * b) + fx * ((1 - fy) * c + fy * d);
+    }
+    *A = v[0];
+    *B = v[1];
+}
+
+/* Pre-integrated maps of one environment. */
+typedef struct {
+    double irr[RL_IRR_H * RL_IRR_W * 3];
+    double pref[(RL_LEVELS - 1) * RL_PREF_H * RL_PREF_W * 3];
+    double lut[RL_LUT_N * RL_LUT_N * 2];
+} relight_maps;
+
+/* Split-sum prefiltered radiance in direction d at roughness rho: linear
+ * between the two nearest levels (level 0 = the environment, bilinear). */
+static void pref_lookup(const relight_maps* M, const float* env, int32_t H, int32_t W, const double d[3],
+                        double rho, double out[3])
+{
+    if (rho < 0.0) rho = 0.0;
+    if (rho > 1.0) rho = 1.0;
+    double t = rho * (RL_LEVELS - 1);
+    int l0 = (int)floor(t);
+    if (l0 > RL_LEVELS - 2) l0 = RL_LEVELS - 2;
+    double f = t - l0;
+    double a[3], b[3];
+    if (l0 == 0)
+        oracle_env_lookup(env, H, W, d, a);
+    else
+        map_lookup(M->pref + (size_t)(l0 - 1) * RL_PREF_H * RL_PREF_W * 3, RL_PREF_H, RL_PREF_W, d, a);
+    map_lookup(M->pref + (size_t)l0 * RL_PREF_H * RL_PREF_W * 3, RL_PREF_H, RL_PREF_W, d, b);
+    for (int k = 0; k < 3; ++k) out[k] = (1.0 - f) * a[k] + f * b[k];
+}
+
+/* Exported maps (for pins and for the GPU maps' parity): irr [32,64,3],
+ * pref [5,64,128,3] (levels 1..5), lut [32,32,2], row_cdf [H+1],
+ * col_cdf [H, W+1]; any pointer may be NULL. */
+int oracle_relight_maps(const float* env, int32_t H, int32_t W, int n_threads, double* irr, double* pref,
+                        double* lut, double* row_cdf, double* col_cdf)
+{
+    if (H <= 0 || W <= 0 || !env) return -1;
+    nthreads_set(n_threads);
+    if (irr) relight_irradiance(env, H, W, irr);
+    if (pref)
+        for (int l = 1; l < RL_LEVELS; ++l)
+            relight_prefilter(env, H, W, l, pref + (size_t)(l - 1) * RL_PREF_H * RL_PREF_W * 3);
+    if (lut) relight_lut(lut);
+    if (row_cdf && col_cdf) relight_cdf(env, H, W, row_cdf, col_cdf);
+    return 0;
+}
+
+/* Environment samples only (for sampler pins): dirs [P, S, 3], pdf [P, S]. */
+int oracle_env_samples(const float* env, int32_t H, int32_t W, int64_t P, int32_t S, uint64_t seed,
+                       double* dirs, double* pdf)
+{
+    double* row_cdf = (double*)malloc(sizeof(double) * (size_t)(H + 1));
+    double* col_cdf = (double*)malloc(sizeof(double) * (size_t)H * (size_t)(W + 1));
+    if (!row_cdf || !col_cdf) { free(row_cdf); free(col_cdf); return -1; }
+    relight_cdf(env, H, W, row_cdf, col_cdf);
+    for (int64_t p = 0; p < P; ++p)
+        for (int64_t s = 0; s < S; ++s) {
+            double w[3] = {0, 0, 1}, q = 0.0;
+            env_sample(row_cdf, col_cdf, H, W, uniform01(seed, p, s, S, 0), uniform01(seed, p, s, S, 1), w, &q);
+            for (int k = 0; k < 3; ++k) dirs[(p * S + s) * 3 + k] = w[k];
+            pdf[p * S + s] = q;
+        }
+    free(row_cdf);
+    free(col_cdf);
+    return 0;
+}
+
+/* Relighting estimate at each point (the point's own BRDF as in the
+ * shading estimate; n flipped towards w_o):
+ *   rgb = 1/S sum_s f(w_s, w_o) L_i(w_s) max(0, w_s.n) / pdf(w_s),
+ * w_s drawn from the environment tables with uniforms (p S + s) 2 + dim of
+ * `seed`. L_i = V E(w) + L_ind with (V, and the blended material) from
+ * tracing (x, w): O = 1 - V, A_r = sum(w a)/O, R_r = sum(w r)/O, N_r the
+ * normalised sum(w n) (the paper's normalised blend weights), flipped to
+ * face v = -w; L_ind = O (A_r Irr(N_r) + Pref(reflect(v, N_r), R_r)
+ * (F0 LUT_A(N_r.v, R_r) + LUT_B(N_r.v, R_r))), F0 = 0.04. The traced
+ * channels (params feat_offset, feat_count = 7) are [a (3), r, n (3)].
+ * Outputs rgb [P,3]; vis [P] and ind [P,3] are means over all samples;
+ * flags [P] ORs the traced rays' ambiguity flags. */
+int oracle_relight(const float* means, const float* quats, const float* scales, const float* opacity,
+                   const float* feats, int64_t n, int32_t F_total,
+                   const float* x_in, const float* n_in, const float* albedo, const float* rough,
+                   const float* wo_in, int64_t Pn, const float* env, int32_t H, int32_t W, int32_t S,
+                   uint64_t seed, const int64_t* point_ids, const oracle_params* P, const oracle_margins* M,
+                   double* out_rgb, double* out_vis, double* out_ind, uint32_t* out_flags, int n_threads)
+{
+    if (n < 0 || Pn < 0 || !P || P->feat_count != 7 || S <= 0 || H <= 0 || W <= 0) return -1;
+    if (P->feat_offset < 0 || P->feat_offset + 7 > F_total) return -1;
+    relight_maps* maps = (relight_maps*)malloc(sizeof(relight_maps));
+    double* row_cdf = (double*)malloc(sizeof(double) * (size_t)(H + 1));
+    double* col_cdf = (double*)malloc(sizeof(double) * (size_t)H * (size_t)(W + 1));
+    surfel64* s = (surfel64*)malloc(sizeof(surfel64) * (size_t)(n > 0 ? n : 1));
+    if (!maps || !row_cdf || !col_cdf || !s) {
+        free(maps); free(row_cdf); free(col_cdf); free(s);
+        return -1;
+    }
+    oracle_relight_maps(env, H, W, n_threads, maps->irr, maps->pref, maps->lut, row_cdf, col_cdf);
+    load_surfels(means, quats, scales, opacity, n, P->alpha_min, s);
+    nthreads_set(n_threads);
+    int err = 0;
+#pragma omp parallel
+    {
+        hit64* hits = (hit64*)malloc(sizeof(hit64) * (size_t)(n > 0 ? n : 1));
+        near64* nears = (near64*)malloc(sizeof(near64) * (size_t)(n > 0 ? n : 1));
+        double* Tl = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        if (!hits || !nears || !Tl) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t p = 0; p < Pn; ++p) {
+                double x[3] = {x_in[3 * p], x_in[3 * p + 1], x_in[3 * p + 2]};
+                double nn[3] = {n_in[3 * p], n_in[3 * p + 1], n_in[3 * p + 2]};
+                double wo[3] = {wo_in[3 * p], wo_in[3 * p + 1], wo_in[3 * p + 2]};
+                double a[3] = {albedo[3 * p], albedo[3 * p + 1], albedo[3 * p + 2]};
+                double r = rough[p];
+                int64_t key = point_ids ? point_ids[p] : p;
+                normalize3(nn);
+                normalize3(wo);
+                if (dot3(nn, wo) <= 0.0) { nn[0] = -nn[0]; nn[1] = -nn[1]; nn[2] = -nn[2]; }
+                double no = dot3(nn, wo);
+                double acc[3] = {0, 0, 0}, sv = 0.0, si[3] = {0, 0, 0};
+                uint32_t fl = 0;
+                for (int64_t sI = 0; sI < S; ++sI) {
+                    double w[3], pdf;
+                    if (!env_sample(row_cdf, col_cdf, H, W, uniform01(seed, key, sI, S, 0),
+                                    uniform01(seed, key, sI, S, 1), w, &pdf))
+                        continue;
+                    int64_t nnr = 0;
+                    int64_t nh = collect_hits(s, n, x, w, P, M, hits, nears, &nnr);
+                    double C[7], D, Tfin;
+                    int64_t nc = composite(hits, nh, feats, F_total, P, C, &D, &Tfin, Tl);
+                    if (M) fl |= resolve_flags(hits, nh, nc, nears, nnr, P, M, Tl, Tfin);
+                    double V = Tfin, O = 1.0 - Tfin, Lind[3] = {0, 0, 0};
+                    if (O > 0.0) {
+                        double Ar[3] = {C[0] / O, C[1] / O, C[2] / O}, Rr = C[3] / O;
+                        double Nr[3] = {C[4], C[5], C[6]}, v[3] = {-w[0], -w[1], -w[2]};
+                        double len = sqrt(dot3(Nr, Nr));
+                        if (len > 1e-12) {
+                            for (int k = 0; k < 3; ++k) Nr[k] /= len;
+                        } else {
+                            for (int k = 0; k < 3; ++k) Nr[k] = v[k];
+                        }
+                        if (dot3(Nr, v) < 0.0) for (int k = 0; k < 3; ++k) Nr[k] = -Nr[k];
+                        double mu = dot3(Nr, v);
+                        if (mu > 1.0) mu = 1.0;
+                        double refl[3], irr[3], pref[3], LA, LB;
+                        for (int k = 0; k < 3; ++k) refl[k] = 2.0 * mu * Nr[k] - v[k];
+                        map_lookup(maps->irr, RL_IRR_H, RL_IRR_W, Nr, irr);
+                        pref_lookup(maps, env, H, W, refl, Rr, pref);
+                        lut_lookup(maps->lut, mu, Rr, &LA, &LB);
+                        for (int k = 0; k < 3; ++k) Lind[k] = O * (Ar[k] * irr[k] + pref[k] * (0.04 * LA + LB));
+                    }
+                    double E[3];
+                    oracle_env_lookup(env, H, W, w, E);
+                    sv += V;
+                    for (int k = 0; k < 3; ++k) si[k] += Lind[k];
+                    double ni = dot3(nn, w);
+                    if (ni <= 0.0) continue;
+                    double h[3] = {w[0] + wo[0], w[1] + wo[1], w[2] + wo[2]};
+                    normalize3(h);
+                    spec_terms t = spec_eval(r, ni, no, dot3(nn, h), dot3(wo, h));
+                    double fs = t.D * t.F * t.G1i * t.G1o / (4.0 * ni * no);
+                    for (int k = 0; k < 3; ++k) acc[k] += (a[k] / OR_PI + fs) * (V * E[k] + Lind[k]) * ni / pdf;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    out_rgb[3 * p + k] = acc[k] / (double)S;
+                    if (out_ind) out_ind[3 * p + k] = si[k] / (double)S;
+                }
+                if (out_vis) out_vis[p] = sv / (double)S;
+                if (out_flags) out_flags[p] = fl;
+            }
+        }
+        free(hits); free(nears); free(Tl);
+    }
+    free(maps); free(row_cdf); free(col_cdf); free(s);
+    return err ? -1 : 0;
+}
