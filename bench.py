@@ -419,6 +419,24 @@ def mc_leg(args, dev):
     torch.cuda.synchronize()
     fused_ms = ev[0].elapsed_time(ev[1])
     rays = Pn * 64
+    # relighting query under a new environment: pre-integration, then
+    # 64 environment-importance samples per point tracing albedo/roughness/normal
+    env_new = T(synth.env_map(seed=1005))
+    ev[0].record(stream)
+    E = irgs.EnvMap(env_new)
+    ev[1].record(stream)
+    pr = irgs.TraceParams(k=16, feat_offset=3, feat_count=7, t_min=1e-3)
+    orl = irgs.relight(S2, E, *g2, 64, 2025, pr)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    env_ms = ev[0].elapsed_time(ev[1])
+    ev[0].record(stream)
+    for _ in range(reps):
+        irgs.relight(S2, E, *g2, 64, 2025, pr, out=orl)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    relight_ms = ev[0].elapsed_time(ev[1]) / reps
+    E.close()
     if S2.status() != 0:
         raise RuntimeError("device error in the MC leg")
     S2.close()
@@ -427,7 +445,10 @@ def mc_leg(args, dev):
             "ms": fms, "mrays_s": rays / (fms * 1e-3) / 1e6, "points_per_s": Pn / (fms * 1e-3),
             "bwd_ms": bms, "bwd_mrays_s": rays / (bms * 1e-3) / 1e6,
             "path": "secondary rays regrouped by direction bin and origin Morton code, one stack per ray",
-            "fused_per_lane_ms": fused_ms}
+            "fused_per_lane_ms": fused_ms,
+            "relight": {"workload": f"{Pn} points x 64 environment-importance samples, 512x256 environment, "
+                                    "traced albedo/roughness/normal shaded with split-sum maps",
+                        "envmap_ms": env_ms, "ms": relight_ms, "mrays_s": rays / (relight_ms * 1e-3) / 1e6}}
 
 
 def serve_leg(args, dev):

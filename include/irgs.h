@@ -307,6 +307,77 @@ irgs_status irgs_shade_mc_backward(irgs_scene scene, const float* x, const float
                                    void* stream);
 
 /* ---------------------------------------------------------------------- */
+/* Relighting (supplementary "Relighting details", Eq. 18).               */
+/* ---------------------------------------------------------------------- */
+
+/* Sizes of the pre-integrated maps. */
+#define IRGS_RELIGHT_IRR_H 32
+#define IRGS_RELIGHT_IRR_W 64
+#define IRGS_RELIGHT_LEVELS 6
+#define IRGS_RELIGHT_PREF_H 64
+#define IRGS_RELIGHT_PREF_W 128
+#define IRGS_RELIGHT_LUT_N 32
+
+typedef struct irgs_envmap_s* irgs_envmap;
+
+/*
+ * Pre-integrate an environment for relighting (all maps equirect, z up,
+ * texel centres as in irgs_shade_mc, over all H x W texels t of the
+ * environment, each of constant radiance E_t over its exact band solid
+ * angle dOmega_t seen from its centre direction w_t):
+ *   irradiance  Irr(N) = 1/pi sum_t E_t max(0, w_t.N) dOmega_t, at the centres
+ *               of a 32 x 64 map;
+ *   prefilter   for roughness rho_l = l/5, l = 1..5, at the centres R of
+ *               64 x 128 maps: sum_t E_t D(R.h_t) max(0, w_t.R) dOmega_t /
+ *               sum_t D(R.h_t) max(0, w_t.R) dOmega_t, h_t = normalise(w_t + R),
+ *               D GGX with alpha_g = rho^2 (split sum with n = v = R; level 0
+ *               is the environment itself);
+ *   BRDF table  over cell centres (n.v, rho) = ((i+0.5)/32, (j+0.5)/32): the
+ *               split-sum factors A, B of int f_s (w.n) dw = F0 A + B (Schlick
+ *               F split into F0 (1 - c^5) + c^5, c = 1 - v.h), from 1024
+ *               Hammersley GGX half vectors ((k+0.5)/1024, radical inverse);
+ *   sampling    FP64 cdfs of the texel weights lum(E_t) sin(theta of the row
+ *               centre), lum = 0.2126 r + 0.7152 g + 0.0722 b, per row over
+ *               columns and over rows.
+ *   env : device [H, W, 3] radiance, copied (the caller keeps ownership).
+ *   out : receives the handle; free it with irgs_envmap_destroy.
+ * Enqueued on `stream`; allocates about 1.2 MB + 28 H W bytes of device memory.
+ */
+irgs_status irgs_envmap_create(const float* env, int32_t H, int32_t W, void* stream, irgs_envmap* out);
+
+/* Synchronises the device, then frees the maps. NULL is ignored. */
+irgs_status irgs_envmap_destroy(irgs_envmap envmap);
+
+/* Copy the maps out (any pointer may be NULL; device or host memory, copied
+ * with cudaMemcpyAsync on `stream`): irr [32,64,3], pref [5,64,128,3]
+ * (levels 1..5), lut [32,32,2] (A, B), row_cdf [H+1], col_cdf [H, W+1]. */
+irgs_status irgs_envmap_export(irgs_envmap envmap, float* irr, float* pref, float* lut, double* row_cdf,
+                               double* col_cdf, void* stream);
+
+/*
+ * Relighting estimate at G-buffer points under the environment of `envmap`:
+ *   rgb = 1/S sum_s f(w_s, w_o) L_i(w_s) max(0, w_s.n) / pdf(w_s)
+ * with f the point's BRDF as in irgs_shade_mc (n flipped towards w_o), w_s
+ * drawn by importance sampling the environment (row from the row cdf at
+ * u1 x total, column from that row's cdf at u2 x row weight, the leftover
+ * fractions placing w_s uniformly in (phi, theta) inside the texel; pdf =
+ * (weight / total) W H / (2 pi^2 sin theta)), uniforms as in irgs_shade_mc
+ * with S = n_samples. Each w_s is traced (params.feat_offset selects 7
+ * channels [albedo (3), roughness, normal (3)], feat_count = 7, t_min > 0):
+ * with O = 1 - V the traced opacity, the blend gives A_r = sum(w a)/O,
+ * R_r = sum(w r)/O, N_r = normalise(sum(w n)) flipped to face v = -w_s, and
+ *   L_i = V E(w_s) + O (A_r Irr(N_r) + Pref(reflect(v, N_r), R_r)
+ *                        (0.04 A + B)(N_r.v, R_r)),
+ * Pref linear between its two nearest roughness levels, all maps bilinear.
+ * out_rgb [P,3]; out_vis [P] and out_ind [P,3] (means of V and of the
+ * indirect term over all samples) may be NULL.
+ */
+irgs_status irgs_relight(irgs_scene scene, irgs_envmap envmap, const float* x, const float* n,
+                         const float* albedo, const float* rough, const float* wo, int64_t n_points,
+                         int32_t n_samples, uint64_t seed, const irgs_trace_params* params,
+                         float* out_rgb, float* out_vis, float* out_ind, void* stream);
+
+/* ---------------------------------------------------------------------- */
 /* Serving: several resident scenes, many requests per persistent launch. */
 /* ---------------------------------------------------------------------- */
 

@@ -21,7 +21,7 @@ from . import _lib
 from ._lib import IrgsError
 
 __all__ = ["TraceParams", "Scene", "trace", "trace_forward", "trace_backward", "shade_mc",
-           "shade_mc_backward", "shade", "IrgsError", "library_path"]
+           "shade_mc_backward", "shade", "EnvMap", "relight", "IrgsError", "library_path"]
 
 
 FLAG_PER_THREAD = 1   # one traversal stack per ray
@@ -410,3 +410,86 @@ def shade(scene: Scene, x, n, albedo, rough, wo, env, n_diffuse: int, n_spec: in
     rough, env and the tensors the scene was built from (directions fixed)."""
     return _ShadeFn.apply(scene.means, scene.quats, scene.scales, scene.opacity, scene.features, albedo, rough,
                           env, x, n, wo, scene, (n_diffuse, n_spec, seed, params, mode))
+
+
+class EnvMap:
+    """Pre-integrated maps of an environment [H,W,3] for the relighting query
+    (irradiance, split-sum prefiltered levels, BRDF table, sampling cdfs)."""
+
+    IRR = (32, 64)
+    LEVELS = 6
+    PREF = (64, 128)
+    LUT_N = 32
+
+    def __init__(self, env, device=None):
+        env = _dev_f32(env, "env", 3)
+        if device is not None:
+            env = env.to(device)
+        if env.dim() != 3:
+            raise ValueError("env must be [H, W, 3]")
+        self.device = env.device
+        self.H, self.W = int(env.shape[0]), int(env.shape[1])
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.lib().irgs_envmap_create(_ptr(env), self.H, self.W, _stream(self.device),
+                                                     C.byref(h)), "irgs_envmap_create")
+        self._h = h
+
+    @property
+    def handle(self) -> C.c_void_p:
+        if self._h is None:
+            raise ValueError("environment map is closed")
+        return self._h
+
+    def export(self):
+        """Host copies: irr [32,64,3], pref [5,64,128,3], lut [32,32,2],
+        row_cdf [H+1] (float64), col_cdf [H,W+1] (float64)."""
+        import numpy as np
+        out = {"irr": np.zeros(self.IRR + (3,), np.float32),
+               "pref": np.zeros((self.LEVELS - 1,) + self.PREF + (3,), np.float32),
+               "lut": np.zeros((self.LUT_N, self.LUT_N, 2), np.float32),
+               "row_cdf": np.zeros(self.H + 1), "col_cdf": np.zeros((self.H, self.W + 1))}
+        with torch.cuda.device(self.device):
+            _lib.check(_lib.lib().irgs_envmap_export(self.handle, *(a.ctypes.data_as(C.c_void_p)
+                                                                    for a in out.values()), None),
+                       "irgs_envmap_export")
+            torch.cuda.synchronize(self.device)
+        return out
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            _lib.lib().irgs_envmap_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def relight(scene: Scene, envmap: EnvMap, x, n, albedo, rough, wo, n_samples: int, seed: int,
+            params: TraceParams, want_aux: bool = False, out=None):
+    """Relighting estimate per G-buffer point under `envmap` (supplementary
+    relighting details): params.feat_offset / feat_count = 7 select the
+    traced [albedo (3), roughness, normal (3)] channels. Returns rgb [P,3]
+    (and, with want_aux, vis [P] and ind [P,3])."""
+    x = _dev_f32(x, "x", 3).reshape(-1, 3)
+    P = x.shape[0]
+    n = _dev_f32(n, "n", 3).reshape(P, 3)
+    albedo = _dev_f32(albedo, "albedo", 3).reshape(P, 3)
+    rough = _dev_f32(rough, "rough").reshape(P)
+    wo = _dev_f32(wo, "wo", 3).reshape(P, 3)
+    dev = scene.device
+    if out is None:
+        out = {"rgb": torch.empty((P, 3), device=dev)}
+        if want_aux:
+            out["vis"] = torch.empty(P, device=dev)
+            out["ind"] = torch.empty((P, 3), device=dev)
+    p = params.c()
+    with torch.cuda.device(dev):
+        _lib.check(_lib.lib().irgs_relight(
+            scene.handle, envmap.handle, _ptr(x), _ptr(n), _ptr(albedo), _ptr(rough), _ptr(wo), P,
+            int(n_samples), C.c_uint64(int(seed) & (2 ** 64 - 1)), C.byref(p), _ptr(out["rgb"]),
+            _ptr(out.get("vis")), _ptr(out.get("ind")), _stream(dev)), "irgs_relight")
+    return out

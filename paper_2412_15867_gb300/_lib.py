@@ -42,6 +42,11 @@ _SIGS = {
     "irgs_status_string": (C.c_char_p, [C.c_int]),
     "irgs_abi_version": (C.c_int32, []),
     "irgs_refit_scene": (C.c_int, [P, C.POINTER(Surfels), P]),
+    "irgs_envmap_create": (C.c_int, [P, C.c_int32, C.c_int32, P, C.POINTER(C.c_void_p)]),
+    "irgs_envmap_destroy": (C.c_int, [P]),
+    "irgs_envmap_export": (C.c_int, [P, P, P, P, P, P, P]),
+    "irgs_relight": (C.c_int, [P, P, P, P, P, P, P, C.c_int64, C.c_int32, C.c_uint64, C.POINTER(TraceParamsC),
+                               P, P, P, P]),
     "irgs_kernel_launches": (C.c_uint64, []),
     "irgs_build_scene": (C.c_int, [C.POINTER(Surfels), C.c_float, P, C.POINTER(P)]),
     "irgs_update_scene": (C.c_int, [P, C.POINTER(Surfels), P]),

@@ -283,6 +283,45 @@ irgs_status irgs_shade_mc_backward(irgs_scene sc, const float* x, const float* n
                                             g_features, static_cast<cudaStream_t>(stream));
 }
 
+irgs_status irgs_envmap_create(const float* env, int32_t H, int32_t W, void* stream, irgs_envmap* out) {
+    if (env == nullptr || out == nullptr || H <= 0 || W <= 0) return IRGS_ERR_INVALID_ARG;
+    if ((int64_t)H * W > (int64_t)1 << 26) return IRGS_ERR_INVALID_ARG;
+    return irgs::build_envmap_impl(env, H, W, static_cast<cudaStream_t>(stream), out);
+}
+
+irgs_status irgs_envmap_destroy(irgs_envmap m) {
+    if (m == nullptr) return IRGS_OK;
+    cudaSetDevice(m->device);
+    cudaDeviceSynchronize();
+    irgs::free_envmap(m);
+    return IRGS_OK;
+}
+
+irgs_status irgs_envmap_export(irgs_envmap m, float* irr, float* pref, float* lut, double* row_cdf,
+                               double* col_cdf, void* stream) {
+    if (m == nullptr) return IRGS_ERR_INVALID_ARG;
+    if (cudaSetDevice(m->device) != cudaSuccess) return IRGS_ERR_CUDA;
+    return irgs::export_envmap_impl(m, irr, pref, lut, row_cdf, col_cdf, static_cast<cudaStream_t>(stream));
+}
+
+irgs_status irgs_relight(irgs_scene sc, irgs_envmap m, const float* x, const float* n, const float* albedo,
+                         const float* rough, const float* wo, int64_t n_points, int32_t n_samples, uint64_t seed,
+                         const irgs_trace_params* params, float* out_rgb, float* out_vis, float* out_ind,
+                         void* stream) {
+    if (sc == nullptr || m == nullptr || n_points < 0) return IRGS_ERR_INVALID_ARG;
+    irgs_status s = check_params(sc, params);
+    if (s != IRGS_OK) return s;
+    if (params->k != 8 && params->k != 16) return IRGS_ERR_UNSUPPORTED;
+    if (params->feat_count != 7 || !(params->t_min > 0.f)) return IRGS_ERR_INVALID_ARG;
+    if (n_samples <= 0 || n_samples > (1 << 24)) return IRGS_ERR_INVALID_ARG;
+    if (m->device != sc->device) return IRGS_ERR_INVALID_ARG;
+    if (n_points > 0 && (!x || !n || !albedo || !rough || !wo || !out_rgb)) return IRGS_ERR_INVALID_ARG;
+    if (n_points >= (int64_t)UINT32_MAX * 4) return IRGS_ERR_INVALID_ARG;
+    if ((s = use_device(sc)) != IRGS_OK) return s;
+    return irgs::launch_relight(sc->view(), m, x, n, albedo, rough, wo, n_points, n_samples, seed, *params, out_rgb,
+                                out_vis, out_ind, static_cast<cudaStream_t>(stream));
+}
+
 irgs_status irgs_build_lbvh_noalloc(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,
                                     float* nodes, float* leaf_boxes, void* stream) {
     if (s == nullptr) return IRGS_ERR_INVALID_ARG;

@@ -1,0 +1,427 @@
+// Relighting query (IRGS supplementary "Relighting details", Eq. 18; Sec. 4,
+// relighting paragraph).
+//
+// Under a new environment the surfels' optimised radiance no longer holds,
+// so each incident ray instead blends the albedo, roughness and normal of
+// the surfels it crosses (normalised blend weights) and that aggregate
+// surface is shaded with pre-integrated maps of the environment:
+//   L_ind = O (A_r Irr(N_r) + Pref(reflect(v, N_r), R_r) (F0 A + B)(N_r.v, R_r)),
+// O = 1 - V the ray's opacity, v = -w_i, Irr the diffuse irradiance map,
+// Pref the split-sum prefiltered radiance and (A, B) the split-sum BRDF
+// table. Incident directions are drawn by importance sampling the
+// environment's intensity. Pre-integration (once per environment):
+//   irradiance  Irr(N) = 1/pi sum_t E_t max(0, w_t.N) dOmega_t      [32 x 64]
+//   prefilter   Pref_l(R) = sum_t E_t D_l(R.h_t) (w_t.R)+ dOmega_t / sum_t D_l (w_t.R)+ dOmega_t,
+//               roughness l/5, l = 1..5                               [64 x 128 each]
+//   BRDF table  A, B over (n.v, roughness) cell centres, 1024 Hammersley
+//               GGX half vectors per cell                             [32 x 32]
+//   sampling    row and per-row column cdfs of lum(E) sin(theta_row), FP64
+// over all environment texels t (centre direction w_t, exact band solid
+// angle dOmega_t). One block per output texel sums the environment with a
+// fixed order, so the maps are deterministic.
+#include <cuda_runtime.h>
+
+#include <new>
+
+#include "scene.h"
+#include "shade.cuh"
+#include "trace.cuh"
+
+namespace irgs {
+namespace {
+
+constexpr int kIrrH = IRGS_RELIGHT_IRR_H, kIrrW = IRGS_RELIGHT_IRR_W;
+constexpr int kLevels = IRGS_RELIGHT_LEVELS;
+constexpr int kPrefH = IRGS_RELIGHT_PREF_H, kPrefW = IRGS_RELIGHT_PREF_W;
+constexpr int kLutN = IRGS_RELIGHT_LUT_N;
+constexpr int kLutSamples = 1024;
+constexpr int kReduceThreads = 256;
+constexpr int kRelightThreads = 128;
+
+// Centre direction of texel (row, col) of an h x w equirect map.
+__device__ __forceinline__ f3 texel_dir(int h, int w, int row, int col) {
+    float st, ct, sp, cp;
+    sincospif(((float)row + 0.5f) / (float)h, &st, &ct);
+    sincospif(((float)col + 0.5f) * 2.f / (float)w - 1.f, &sp, &cp);
+    return mk3(st * cp, st * sp, ct);
+}
+
+// Solid angle of a texel of `row`: (cos t0 - cos t1) 2 pi / W written as
+// 2 sin((t0 + t1)/2) sin((t1 - t0)/2) 2 pi / W (no cancellation at the poles).
+__device__ __forceinline__ float texel_solid_angle(int H, int W, int row) {
+    const float m = sinpif(((float)row + 0.5f) / (float)H);
+    const float h = sinpif(0.5f / (float)H);
+    return 2.f * m * h * 2.f * kPi / (float)W;
+}
+
+template <int N>
+__device__ __forceinline__ void block_sum(float (&v)[N]) {
+    __shared__ float part[N][kReduceThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+        for (int k = 0; k < N; ++k) part[k][warp] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < N; ++k) {
+            float s = 0.f;
+            for (int w = 0; w < kReduceThreads / 32; ++w) s += part[k][w];
+            v[k] = s;
+        }
+}
+
+// One block per irradiance texel.
+__global__ void __launch_bounds__(kReduceThreads) k_irradiance(const float* __restrict__ env, int H, int W,
+                                                               float* __restrict__ irr) {
+    const int i = blockIdx.x;
+    const f3 N = texel_dir(kIrrH, kIrrW, i / kIrrW, i % kIrrW);
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int t = threadIdx.x; t < H * W; t += kReduceThreads) {
+        const int r = t / W, c = t - r * W;
+        const float cs = dot3(texel_dir(H, W, r, c), N);
+        if (cs <= 0.f) continue;
+        const float wgt = cs * texel_solid_angle(H, W, r);
+        const float* e = env + (int64_t)t * 3;
+        acc[0] = fmaf(e[0], wgt, acc[0]);
+        acc[1] = fmaf(e[1], wgt, acc[1]);
+        acc[2] = fmaf(e[2], wgt, acc[2]);
+    }
+    block_sum<3>(acc);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) irr[(int64_t)i * 3 + k] = acc[k] * (1.f / kPi);
+}
+
+// One block per texel of prefilter levels 1 .. kLevels - 1.
+__global__ void __launch_bounds__(kReduceThreads) k_prefilter(const float* __restrict__ env, int H, int W,
+                                                              float* __restrict__ pref) {
+    const int per_level = kPrefH * kPrefW;
+    const int level = 1 + blockIdx.x / per_level;
+    const int i = blockIdx.x % per_level;
+    const float rho = (float)level / (float)(kLevels - 1);
+    const float a2 = rho * rho * rho * rho;
+    const f3 R = texel_dir(kPrefH, kPrefW, i / kPrefW, i % kPrefW);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int t = threadIdx.x; t < H * W; t += kReduceThreads) {
+        const int r = t / W, c = t - r * W;
+        const f3 w = texel_dir(H, W, r, c);
+        const float cs = dot3(w, R);
+        if (cs <= 0.f) continue;
+        const f3 h = normalize3(add3(w, R));
+        const float nh = dot3(R, h);
+        const f3 x = cross3(R, h);
+        const float q = fmaf(nh * nh, a2, dot3(x, x));   // (n.h)^2 (a2 - 1) + 1 without cancellation
+        const float wgt = a2 / (kPi * q * q) * cs * texel_solid_angle(H, W, r);
+        const float* e = env + (int64_t)t * 3;
+        acc[0] = fmaf(e[0], wgt, acc[0]);
+        acc[1] = fmaf(e[1], wgt, acc[1]);
+        acc[2] = fmaf(e[2], wgt, acc[2]);
+        acc[3] += wgt;
+    }
+    block_sum<4>(acc);
+    if (threadIdx.x == 0) {
+        float* o = pref + ((int64_t)(level - 1) * per_level + i) * 3;
+        for (int k = 0; k < 3; ++k) o[k] = acc[3] > 0.f ? acc[k] / acc[3] : 0.f;
+    }
+}
+
+// One thread per table cell.
+__global__ void k_brdf_table(float* __restrict__ lut) {
+    const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= kLutN * kLutN) return;
+    const int i = cell / kLutN, j = cell % kLutN;
+    const float mu = ((float)i + 0.5f) / (float)kLutN, rho = ((float)j + 0.5f) / (float)kLutN;
+    const float ag = rho * rho, a2 = ag * ag, kk = 0.5f * ag;
+    const f3 v = mk3(sqrtf(1.f - mu * mu), 0.f, mu);
+    float A = 0.f, B = 0.f;
+    for (int s = 0; s < kLutSamples; ++s) {
+        const float u1 = ((float)s + 0.5f) / (float)kLutSamples;
+        const float u2 = (float)__brev((unsigned)s) * 2.3283064365386963e-10f;   // radical inverse, base 2
+        const float om = 1.f - u1;
+        const float inv = 1.f / fmaf(a2, u1, om);
+        const float ct = sqrtf(om * inv), st = sqrtf(a2 * u1 * inv);
+        float sp, cp;
+        sincospif(2.f * u2, &sp, &cp);
+        const f3 h = mk3(st * cp, st * sp, ct);
+        const float vh = dot3(v, h);
+        const float lz = 2.f * vh * h.z - v.z;
+        if (lz <= 0.f || vh <= 0.f) continue;
+        const float G = (lz / (lz * (1.f - kk) + kk)) * (mu / (mu * (1.f - kk) + kk));
+        const float gv = G * vh / (h.z * mu);
+        const float om5 = 1.f - vh, om52 = om5 * om5;
+        const float fc = om52 * om52 * om5;
+        A += (1.f - fc) * gv;
+        B += fc * gv;
+    }
+    lut[cell * 2] = A / (float)kLutSamples;
+    lut[cell * 2 + 1] = B / (float)kLutSamples;
+}
+
+// Importance-sampling tables, FP64, sequential in row-major order (the sums
+// are deterministic): one thread per row for the column cdfs, then one
+// thread for the row cdf.
+__global__ void k_env_col_cdf(const float* __restrict__ env, int H, int W, double* __restrict__ col_cdf) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= H) return;
+    const double s = sin(((double)r + 0.5) * 3.14159265358979323846 / (double)H);
+    double* cc = col_cdf + (int64_t)r * (W + 1);
+    double run = 0.0;
+    cc[0] = 0.0;
+    for (int c = 0; c < W; ++c) {
+        const float* e = env + ((int64_t)r * W + c) * 3;
+        const double lum = __dadd_rn(__dadd_rn(__dmul_rn(0.2126, (double)e[0]), __dmul_rn(0.7152, (double)e[1])),
+                                     __dmul_rn(0.0722, (double)e[2]));
+        run = __dadd_rn(run, __dmul_rn(lum, s));
+        cc[c + 1] = run;
+    }
+}
+
+__global__ void k_env_row_cdf(const double* __restrict__ col_cdf, int H, int W, double* __restrict__ row_cdf) {
+    double run = 0.0;
+    row_cdf[0] = 0.0;
+    for (int r = 0; r < H; ++r) {
+        run = __dadd_rn(run, col_cdf[(int64_t)r * (W + 1) + W]);
+        row_cdf[r + 1] = run;
+    }
+}
+
+// Largest k in [0, n) with cdf[k] <= t (cdf[0] <= t < cdf[n]).
+__device__ __forceinline__ int cdf_find(const double* __restrict__ cdf, int n, double t) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (cdf[mid] <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Environment sample from (u1, u2) (row, then column within the row; the
+// leftover fractions place the direction inside the texel). Returns false
+// if the environment has no weight.
+__device__ __forceinline__ bool env_sample(const double* __restrict__ row_cdf, const double* __restrict__ col_cdf,
+                                           int H, int W, double u1, double u2, f3& w, float& pdf) {
+    const double total = row_cdf[H];
+    if (!(total > 0.0)) return false;
+    const double t1 = u1 * total;
+    const int r = cdf_find(row_cdf, H, t1);
+    const double* cc = col_cdf + (int64_t)r * (W + 1);
+    const double rw = cc[W];
+    const double fv = (t1 - row_cdf[r]) / rw;
+    const double t2 = u2 * rw;
+    const int c = cdf_find(cc, W, t2);
+    const double wt = cc[c + 1] - cc[c];
+    const double fu = (t2 - cc[c]) / wt;
+    double st, ct, sp, cp;
+    sincospi(((double)r + fv) / (double)H, &st, &ct);
+    sincospi(((double)c + fu) * 2.0 / (double)W - 1.0, &sp, &cp);
+    w = mk3((float)(st * cp), (float)(st * sp), (float)ct);
+    pdf = st > 0.0 ? (float)((wt / total) * (double)W * (double)H / (2.0 * 3.14159265358979323846 *
+                                                                       3.14159265358979323846 * st))
+                   : 0.f;
+    return pdf > 0.f;
+}
+
+struct EnvMaps {
+    const float *env, *irr, *pref, *lut;
+    const double *row_cdf, *col_cdf;
+    int H, W;
+};
+
+// Split-sum prefiltered radiance at roughness rho: linear between the two
+// nearest levels (level 0 is the environment).
+__device__ __forceinline__ f3 pref_lookup(const EnvMaps& M, f3 d, float rho) {
+    rho = fminf(fmaxf(rho, 0.f), 1.f);
+    const float t = rho * (float)(kLevels - 1);
+    int l0 = (int)floorf(t);
+    l0 = l0 > kLevels - 2 ? kLevels - 2 : l0;
+    const float f = t - (float)l0;
+    const f3 a = l0 == 0 ? env_lookup(M.env, M.H, M.W, d)
+                         : env_lookup(M.pref + (int64_t)(l0 - 1) * kPrefH * kPrefW * 3, kPrefH, kPrefW, d);
+    const f3 b = env_lookup(M.pref + (int64_t)l0 * kPrefH * kPrefW * 3, kPrefH, kPrefW, d);
+    return add3(mul3(a, 1.f - f), mul3(b, f));
+}
+
+// Bilinear lookup of the BRDF table at (mu, rho), coordinates clamped to the
+// cell centres.
+__device__ __forceinline__ float2 lut_lookup(const float* __restrict__ lut, float mu, float rho) {
+    const float x = fminf(fmaxf(mu * kLutN - 0.5f, 0.f), (float)(kLutN - 1));
+    const float y = fminf(fmaxf(rho * kLutN - 0.5f, 0.f), (float)(kLutN - 1));
+    int i0 = (int)floorf(x), j0 = (int)floorf(y);
+    i0 = i0 > kLutN - 2 ? kLutN - 2 : i0;
+    j0 = j0 > kLutN - 2 ? kLutN - 2 : j0;
+    const float fx = x - (float)i0, fy = y - (float)j0;
+    const float2* L = reinterpret_cast<const float2*>(lut);
+    const float2 a = __ldg(L + i0 * kLutN + j0), b = __ldg(L + i0 * kLutN + j0 + 1);
+    const float2 c = __ldg(L + (i0 + 1) * kLutN + j0), d = __ldg(L + (i0 + 1) * kLutN + j0 + 1);
+    return make_float2((1.f - fx) * ((1.f - fy) * a.x + fy * b.x) + fx * ((1.f - fy) * c.x + fy * d.x),
+                       (1.f - fx) * ((1.f - fy) * a.y + fy * b.y) + fx * ((1.f - fy) * c.y + fy * d.y));
+}
+
+__device__ __forceinline__ f3 ld3r(const float* p, int64_t i) { return mk3(p[3 * i], p[3 * i + 1], p[3 * i + 2]); }
+
+// One warp per point; lanes take samples s = lane, lane + 32, ...; the traced
+// channels are [albedo (3), roughness, normal (3)].
+template <int K>
+__global__ void __launch_bounds__(kRelightThreads) k_relight(SceneView S, EnvMaps M, const float* __restrict__ xg,
+                                                             const float* __restrict__ ng,
+                                                             const float* __restrict__ ag,
+                                                             const float* __restrict__ rg,
+                                                             const float* __restrict__ wog, int64_t Pn, int Sn,
+                                                             uint64_t seed, TraceParams TP, float* __restrict__ rgb,
+                                                             float* __restrict__ vis, float* __restrict__ ind) {
+    static_assert(kRelightThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
+    const int lane = threadIdx.x & 31;
+    const int64_t p = blockIdx.x * (int64_t)(kRelightThreads / 32) + (threadIdx.x >> 5);
+    if (p >= Pn) return;
+    const f3 x = ld3r(xg, p), a = ld3r(ag, p);
+    const ShadeFrame F = shade_frame(ld3r(ng, p), ld3r(wog, p), rg[p]);
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // rgb, V, L_ind
+    for (int s = lane; s < Sn; s += 32) {
+        const uint64_t i0 = ((uint64_t)p * (uint64_t)Sn + (uint64_t)s) * 2ull;
+        const double u1 = (double)u01_from_bits(splitmix64_at(seed, i0));
+        const double u2 = (double)u01_from_bits(splitmix64_at(seed, i0 + 1));
+        f3 w;
+        float pdf;
+        if (!env_sample(M.row_cdf, M.col_cdf, M.H, M.W, u1, u2, w, pdf)) continue;
+        MarchState<K, 7> st;
+        const bool ok = march_forward<K, 7, false>(S, make_ray(x, w), TP, st, nullptr, 0, true);
+        if (!ok) atomicOr(S.status, kErrStackOverflow);
+        const float V = st.T, O = 1.f - st.T;
+        f3 Lind = mk3(0.f, 0.f, 0.f);
+        if (O > 0.f) {
+            const f3 Ar = mul3(mk3(st.C[0], st.C[1], st.C[2]), 1.f / O);
+            const float Rr = st.C[3] / O;
+            const f3 v = mul3(w, -1.f);
+            f3 Nr = mk3(st.C[4], st.C[5], st.C[6]);
+            const float len2 = dot3(Nr, Nr);
+            Nr = len2 > 1e-24f ? mul3(Nr, rsqrtf(len2)) : v;
+            if (dot3(Nr, v) < 0.f) Nr = mul3(Nr, -1.f);
+            const float mu = fminf(dot3(Nr, v), 1.f);
+            const f3 refl = sub3(mul3(Nr, 2.f * mu), v);
+            const f3 irr = env_lookup(M.irr, kIrrH, kIrrW, Nr);
+            const f3 pf = pref_lookup(M, refl, Rr);
+            const float2 AB = lut_lookup(M.lut, mu, Rr);
+            const float spec = kF0 * AB.x + AB.y;
+            Lind = mul3(add3(mk3(Ar.x * irr.x, Ar.y * irr.y, Ar.z * irr.z), mul3(pf, spec)), O);
+        }
+        acc[3] += V;
+        acc[4] += Lind.x;
+        acc[5] += Lind.y;
+        acc[6] += Lind.z;
+        const float ni = dot3(F.n, w);
+        if (ni <= 0.f) continue;
+        const f3 h = normalize3(add3(w, F.wo));
+        const float nh = dot3(F.n, h), oh = dot3(F.wo, h);
+        const float q = ggx_q(F, h, nh);
+        const float D = F.a2 / (kPi * q * q);
+        const float G1i = ni / (ni * (1.f - F.kk) + F.kk);
+        const float fs_cos = D * fresnel(oh) * G1i * F.G1o / (4.f * F.no);   // f_s (w.n)
+        const f3 E = env_lookup(M.env, M.H, M.W, w);
+        const float Li[3] = {V * E.x + Lind.x, V * E.y + Lind.y, V * E.z + Lind.z};
+        const float av[3] = {a.x, a.y, a.z};
+        const float inv_pdf = 1.f / pdf;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] += (av[c] * (1.f / kPi) * ni + fs_cos) * Li[c] * inv_pdf;
+    }
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+    if (lane == 0) {
+        const float inv = 1.f / (float)Sn;
+        for (int c = 0; c < 3; ++c) rgb[3 * p + c] = acc[c] * inv;
+        if (vis != nullptr) vis[p] = acc[3] * inv;
+        if (ind != nullptr)
+            for (int c = 0; c < 3; ++c) ind[3 * p + c] = acc[4 + c] * inv;
+    }
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count, int64_t& bytes) {
+    const size_t b = sizeof(T) * (count > 0 ? count : 1);
+    bytes += (int64_t)b;
+    return cudaMalloc(reinterpret_cast<void**>(p), b);
+}
+
+}  // namespace
+
+void free_envmap(irgs_envmap m) {
+    if (m == nullptr) return;
+    void* ptrs[] = {m->env, m->irr, m->pref, m->lut, m->row_cdf, m->col_cdf};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete m;
+}
+
+irgs_status build_envmap_impl(const float* env, int32_t H, int32_t W, cudaStream_t st, irgs_envmap* out) {
+    irgs_envmap m = new (std::nothrow) irgs_envmap_s();
+    if (m == nullptr) return IRGS_ERR_OOM;
+    cudaGetDevice(&m->device);
+    m->H = H;
+    m->W = W;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(dalloc(&m->env, (size_t)H * W * 3, m->bytes));
+    A(dalloc(&m->irr, (size_t)kIrrH * kIrrW * 3, m->bytes));
+    A(dalloc(&m->pref, (size_t)(kLevels - 1) * kPrefH * kPrefW * 3, m->bytes));
+    A(dalloc(&m->lut, (size_t)kLutN * kLutN * 2, m->bytes));
+    A(dalloc(&m->row_cdf, (size_t)H + 1, m->bytes));
+    A(dalloc(&m->col_cdf, (size_t)H * (W + 1), m->bytes));
+    if (e != cudaSuccess) {
+        free_envmap(m);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? IRGS_ERR_OOM : IRGS_ERR_CUDA;
+    }
+    A(cudaMemcpyAsync(m->env, env, sizeof(float) * (size_t)H * W * 3, cudaMemcpyDeviceToDevice, st));
+    k_irradiance<<<kIrrH * kIrrW, kReduceThreads, 0, st>>>(m->env, H, W, m->irr);
+    k_prefilter<<<(kLevels - 1) * kPrefH * kPrefW, kReduceThreads, 0, st>>>(m->env, H, W, m->pref);
+    k_brdf_table<<<(kLutN * kLutN + 127) / 128, 128, 0, st>>>(m->lut);
+    k_env_col_cdf<<<(H + 127) / 128, 128, 0, st>>>(m->env, H, W, m->col_cdf);
+    k_env_row_cdf<<<1, 1, 0, st>>>(m->col_cdf, H, W, m->row_cdf);
+    count_launches(5);
+    A(cudaGetLastError());
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        free_envmap(m);
+        return IRGS_ERR_CUDA;
+    }
+    *out = m;
+    return IRGS_OK;
+}
+
+irgs_status export_envmap_impl(irgs_envmap m, float* irr, float* pref, float* lut, double* row_cdf,
+                               double* col_cdf, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    const cudaMemcpyKind k = cudaMemcpyDefault;
+    if (irr) A(cudaMemcpyAsync(irr, m->irr, sizeof(float) * kIrrH * kIrrW * 3, k, st));
+    if (pref) A(cudaMemcpyAsync(pref, m->pref, sizeof(float) * (kLevels - 1) * kPrefH * kPrefW * 3, k, st));
+    if (lut) A(cudaMemcpyAsync(lut, m->lut, sizeof(float) * kLutN * kLutN * 2, k, st));
+    if (row_cdf) A(cudaMemcpyAsync(row_cdf, m->row_cdf, sizeof(double) * (m->H + 1), k, st));
+    if (col_cdf) A(cudaMemcpyAsync(col_cdf, m->col_cdf, sizeof(double) * (size_t)m->H * (m->W + 1), k, st));
+    return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+}
+
+irgs_status launch_relight(const SceneView& S, irgs_envmap m, const float* x, const float* n, const float* albedo,
+                           const float* rough, const float* wo, int64_t P, int32_t n_samples, uint64_t seed,
+                           const irgs_trace_params& p, float* rgb, float* vis, float* ind, cudaStream_t st) {
+    if (P == 0) return IRGS_OK;
+    const TraceParams TP = to_params(p);
+    const EnvMaps M{m->env, m->irr, m->pref, m->lut, m->row_cdf, m->col_cdf, m->H, m->W};
+    const int64_t blocks = (P + kRelightThreads / 32 - 1) / (kRelightThreads / 32);
+    switch (p.k) {
+        case 8:
+            k_relight<8><<<(unsigned)blocks, kRelightThreads, 0, st>>>(S, M, x, n, albedo, rough, wo, P, n_samples,
+                                                                      seed, TP, rgb, vis, ind);
+            break;
+        case 16:
+            k_relight<16><<<(unsigned)blocks, kRelightThreads, 0, st>>>(S, M, x, n, albedo, rough, wo, P, n_samples,
+                                                                       seed, TP, rgb, vis, ind);
+            break;
+        default: return IRGS_ERR_UNSUPPORTED;
+    }
+    count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+}
+
+}  // namespace irgs

@@ -57,7 +57,29 @@ struct irgs_scene_s {
     }
 };
 
+// Pre-integrated maps of one environment for the relighting query.
+struct irgs_envmap_s {
+    int device = 0;
+    int32_t H = 0, W = 0;
+    int64_t bytes = 0;
+    float* env = nullptr;       // [H, W, 3] copy
+    float* irr = nullptr;       // [IRGS_RELIGHT_IRR_H, IRGS_RELIGHT_IRR_W, 3]
+    float* pref = nullptr;      // [IRGS_RELIGHT_LEVELS - 1, IRGS_RELIGHT_PREF_H, IRGS_RELIGHT_PREF_W, 3]
+    float* lut = nullptr;       // [IRGS_RELIGHT_LUT_N, IRGS_RELIGHT_LUT_N, 2]
+    double* row_cdf = nullptr;  // [H + 1]
+    double* col_cdf = nullptr;  // [H, W + 1]
+};
+
 namespace irgs {
+
+// relight.cu
+irgs_status build_envmap_impl(const float* env, int32_t H, int32_t W, cudaStream_t st, irgs_envmap* out);
+void free_envmap(irgs_envmap m);
+irgs_status export_envmap_impl(irgs_envmap m, float* irr, float* pref, float* lut, double* row_cdf,
+                               double* col_cdf, cudaStream_t st);
+irgs_status launch_relight(const SceneView& sv, irgs_envmap m, const float* x, const float* n, const float* albedo,
+                           const float* rough, const float* wo, int64_t P, int32_t n_samples, uint64_t seed,
+                           const irgs_trace_params& p, float* rgb, float* vis, float* ind, cudaStream_t st);
 
 // scene.cu
 irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_t st, irgs_scene* out);
