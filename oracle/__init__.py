@@ -117,6 +117,8 @@ def _load():
     lib.oracle_sample_dirs.argtypes = [P, P, P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P]
     lib.oracle_num_threads.restype = C.c_int
     lib.oracle_num_threads.argtypes = [C.c_int]
+    lib.oracle_rasterize.restype = C.c_int
+    lib.oracle_rasterize.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P, P, P, P, P, P, P, P, C.c_int]
     lib.oracle_relight_maps.restype = C.c_int
     lib.oracle_relight_maps.argtypes = [P, C.c_int32, C.c_int32, C.c_int, P, P, P, P, P]
     lib.oracle_env_samples.restype = C.c_int
@@ -362,4 +364,49 @@ def relight(scene, x, nrm, albedo, rough, wo, env, n_samples: int, seed: int, pa
                             _ptr(out["ind"]), _ptr(out["flags"]), int(n_threads))
     if rc != 0:
         raise ValueError("oracle_relight rejected its arguments")
+    return out
+
+
+F_BRANCH = 128   # rasteriser: the 3D and screen-space terms of rho^2 nearly tie
+
+
+class Camera(C.Structure):
+    """Pinhole camera: pixel (px, py) looks along normalise(forward + x right
+    + y up), x = ((px + 0.5)/width 2 - 1) tan_half_fov width/height,
+    y = (1 - (py + 0.5)/height 2) tan_half_fov."""
+    _fields_ = [("origin", C.c_float * 3), ("forward", C.c_float * 3), ("right", C.c_float * 3),
+                ("up", C.c_float * 3), ("tan_half_fov", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+def camera(origin, forward, right, up, tan_half_fov, width, height) -> Camera:
+    c = Camera()
+    c.origin[:] = [float(v) for v in origin]
+    c.forward[:] = [float(v) for v in forward]
+    c.right[:] = [float(v) for v in right]
+    c.up[:] = [float(v) for v in up]
+    c.tan_half_fov = float(tan_half_fov)
+    c.width, c.height = int(width), int(height)
+    return c
+
+
+def rasterize(scene, cam: Camera, params: Params = Params(), margins: Margins | None = Margins(),
+              n_threads: int = 0):
+    """2D Gaussian rasterisation of a width x height image (row-major): the
+    surfels with centre view depth > params.t_min blended in centre-depth
+    order with the 2DGS low-pass filter. Returns feat [P,Fc], depth [P],
+    opacity [P], n_hits [P], flags [P]."""
+    lib = _load()
+    means, quats, scales, opacity, feats = _surfel_arrays(scene)
+    n, F = means.shape[0], feats.shape[1]
+    Pn = cam.width * cam.height
+    out = {"feat": np.zeros((Pn, params.feat_count)), "depth": np.zeros(Pn), "opacity": np.zeros(Pn),
+           "n_hits": np.zeros(Pn, np.int32), "flags": np.zeros(Pn, np.uint32)}
+    p = params.c()
+    m = margins.c() if margins is not None else None
+    rc = lib.oracle_rasterize(_ptr(means), _ptr(quats), _ptr(scales), _ptr(opacity), _ptr(feats), n, F,
+                              C.byref(cam), C.byref(p), C.byref(m) if m is not None else None, _ptr(out["feat"]),
+                              _ptr(out["depth"]), _ptr(out["opacity"]), _ptr(out["n_hits"]), _ptr(out["flags"]),
+                              int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_rasterize rejected its arguments")
     return out

@@ -1304,3 +1304,139 @@ int oracle_relight(const float* means, const float* quats, const float* scales, 
     free(maps); free(row_cdf); free(col_cdf); free(s);
     return err ? -1 : 0;
 }
+
+/* ====================================================================== */
+/* 2D Gaussian rasterisation of a G-buffer (Sec. 3.3 stage I/II: the maps  */
+/* of Eq. 9 are rendered by 2DGS rasterisation, which blends Eq. 2 in the  */
+/* order of the splats' centre depths rather than of the per-pixel         */
+/* intersection depths, with the 2DGS screen-space low-pass filter).       */
+/* ====================================================================== */
+
+/* Pinhole camera (the same convention as the CUDA library's camera rays). */
+typedef struct {
+    float origin[3], forward[3], right[3], up[3];
+    float tan_half_fov;
+    int32_t width, height;
+} oracle_camera;
+
+typedef struct { double z; int64_t id; } zkey64;
+
+static int zkey_cmp(const void* a, const void* b)
+{
+    const zkey64* x = (const zkey64*)a;
+    const zkey64* y = (const zkey64*)b;
+    if (x->z < y->z) return -1;
+    if (x->z > y->z) return 1;
+    return (x->id < y->id) ? -1 : (x->id > y->id);
+}
+
+/* Extra flag of the rasteriser: the 3D and screen-space terms of rho^2 are
+ * within the margin of each other (the blended depth switches between the
+ * intersection and the centre there). */
+enum { OF_BRANCH = 128u };
+
+/* Rasterise: for every pixel (px, py) of a width x height image (row-major
+ * output), with the camera ray d of that pixel (unit; the camera's formula in
+ * FP64), the surfels whose centre has view depth z_c = (mu - o).forward >
+ * t_min are blended in ascending (z_c, user index) order. Per surfel:
+ *   rho3^2 = u^2 + v^2 of the ray-plane intersection (Eq. 6-7) when
+ *            |n.d| >= 1e-8 and tau > 0, else +inf;
+ *   rho2^2 = |(px, py) - c|^2 / sigma^2, c the projected centre in pixel
+ *            coordinates (pixel centres at integers), sigma^2 = 1/2 (the
+ *            2DGS low-pass filter);
+ *   rho^2 = min(rho3^2, rho2^2); kept if rho^2 <= rho_c^2 and
+ *   alpha = min(alpha_max, o exp(-rho^2/2)) >= alpha_min; its depth is tau
+ *   if rho3^2 <= rho2^2, else (mu - o).d.
+ * Blending as the tracer (w = T alpha, stop after the hit that makes
+ * T < T_min). Outputs per pixel: feat [fc], depth, opacity 1 - T, n_hits,
+ * flags. */
+int oracle_rasterize(const float* means, const float* quats, const float* scales, const float* opacity,
+                     const float* feats, int64_t n, int32_t F_total, const oracle_camera* cam,
+                     const oracle_params* P, const oracle_margins* M, double* out_feat, double* out_depth,
+                     double* out_opacity, int32_t* out_nhits, uint32_t* out_flags, int n_threads)
+{
+    if (!cam || !P || n < 0 || cam->width <= 0 || cam->height <= 0) return -1;
+    if (P->feat_count < 0 || P->feat_offset < 0 || P->feat_offset + P->feat_count > F_total) return -1;
+    surfel64* s = (surfel64*)malloc(sizeof(surfel64) * (size_t)(n > 0 ? n : 1));
+    zkey64* order = (zkey64*)malloc(sizeof(zkey64) * (size_t)(n > 0 ? n : 1));
+    if (!s || !order) { free(s); free(order); return -1; }
+    load_surfels(means, quats, scales, opacity, n, P->alpha_min, s);
+    double o[3], fw[3], rt[3], up[3];
+    for (int k = 0; k < 3; ++k) {
+        o[k] = cam->origin[k]; fw[k] = cam->forward[k]; rt[k] = cam->right[k]; up[k] = cam->up[k];
+    }
+    const double W = cam->width, H = cam->height, tf = cam->tan_half_fov, aspect = W / H;
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double mo[3] = {s[i].mu[0] - o[0], s[i].mu[1] - o[1], s[i].mu[2] - o[2]};
+        double z = dot3(mo, fw);
+        if (!(z > P->t_min) || s[i].rc2 < 0.0) continue;
+        order[m].z = z;
+        order[m].id = i;
+        ++m;
+    }
+    qsort(order, (size_t)m, sizeof(zkey64), zkey_cmp);
+    const double sigma2 = 0.5;
+    nthreads_set(n_threads);
+    const int64_t npix = (int64_t)cam->width * cam->height;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t pix = 0; pix < npix; ++pix) {
+        const int64_t py = pix / cam->width, px = pix % cam->width;
+        double sx = (px + 0.5) / W * 2.0 - 1.0, sy = 1.0 - (py + 0.5) / H * 2.0;
+        double d[3];
+        for (int k = 0; k < 3; ++k) d[k] = fw[k] + sx * tf * aspect * rt[k] + sy * tf * up[k];
+        normalize3(d);
+        double T = 1.0, D = 0.0, C[64];
+        for (int c = 0; c < P->feat_count; ++c) C[c] = 0.0;
+        int32_t nh = 0;
+        uint32_t fl = 0;
+        double z_prev = -1.0;
+        for (int64_t j = 0; j < m; ++j) {
+            const surfel64* S = &s[order[j].id];
+            double mo[3] = {S->mu[0] - o[0], S->mu[1] - o[1], S->mu[2] - o[2]};
+            double zc = order[j].z;
+            double pxc = (dot3(mo, rt) / zc / (tf * aspect) + 1.0) * 0.5 * W - 0.5;
+            double pyc = (1.0 - dot3(mo, up) / zc / tf) * 0.5 * H - 0.5;
+            double rho2d = ((px - pxc) * (px - pxc) + (py - pyc) * (py - pyc)) / sigma2;
+            cand64 c;
+            double rho3d = INFINITY;
+            int hit3 = intersect(S, o, d, &c) && c.tau > 0.0;
+            if (hit3) rho3d = c.rho2;
+            double rho2 = rho3d < rho2d ? rho3d : rho2d;
+            double araw = S->o * exp(-0.5 * rho2);
+            if (M) {
+                uint32_t kind = 0;
+                if (fabs(rho2 - S->rc2) < M->rho_rel * (S->rc2 > 1e-12 ? S->rc2 : 1e-12)) kind |= OF_RHO;
+                if (fabs(araw - P->alpha_min) < M->alpha_abs) kind |= OF_ALPHA;
+                if (fabs(araw - P->alpha_max) < M->clamp_abs) kind |= OF_CLAMP;
+                if (hit3 && fabs(rho3d - rho2d) < M->rho_rel * (rho2 > 1e-12 ? rho2 : 1e-12)) kind |= OF_BRANCH;
+                if (fabs(c.den) < 2e-8 && fabs(c.den) >= 0.5e-8) kind |= OF_GRAZE;
+                if (hit3 && fabs(c.tau) < M->t_abs) kind |= OF_TRANGE;
+                fl |= kind;
+            }
+            if (rho2 > S->rc2) continue;
+            double alpha = araw < P->alpha_max ? araw : P->alpha_max;
+            if (alpha < P->alpha_min) continue;
+            if (M && z_prev >= 0.0 && fabs(zc - z_prev) < M->tie_abs * (zc > 1.0 ? zc : 1.0)) fl |= OF_TIE;
+            z_prev = zc;
+            double depth = rho3d <= rho2d ? c.tau : dot3(mo, d);
+            double w = T * alpha;
+            const float* f = feats + order[j].id * (int64_t)F_total + P->feat_offset;
+            for (int cc = 0; cc < P->feat_count; ++cc) C[cc] += w * (double)f[cc];
+            D += w * depth;
+            double Tn = T * (1.0 - alpha);
+            if (M && fabs(Tn - P->T_min) < M->T_rel * P->T_min) fl |= OF_T;
+            T = Tn;
+            ++nh;
+            if (T < P->T_min) break;
+        }
+        for (int cc = 0; cc < P->feat_count; ++cc) out_feat[pix * P->feat_count + cc] = C[cc];
+        out_depth[pix] = D;
+        out_opacity[pix] = 1.0 - T;
+        out_nhits[pix] = nh;
+        if (out_flags) out_flags[pix] = fl;
+    }
+    free(s);
+    free(order);
+    return 0;
+}
