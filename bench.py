@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mc", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-raster", action="store_true")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving leg")
     ap.add_argument("--mc-only", action="store_true", help="run only the Monte Carlo shading leg")
     ap.add_argument("--mc-points", type=int, default=640_000)
@@ -267,6 +268,25 @@ def run_ours(args):
     torch.cuda.synchronize()
     refit_ms = ra.elapsed_time(rb) / 5
 
+    # ---- 2D Gaussian rasterisation of the same cameras (the G-buffer pass of stage II)
+    raster = None
+    if not args.no_raster and rank == 0:
+        from paper_2412_15867_gb300 import serve as _serve
+        n_cam = min(args.cams, 20)
+        rcams = [_serve.make_camera(e, args.res, args.res, fov_deg=60.0) for e in cams[:n_cam]]
+        pr = irgs.TraceParams(k=16, feat_count=F)
+        ro_ = irgs.rasterize(scene, rcams[0], pr)
+        torch.cuda.synchronize()
+        ra.record(stream)
+        for c_ in rcams:
+            irgs.rasterize(scene, c_, pr, out=ro_)
+        rb.record(stream)
+        torch.cuda.synchronize()
+        r_ms = ra.elapsed_time(rb) / n_cam
+        raster = {"workload": f"{n_cam} of the cameras, {args.res}x{args.res}, {F} channels, 16x16 tiles",
+                  "ms_per_image": r_ms, "mpix_s": args.res * args.res / (r_ms * 1e-3) / 1e6,
+                  "traced_ms_per_image": fwd_ms / args.cams}
+
     # ---- roofline of the dominant kernel (by time)
     nh = out["n_hits"]
     if bwd_ms >= fwd_ms:
@@ -367,7 +387,7 @@ def run_ours(args):
             "mean_hits_per_ray": float(nh.float().mean()), "max_hits_per_ray": int(nh.max()),
             "replayed_ray_frac": float((nh > args.saved_hits).float().mean()) if args.saved_hits > 0 else 1.0,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk, "mc": mc, "serving": serving,
+            "clocks": clk, "raster": raster, "mc": mc, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -475,6 +475,29 @@ irgs_status irgs_camera_rays(const irgs_camera* cam, int64_t first, int64_t coun
                              void* stream);
 
 /*
+ * 2D Gaussian rasterisation of a G-buffer (Sec. 3.3: the stage-I/II maps of
+ * Eq. 9-10 are rasterised, not traced). Row-major width x height image of
+ * `cam` (its tile fields are ignored). For each pixel and its camera ray d,
+ * the surfels whose centre has view depth z_c = (mu - origin).forward >
+ * params->t_min are blended with Eq. 2 (w = T alpha, stop after the hit that
+ * makes T < T_min) in ascending (z_c, user index) order. Per surfel:
+ *   rho3^2 = u^2 + v^2 of the ray's intersection with its plane (Eq. 6-7),
+ *            +inf if |n.d| < 1e-8 or tau <= 0;
+ *   rho2^2 = |pixel centre - projected centre|^2 / (1/2)   (pixels; the
+ *            2DGS screen-space low-pass filter);
+ *   rho^2 = min(rho3^2, rho2^2); kept if rho^2 <= rho_c^2 and
+ *   alpha = min(alpha_max, o exp(-rho^2/2)) >= alpha_min; its depth is tau
+ *   if rho3^2 <= rho2^2, else (mu - origin).d.
+ * Outputs as irgs_trace_forward: out_feat [P, feat_count], out_depth [P],
+ * out_opacity [P], out_nhits [P] (or NULL), P = width x height. Uses scratch
+ * from the stream-ordered allocator and synchronises `stream` once (to size
+ * the per-tile lists). params->flags must be 0.
+ */
+irgs_status irgs_rasterize(irgs_scene scene, const irgs_camera* cam, const irgs_trace_params* params,
+                           float* out_feat, float* out_depth, float* out_opacity, int32_t* out_nhits,
+                           void* stream);
+
+/*
  * Allocation-free LBVH build (the paper has no counterpart; this is a
  * deployment variant of irgs_build_scene).
  *

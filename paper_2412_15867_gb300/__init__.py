@@ -21,7 +21,7 @@ from . import _lib
 from ._lib import IrgsError
 
 __all__ = ["TraceParams", "Scene", "trace", "trace_forward", "trace_backward", "shade_mc",
-           "shade_mc_backward", "shade", "EnvMap", "relight", "IrgsError", "library_path"]
+           "shade_mc_backward", "shade", "EnvMap", "relight", "rasterize", "IrgsError", "library_path"]
 
 
 FLAG_PER_THREAD = 1   # one traversal stack per ray
@@ -492,4 +492,23 @@ def relight(scene: Scene, envmap: EnvMap, x, n, albedo, rough, wo, n_samples: in
             scene.handle, envmap.handle, _ptr(x), _ptr(n), _ptr(albedo), _ptr(rough), _ptr(wo), P,
             int(n_samples), C.c_uint64(int(seed) & (2 ** 64 - 1)), C.byref(p), _ptr(out["rgb"]),
             _ptr(out.get("vis")), _ptr(out.get("ind")), _stream(dev)), "irgs_relight")
+    return out
+
+
+def rasterize(scene: Scene, cam, params: TraceParams = TraceParams(), out=None):
+    """2D Gaussian rasterisation of the camera's width x height image
+    (row-major; `cam` is a serve.Camera, its tile fields ignored): surfels
+    with centre view depth > params.t_min blended in centre-depth order
+    with the 2DGS screen-space filter. Returns feat [P,Fc], depth [P],
+    opacity [P], n_hits [P]."""
+    P = int(cam.width) * int(cam.height)
+    dev = scene.device
+    if out is None:
+        out = {"feat": torch.empty((P, params.feat_count), device=dev), "depth": torch.empty(P, device=dev),
+               "opacity": torch.empty(P, device=dev), "n_hits": torch.empty(P, device=dev, dtype=torch.int32)}
+    p = params.c()
+    with torch.cuda.device(dev):
+        _lib.check(_lib.lib().irgs_rasterize(
+            scene.handle, C.cast(C.pointer(cam), C.c_void_p), C.byref(p), _ptr(out["feat"]), _ptr(out["depth"]),
+            _ptr(out["opacity"]), _ptr(out.get("n_hits")), _stream(dev)), "irgs_rasterize")
     return out

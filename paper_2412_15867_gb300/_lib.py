@@ -43,6 +43,7 @@ _SIGS = {
     "irgs_abi_version": (C.c_int32, []),
     "irgs_refit_scene": (C.c_int, [P, C.POINTER(Surfels), P]),
     "irgs_envmap_create": (C.c_int, [P, C.c_int32, C.c_int32, P, C.POINTER(C.c_void_p)]),
+    "irgs_rasterize": (C.c_int, [P, P, C.POINTER(TraceParamsC), P, P, P, P, P]),
     "irgs_envmap_destroy": (C.c_int, [P]),
     "irgs_envmap_export": (C.c_int, [P, P, P, P, P, P, P]),
     "irgs_relight": (C.c_int, [P, P, P, P, P, P, P, C.c_int64, C.c_int32, C.c_uint64, C.POINTER(TraceParamsC),

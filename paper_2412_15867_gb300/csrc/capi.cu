@@ -283,6 +283,20 @@ irgs_status irgs_shade_mc_backward(irgs_scene sc, const float* x, const float* n
                                             g_features, static_cast<cudaStream_t>(stream));
 }
 
+irgs_status irgs_rasterize(irgs_scene sc, const irgs_camera* cam, const irgs_trace_params* params, float* out_feat,
+                           float* out_depth, float* out_opacity, int32_t* out_nhits, void* stream) {
+    if (sc == nullptr || cam == nullptr) return IRGS_ERR_INVALID_ARG;
+    irgs_status s = check_params(sc, params);
+    if (s != IRGS_OK) return s;
+    if (params->flags != 0u || params->feat_count > 16) return IRGS_ERR_UNSUPPORTED;
+    if (cam->width <= 0 || cam->height <= 0 || !(cam->tan_half_fov > 0.f)) return IRGS_ERR_INVALID_ARG;
+    if ((int64_t)cam->width * cam->height > ((int64_t)1 << 31) - 1) return IRGS_ERR_INVALID_ARG;
+    if (!out_depth || !out_opacity || (params->feat_count > 0 && !out_feat)) return IRGS_ERR_INVALID_ARG;
+    if ((s = use_device(sc)) != IRGS_OK) return s;
+    return irgs::launch_rasterize(sc->view(), sc->leaf_box, *cam, *params, out_feat, out_depth, out_opacity,
+                                  out_nhits, static_cast<cudaStream_t>(stream));
+}
+
 irgs_status irgs_envmap_create(const float* env, int32_t H, int32_t W, void* stream, irgs_envmap* out) {
     if (env == nullptr || out == nullptr || H <= 0 || W <= 0) return IRGS_ERR_INVALID_ARG;
     if ((int64_t)H * W > (int64_t)1 << 26) return IRGS_ERR_INVALID_ARG;

@@ -528,19 +528,28 @@ int64_t sort_hist_words(int64_t n) {
 }
 
 cudaError_t sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp, int32_t* vals_tmp, uint32_t* hist,
-                       int64_t n, cudaStream_t st) {
+                       int64_t n, cudaStream_t st, int key_bits) {
     if (n <= 0) return cudaSuccess;
     const int64_t tiles = (n + kTile - 1) / kTile;
+    // an even number of 8-bit passes, so that the result ends in keys / vals
+    const int passes = ((key_bits + 15) / 16) * 2;
     uint32_t* ka = keys; int32_t* va = vals;
     uint32_t* kb = keys_tmp; int32_t* vb = vals_tmp;
-    for (int shift = 0; shift < 32; shift += 8) {
+    for (int shift = 0; shift < 8 * passes; shift += 8) {
         k_sort_hist<<<(unsigned)tiles, 256, 0, st>>>(ka, n, shift, (int)tiles, hist);
         k_scan_exclusive<<<1, 1024, 0, st>>>(hist, 256 * tiles);
         k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(ka, va, n, shift, (int)tiles, hist, kb, vb);
         uint32_t* tk = ka; ka = kb; kb = tk;
         int32_t* tv = va; va = vb; vb = tv;
     }
-    count_launches(12);
+    count_launches(3 * passes);
+    return cudaGetLastError();
+}
+
+cudaError_t scan_exclusive(uint32_t* a, int64_t m, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    k_scan_exclusive<<<1, 1024, 0, st>>>(a, m);
+    count_launches(1);
     return cudaGetLastError();
 }
 

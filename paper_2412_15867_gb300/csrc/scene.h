@@ -72,6 +72,11 @@ struct irgs_envmap_s {
 
 namespace irgs {
 
+// raster.cu
+irgs_status launch_rasterize(const SceneView& sv, const float* leaf_box, const irgs_camera& cam,
+                             const irgs_trace_params& p, float* feat, float* depth, float* opac, int32_t* nhits,
+                             cudaStream_t st);
+
 // relight.cu
 irgs_status build_envmap_impl(const float* env, int32_t H, int32_t W, cudaStream_t st, irgs_envmap* out);
 void free_envmap(irgs_envmap m);
@@ -88,12 +93,14 @@ irgs_status refit_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t 
 irgs_status build_lbvh_noalloc_impl(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,
                                     float* nodes, float* leaf_boxes, cudaStream_t st);
 void free_scene(irgs_scene sc);
-// Stable LSD radix sort of (keys, vals) pairs by all 32 key bits (four 8-bit
-// passes; the result ends in keys/vals). keys_tmp/vals_tmp hold n entries,
-// hist sort_hist_words(n) words.
+// Stable LSD radix sort of (keys, vals) pairs by the low key_bits bits of
+// the keys (8-bit passes, rounded up to an even count; the result ends in
+// keys/vals). keys_tmp/vals_tmp hold n entries, hist sort_hist_words(n) words.
 int64_t sort_hist_words(int64_t n);
 cudaError_t sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp, int32_t* vals_tmp, uint32_t* hist,
-                       int64_t n, cudaStream_t st);
+                       int64_t n, cudaStream_t st, int key_bits = 32);
+// In-place exclusive prefix sum of m words (one block; for up to a few million).
+cudaError_t scan_exclusive(uint32_t* a, int64_t m, cudaStream_t st);
 
 // trace_fwd.cu
 irgs_status launch_trace_forward(const SceneView& sv, const float* ro, const float* rd, int64_t R,

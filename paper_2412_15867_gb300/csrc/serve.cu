@@ -20,6 +20,7 @@
 #include <new>
 
 #include "../../include/irgs.h"
+#include "camera.cuh"
 #include "scene.h"
 #include "shade.cuh"
 #include "trace.cuh"
@@ -56,9 +57,7 @@ struct ServeArgs {
     TraceParams render, gbuf, shade;
 };
 
-// Pixel p of a camera (tile by tile when tile_w x tile_h > 1) -> ray. Written
-// with explicit round-to-nearest operations so every kernel that inlines it
-// produces bit-identical rays.
+// Pixel p of a camera (tile by tile when tile_w x tile_h > 1) -> ray.
 __device__ __forceinline__ void camera_ray(const irgs_camera& c, int64_t p, f3& o, f3& d) {
     const int tw = c.tile_w, th = c.tile_h;
     const int64_t per = (int64_t)tw * th;
@@ -66,18 +65,7 @@ __device__ __forceinline__ void camera_ray(const irgs_camera& c, int64_t p, f3& 
     const int64_t tiles_x = c.width / tw;
     const int64_t ty = tile / tiles_x, tx = tile - ty * tiles_x;
     const float px = (float)(tx * tw + within % tw), py = (float)(ty * th + within / tw);
-    const float W = (float)c.width, H = (float)c.height;
-    const float aspect = __fdiv_rn(W, H);
-    const float sx = __fsub_rn(__fmul_rn(__fdiv_rn(__fadd_rn(px, 0.5f), W), 2.f), 1.f);
-    const float sy = __fsub_rn(1.f, __fmul_rn(__fdiv_rn(__fadd_rn(py, 0.5f), H), 2.f));
-    const float xn = __fmul_rn(__fmul_rn(sx, c.tan_half_fov), aspect);
-    const float yn = __fmul_rn(sy, c.tan_half_fov);
-    float v[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) v[k] = __fmaf_rn(c.up[k], yn, __fmaf_rn(c.right[k], xn, c.forward[k]));
-    const float len2 = __fmaf_rn(v[0], v[0], __fmaf_rn(v[1], v[1], __fmul_rn(v[2], v[2])));
-    const float inv = __frsqrt_rn(len2);
-    d = mk3(__fmul_rn(v[0], inv), __fmul_rn(v[1], inv), __fmul_rn(v[2], inv));
+    d = camera_dir(c, px, py);
     o = mk3(c.origin[0], c.origin[1], c.origin[2]);
 }
 
