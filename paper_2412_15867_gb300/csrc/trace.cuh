@@ -163,34 +163,34 @@ __device__ __forceinline__ Node load_node(const Node* nodes, int i) {
 }
 
 // k-buffer of the K nearest hits after `last`, sorted by (key, Morton index),
-// kept in shared memory: slot j of thread t lives at [j * THREADS + t], so a
-// warp touching the same slot hits consecutive words. Insertion shifts only
-// the entries behind the new one (hits mostly arrive front to back, so the
-// shift is usually short); the last entry is cached in registers for the
-// cheap "does it fit" test and the traversal's far bound.
+// kept in shared memory as 16-byte entries {key (8 B), Morton index, alpha}:
+// slot j of thread t lives at [j * THREADS + t], so a warp touching the same
+// slot reads consecutive 16-byte words, and one shift step of the insertion
+// is one 128-bit load and one 128-bit store. Insertion shifts only the
+// entries behind the new one (hits mostly arrive front to back, so the shift
+// is usually short); the last entry is cached in registers for the cheap
+// "does it fit" test and the traversal's far bound.
 template <int K, int THREADS>
 struct KBuffer {
-    uint64_t* key;
-    int32_t* m;
-    float* a;
+    static constexpr int kThreads = THREADS;
+    uint4* e;   // x, y: key (low, high); z: Morton index; w: alpha bits
     int cnt;
     uint64_t tail_key;
     int32_t tail_m;
 
     __device__ __forceinline__ void bind() {
-        __shared__ uint64_t s_key[K * THREADS];
-        __shared__ int32_t s_m[K * THREADS];
-        __shared__ float s_a[K * THREADS];
-        key = s_key + threadIdx.x;
-        m = s_m + threadIdx.x;
-        a = s_a + threadIdx.x;
+        __shared__ uint4 s_e[K * THREADS];
+        e = s_e + threadIdx.x;
         cnt = 0;
+    }
+    __device__ __forceinline__ static uint64_t key_of(const uint4& v) {
+        return ((uint64_t)v.y << 32) | (uint64_t)v.x;
     }
     __device__ __forceinline__ void clear() { cnt = 0; }
     __device__ __forceinline__ bool full() const { return cnt == K; }
-    __device__ __forceinline__ uint64_t key_at(int j) const { return key[j * THREADS]; }
-    __device__ __forceinline__ int32_t m_at(int j) const { return m[j * THREADS]; }
-    __device__ __forceinline__ float a_at(int j) const { return a[j * THREADS]; }
+    __device__ __forceinline__ uint64_t key_at(int j) const { return key_of(e[j * THREADS]); }
+    __device__ __forceinline__ int32_t m_at(int j) const { return (int32_t)e[j * THREADS].z; }
+    __device__ __forceinline__ float a_at(int j) const { return __uint_as_float(e[j * THREADS].w); }
     __device__ __forceinline__ bool fits(uint64_t k, int32_t mm) const {
         return cnt < K || k < tail_key || (k == tail_key && mm < tail_m);
     }
@@ -198,21 +198,18 @@ struct KBuffer {
     __device__ __forceinline__ void insert(uint64_t k, int32_t mm, float aa) {
         int j = (cnt < K ? cnt : K - 1) - 1;
         while (j >= 0) {
-            const uint64_t kj = key[j * THREADS];
-            const int32_t mj = m[j * THREADS];
-            if (!(k < kj || (k == kj && mm < mj))) break;
-            key[(j + 1) * THREADS] = kj;
-            m[(j + 1) * THREADS] = mj;
-            a[(j + 1) * THREADS] = a[j * THREADS];
+            const uint4 v = e[j * THREADS];
+            const uint64_t kj = key_of(v);
+            if (!(k < kj || (k == kj && mm < (int32_t)v.z))) break;
+            e[(j + 1) * THREADS] = v;
             --j;
         }
-        key[(j + 1) * THREADS] = k;
-        m[(j + 1) * THREADS] = mm;
-        a[(j + 1) * THREADS] = aa;
+        e[(j + 1) * THREADS] = make_uint4((uint32_t)k, (uint32_t)(k >> 32), (uint32_t)mm, __float_as_uint(aa));
         if (cnt < K) ++cnt;
         if (cnt == K) {
-            tail_key = key[(K - 1) * THREADS];
-            tail_m = m[(K - 1) * THREADS];
+            const uint4 t = e[(K - 1) * THREADS];
+            tail_key = key_of(t);
+            tail_m = (int32_t)t.z;
         }
     }
 };
