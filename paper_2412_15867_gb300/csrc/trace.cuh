@@ -55,10 +55,14 @@ struct HitGeom {
 //   dl  = mu - o' = fma(-t_r, d, a_hi) + a_lo          (small, nearly exact)
 //   tau = t_r + n.dl / n.d,  p - mu = (tau - t_r) d - dl.
 // The depth is returned as the exact pair (kh, kl) = two_sum(t_r, tau - t_r).
+// A candidate whose rounded depth kh lies outside [kh_lo, kh_hi] is rejected
+// before the support and opacity tests (callers pass bounds that only cut
+// candidates their own key tests would reject).
 template <bool GEOM>
 __device__ __forceinline__ bool surfel_hit(const float4& r0, const float4& r1, const float4& r2, const float4& r3,
                                            const Ray& ray, float amin, float amax, float& kh, float& kl,
-                                           float& alpha, HitGeom* g) {
+                                           float& alpha, HitGeom* g, float kh_lo = -INFINITY,
+                                           float kh_hi = INFINITY) {
     float ahx, alx, ahy, aly, ahz, alz;
     two_sum(r0.x, -ray.o.x, ahx, alx);
     two_sum(r0.y, -ray.o.y, ahy, aly);
@@ -72,6 +76,8 @@ __device__ __forceinline__ bool surfel_hit(const float4& r0, const float4& r1, c
     if (!(fabsf(den) >= ray.graze)) return false;
     float num = __fmaf_rn(r3.x, dlx, __fmaf_rn(r3.y, dly, __fmul_rn(r3.z, dlz)));
     float tp = __fdiv_rn(num, den);
+    two_sum(tr, tp, kh, kl);
+    if (kh < kh_lo || kh > kh_hi) return false;
     float ex = __fmaf_rn(tp, d.x, -dlx);
     float ey = __fmaf_rn(tp, d.y, -dly);
     float ez = __fmaf_rn(tp, d.z, -dlz);
@@ -83,7 +89,6 @@ __device__ __forceinline__ bool surfel_hit(const float4& r0, const float4& r1, c
     float a_raw = __fmul_rn(r0.w, G);
     alpha = fminf(a_raw, amax);
     if (!(alpha >= amin)) return false;
-    two_sum(tr, tp, kh, kl);
     if (GEOM) {
         g->e = mk3(ex, ey, ez);
         g->u = u;
@@ -236,7 +241,11 @@ __device__ __forceinline__ void leaf_insert(const SceneView& S, const Ray& ray, 
     const float4* R = S.rec + (int64_t)m * kRecF4;
     const float4 r0 = ldg4(R), r1 = ldg4(R + 1), r2 = ldg4(R + 2), r3 = ldg4(R + 3);
     float kh, kl, a;
-    if (!surfel_hit<false>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a, nullptr)) return;
+    // a rounded depth below the last blended key's, or above the full
+    // buffer's last entry (or t_max), cannot pass the key tests below
+    const float lo = key_depth(last_key);
+    const float hi = kb.full() ? key_depth(kb.tail_key) : P.t_max;
+    if (!surfel_hit<false>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a, nullptr, lo, hi)) return;
     const uint64_t key = depth_key(kh, kl);
     const bool past_min = kh > P.t_min || (kh == P.t_min && kl > 0.f);
     const bool after = past_min && (key > last_key || (key == last_key && m > last_m));
