@@ -46,12 +46,12 @@ FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 # DRAM traffic per launch of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) scaled per ray; keyed by
-# the hash of the sources it was measured on (null once they change).
+# the hash of the sources it was measured on, the hierarchy's builder
+# included (null once they change).
 # Captured on the 10-camera case (6.4M rays; the ~90 MB scene read is ~5% of
 # it, so the per-ray figure slightly overstates a 64M-ray launch).
 TRAFFIC = {
-    "k_trace_forward<16,10>": {"bytes_per_ray": (719.0e6 + 1012.6e6) / 6.4e6, "src_hash": "a016fbfbf5f8"},
-    "k_trace_backward<16,10>": {"bytes_per_ray": (1948.3e6 + 187.7e6) / 6.4e6, "src_hash": "bafef88a9786"},
+    "k_trace_forward<16,10>": {"bytes_per_ray": (716.7e6 + 1012.4e6) / 6.4e6, "src_hash": "e6a19dac764e"},
 }
 
 
@@ -292,11 +292,11 @@ def run_ours(args):
     if bwd_ms >= fwd_ms:
         kname, kms = "k_trace_backward<16,10>", bwd_ms
         flops = algorithmic_flops(nh, 16, sc.n, F, backward=True, saved_hits=args.saved_hits)
-        src = ["trace.cuh", "trace_bwd.cuh", "trace_bwd.cu", "common.cuh"]
+        src = ["trace.cuh", "trace_bwd.cuh", "trace_bwd.cu", "common.cuh", "scene.cu"]
     else:
         kname, kms = "k_trace_forward<16,10>", fwd_ms
         flops = algorithmic_flops(nh, 16, sc.n, F)
-        src = ["trace.cuh", "trace_fwd.cu", "common.cuh"]
+        src = ["trace.cuh", "trace_fwd.cu", "common.cuh", "scene.cu"]
     achieved = flops / (kms * 1e-3) / 1e12
     khash = _kernel_hash(src)
     tr = TRAFFIC.get(kname)
@@ -324,19 +324,46 @@ def run_ours(args):
         scene_e2e = irgs.Scene(dev_in["means"], dev_in["quats"], dev_in["scales"], dev_in["opacity"],
                                dev_in["features"])
 
+        # pipelined by camera chunks: host->device copies of chunk c+1 and
+        # device->host copies of chunk c-1 overlap the traces of chunk c
+        n_chunk = max(1, min(10, args.cams))
+        bounds_ = [(R * i // n_chunk, R * (i + 1) // n_chunk) for i in range(n_chunk)]
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        ev_in = [torch.cuda.Event() for _ in range(n_chunk)]
+        ev_done = [torch.cuda.Event() for _ in range(n_chunk)]
+        ev_out = torch.cuda.Event()
+        scene_keys = ("means", "quats", "scales", "opacity", "features")
+        ray_keys = ("ro", "rd", "gf", "gd", "go")
+
         def e2e_step():
-            for k, v in host_in.items():
-                dev_in[k].copy_(v, non_blocking=True)
+            s_in.wait_stream(stream)
+            s_out.wait_stream(stream)
+            for k in scene_keys:
+                dev_in[k].copy_(host_in[k], non_blocking=True)
+            with torch.cuda.stream(s_in):
+                for i, (lo, hi) in enumerate(bounds_):
+                    for k in ray_keys:
+                        dev_in[k][lo:hi].copy_(host_in[k][lo:hi], non_blocking=True)
+                    ev_in[i].record(s_in)
             scene_e2e.update()
-            o_ = irgs.trace_forward(scene_e2e, dev_in["ro"], dev_in["rd"], p, max_hit_ids=args.saved_hits, out=out)
             for g in grads.values():
                 g.zero_()
-            irgs.trace_backward(scene_e2e, dev_in["ro"], dev_in["rd"], p, o_, dev_in["gf"], dev_in["gd"],
-                                dev_in["go"], grads=grads)
-            for k in ("feat", "depth", "opacity", "n_hits"):
-                host_out[k].copy_(out[k], non_blocking=True)
+            for i, (lo, hi) in enumerate(bounds_):
+                stream.wait_event(ev_in[i])
+                sl = {k: out[k][lo:hi] for k in out}
+                irgs.trace_forward(scene_e2e, dev_in["ro"][lo:hi], dev_in["rd"][lo:hi], p,
+                                   max_hit_ids=args.saved_hits, out=sl)
+                irgs.trace_backward(scene_e2e, dev_in["ro"][lo:hi], dev_in["rd"][lo:hi], p, sl,
+                                    dev_in["gf"][lo:hi], dev_in["gd"][lo:hi], dev_in["go"][lo:hi], grads=grads)
+                ev_done[i].record(stream)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev_done[i])
+                    for k in ("feat", "depth", "opacity", "n_hits"):
+                        host_out[k][lo:hi].copy_(out[k][lo:hi], non_blocking=True)
             for k, v in grads.items():
                 host_out["g_" + k].copy_(v, non_blocking=True)
+            ev_out.record(s_out)
+            stream.wait_event(ev_out)
 
         e2e_step()
         torch.cuda.synchronize()
@@ -349,7 +376,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         e_ms = a.elapsed_time(b) / n_e2e
         e2e = {"value": R * world / (e_ms * 1e-3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
+               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms,
+               "pipeline": f"{n_chunk} camera chunks; copies on two side streams overlap the traces"}
         scene_e2e.close()
 
     # ---- Monte Carlo rendering equation configuration

@@ -176,11 +176,10 @@ irgs_status irgs_scene_export_wide(irgs_scene sc, float* nodes, int64_t cap, int
     if (cudaDeviceSynchronize() != cudaSuccess) return IRGS_ERR_CUDA;
     int64_t nw = 1;
     if (sc->n > 1) {
-        uint32_t last[2] = {0, 0};
-        if (cudaMemcpy(&last[0], sc->wide_rank + (sc->n - 2), sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(&last[1], sc->refit_flag + (sc->n - 2), sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        uint32_t allocated = 0;   // wide nodes the collapse allocated
+        if (cudaMemcpy(&allocated, sc->wide_counters + 3, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
             return IRGS_ERR_CUDA;
-        nw = (int64_t)last[0] + last[1];
+        nw = (int64_t)allocated < sc->max_wide ? (int64_t)allocated : sc->max_wide;
     }
     if (n_wide) *n_wide = nw;
     const int64_t m = nw < cap ? nw : cap;

@@ -345,27 +345,6 @@ __global__ void k_tiny_root(int64_t n, const float* __restrict__ leaf_box, Node*
     nodes[0].d = make_int4(n == 1 ? ~0 : kNoChild, kNoChild, 0, 0);
 }
 
-// K6: 4-wide hierarchy. Every internal node at even depth of the binary tree
-// becomes a wide node whose children are its grandchildren (or its children
-// where those are leaves); the boxes come from the binary nodes, so no box
-// is recomputed.
-__global__ void k_wide_mark(int64_t n, const int32_t* __restrict__ node_parent, uint32_t* __restrict__ flag,
-                            uint32_t* status) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
-    int depth = 0;
-    int32_t p = (int32_t)i;
-    while (p != 0) {
-        p = node_parent[p];
-        if (++depth > 128 || p < 0) {
-            atomicOr(status, kErrBadTree);
-            flag[i] = 0;
-            return;
-        }
-    }
-    flag[i] = (depth & 1) == 0 ? 1u : 0u;
-}
-
 __device__ __forceinline__ void node_child(const Node& nd, int s, int32_t& c, float b[6]) {
     if (s == 0) {
         c = nd.d.x;
@@ -376,50 +355,88 @@ __device__ __forceinline__ void node_child(const Node& nd, int s, int32_t& c, fl
     }
 }
 
-__global__ void k_wide_emit(int64_t n, const Node* __restrict__ nodes, const uint32_t* __restrict__ flag,
-                            const uint32_t* __restrict__ rank, int64_t max_wide, WideNode* __restrict__ wide,
-                            uint32_t* status) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n - 1 || flag[i] == 0u) return;
-    const uint32_t w = rank[i];
-    if ((int64_t)w >= max_wide) {
-        atomicOr(status, kErrBadTree);
-        return;
-    }
-    int32_t cid[4] = {kNoChild, kNoChild, kNoChild, kNoChild};
-    float box[4][6] = {};
-    int m = 0;
-    const Node nd = nodes[i];
-    for (int s = 0; s < 2; ++s) {
-        int32_t c;
-        float b[6];
-        node_child(nd, s, c, b);
-        if (c < 0) {
-            cid[m] = c;
-            for (int k = 0; k < 6; ++k) box[m][k] = b[k];
+// K6, greedy form: wide nodes are made top-down, one frontier level per
+// launch. A wide node starts from the two children of its binary node and
+// repeatedly replaces the internal child of largest box surface area by that
+// child's two children, until it has four (or only leaves). Its internal
+// children get new wide indices and form the next frontier. Levels read and
+// clear rotating counters, so the host never waits on them.
+constexpr int kWideLevels = 64;   // >= the binary depth: each level consumes one binary level at least
+
+__device__ __forceinline__ float box_area(const float b[6]) {
+    const float dx = b[3] - b[0], dy = b[4] - b[1], dz = b[5] - b[2];
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void k_wide_root(int64_t n, int2* __restrict__ frontier, uint32_t* __restrict__ counters) {
+    frontier[0] = make_int2(0, 0);   // binary root -> wide node 0
+    counters[0] = n > 1 ? 1u : 0u;   // level 0 frontier size
+    counters[1] = 0u;
+    counters[2] = 0u;
+    counters[3] = 1u;                // wide nodes allocated
+}
+
+__global__ void k_wide_level(int level, const Node* __restrict__ nodes, const int2* __restrict__ cur,
+                             int2* __restrict__ next, uint32_t* __restrict__ counters, int64_t max_wide,
+                             WideNode* __restrict__ wide, uint32_t* status) {
+    const uint32_t cnt = counters[level % 3];
+    uint32_t* next_count = counters + (level + 1) % 3;
+    if (blockIdx.x == 0 && threadIdx.x == 0) counters[(level + 2) % 3] = 0u;   // the level after next
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += gridDim.x * blockDim.x) {
+        const int2 e = cur[i];
+        int32_t cid[4] = {kNoChild, kNoChild, kNoChild, kNoChild};
+        float box[4][6] = {};
+        const Node nd = nodes[e.x];
+        node_child(nd, 0, cid[0], box[0]);
+        node_child(nd, 1, cid[1], box[1]);
+        int m = 2;
+        while (m < 4) {
+            int best = -1;
+            float ba = -1.f;
+            for (int k = 0; k < m; ++k)
+                if (cid[k] >= 0) {
+                    const float a = box_area(box[k]);
+                    if (a > ba) {
+                        ba = a;
+                        best = k;
+                    }
+                }
+            if (best < 0) break;
+            const Node cn = nodes[cid[best]];
+            node_child(cn, 1, cid[m], box[m]);
+            node_child(cn, 0, cid[best], box[best]);
             ++m;
-        } else {
-            const Node cn = nodes[c];
-            for (int t = 0; t < 2; ++t) {
-                int32_t g;
-                float gb[6];
-                node_child(cn, t, g, gb);
-                cid[m] = g < 0 ? g : (int32_t)rank[g];
-                for (int k = 0; k < 6; ++k) box[m][k] = gb[k];
-                ++m;
-            }
         }
+        int32_t out[4] = {kNoChild, kNoChild, kNoChild, kNoChild};
+        for (int k = 0; k < m; ++k) {
+            if (cid[k] < 0) {
+                out[k] = cid[k];
+                continue;
+            }
+            const uint32_t w = atomicAdd(counters + 3, 1u);
+            if ((int64_t)w >= max_wide) {
+                atomicOr(status, kErrBadTree);
+                continue;
+            }
+            out[k] = (int32_t)w;
+            next[atomicAdd(next_count, 1u)] = make_int2(cid[k], (int32_t)w);
+        }
+        WideNode o;
+        o.lox = make_float4(box[0][0], box[1][0], box[2][0], box[3][0]);
+        o.loy = make_float4(box[0][1], box[1][1], box[2][1], box[3][1]);
+        o.loz = make_float4(box[0][2], box[1][2], box[2][2], box[3][2]);
+        o.hix = make_float4(box[0][3], box[1][3], box[2][3], box[3][3]);
+        o.hiy = make_float4(box[0][4], box[1][4], box[2][4], box[3][4]);
+        o.hiz = make_float4(box[0][5], box[1][5], box[2][5], box[3][5]);
+        o.child = make_int4(out[0], out[1], out[2], out[3]);
+        o.pad = make_int4(m, 0, 0, 0);
+        wide[e.y] = o;
     }
-    WideNode o;
-    o.lox = make_float4(box[0][0], box[1][0], box[2][0], box[3][0]);
-    o.loy = make_float4(box[0][1], box[1][1], box[2][1], box[3][1]);
-    o.loz = make_float4(box[0][2], box[1][2], box[2][2], box[3][2]);
-    o.hix = make_float4(box[0][3], box[1][3], box[2][3], box[3][3]);
-    o.hiy = make_float4(box[0][4], box[1][4], box[2][4], box[3][4]);
-    o.hiz = make_float4(box[0][5], box[1][5], box[2][5], box[3][5]);
-    o.child = make_int4(cid[0], cid[1], cid[2], cid[3]);
-    o.pad = make_int4(m, 0, 0, 0);
-    wide[w] = o;
+}
+
+// After the last level the frontier must be empty.
+__global__ void k_wide_check(const uint32_t* __restrict__ counters, uint32_t* status) {
+    if (counters[kWideLevels % 3] != 0u) atomicOr(status, kErrBadTree);
 }
 
 // Wide root of a one-surfel (or empty) scene.
@@ -456,10 +473,25 @@ void free_scene(irgs_scene sc) {
     void* ptrs[] = {sc->nodes, sc->rec, sc->feat, sc->q_raw, sc->scale, sc->leaf_box, sc->keys,
                     sc->perm, sc->inv_perm, sc->status, sc->rec_user, sc->box_user, sc->keys_tmp, sc->vals_tmp,
                     sc->hist, sc->bounds, sc->leaf_parent, sc->node_parent, sc->refit_flag, sc->wide,
-                    sc->wide_rank};
+                    sc->wide_frontier, sc->wide_counters};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete sc;
+}
+
+// Enqueue the greedy 4-wide collapse of the scene's binary hierarchy (n > 1).
+static void enqueue_wide(irgs_scene sc, cudaStream_t st) {
+    const int64_t n = sc->n;
+    int2* a = sc->wide_frontier;
+    int2* b = sc->wide_frontier + n;
+    k_wide_root<<<1, 1, 0, st>>>(n, a, sc->wide_counters);
+    for (int level = 0; level < kWideLevels; ++level) {
+        k_wide_level<<<152 * 4, 256, 0, st>>>(level, sc->nodes, a, b, sc->wide_counters, sc->max_wide, sc->wide,
+                                             sc->status);
+        int2* t = a; a = b; b = t;
+    }
+    k_wide_check<<<1, 1, 0, st>>>(sc->wide_counters, sc->status);
+    count_launches(kWideLevels + 2);
 }
 
 // Enqueue the whole build (K1-K5) for surfels `s` into the scene's buffers.
@@ -506,13 +538,7 @@ static irgs_status enqueue_build(irgs_scene sc, const irgs_surfels* s, cudaStrea
     count_launches(n == 0 ? 1 : 15 + (F > 0) + (n == 1 ? 1 : 2));
     if (sc->wide != nullptr) {
         if (n > 1) {
-            const int T = 256;
-            k_wide_mark<<<blocks_for(n - 1, T), T, 0, st>>>(n, sc->node_parent, sc->refit_flag, sc->status);
-            A(cudaMemcpyAsync(sc->wide_rank, sc->refit_flag, sizeof(uint32_t) * (n - 1), cudaMemcpyDeviceToDevice, st));
-            k_scan_exclusive<<<1, 1024, 0, st>>>(sc->wide_rank, n - 1);
-            k_wide_emit<<<blocks_for(n - 1, T), T, 0, st>>>(n, sc->nodes, sc->refit_flag, sc->wide_rank, sc->max_wide,
-                                                           sc->wide, sc->status);
-            count_launches(3);
+            enqueue_wide(sc, st);
         } else {
             k_wide_tiny<<<1, 1, 0, st>>>(n, sc->leaf_box, sc->wide);
             count_launches(1);
@@ -586,10 +612,11 @@ irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_
     A(dalloc(&sc->leaf_parent, n, B));
     A(dalloc(&sc->node_parent, nn, B));
     A(dalloc(&sc->refit_flag, nn, B));
-    A(dalloc(&sc->wide_rank, nn, B));
-    // even-depth internal nodes of a binary tree with n leaves: at most 2(n-1)/3 + 1
-    sc->max_wide = 2 * nn / 3 + 2;
+    // every wide node takes at least one binary internal node
+    sc->max_wide = nn + 1;
     A(dalloc(&sc->wide, sc->max_wide, B));
+    A(dalloc(&sc->wide_frontier, 2 * (n > 0 ? n : 1), B));
+    A(dalloc(&sc->wide_counters, 4, B));
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_scene(sc);
@@ -642,14 +669,12 @@ irgs_status refit_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t 
     }
     if (n <= 1) k_tiny_root<<<1, 1, 0, st>>>(n, sc->leaf_box, sc->nodes);
     if (n > 1) {
-        k_wide_mark<<<blocks_for(n - 1, T), T, 0, st>>>(n, sc->node_parent, sc->refit_flag, sc->status);
-        k_wide_emit<<<blocks_for(n - 1, T), T, 0, st>>>(n, sc->nodes, sc->refit_flag, sc->wide_rank, sc->max_wide,
-                                                       sc->wide, sc->status);
+        enqueue_wide(sc, st);
     } else {
         k_wide_tiny<<<1, 1, 0, st>>>(n, sc->leaf_box, sc->wide);
     }
-    // boxes, gather, features, refit, mark, emit (or the tiny root and tiny wide node)
-    count_launches(n == 0 ? 2 : (n == 1 ? 4 + (F > 0) : 5 + (F > 0)));
+    // boxes, gather, features, refit (or the tiny root and tiny wide node); the collapse counts its own
+    count_launches(n == 0 ? 2 : (n == 1 ? 4 + (F > 0) : 3 + (F > 0)));
     A(cudaGetLastError());
     return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
 }

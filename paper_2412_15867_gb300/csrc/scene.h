@@ -27,6 +27,8 @@ struct irgs_scene_s {
     uint32_t* status = nullptr;       // device error word
     irgs::WideNode* wide = nullptr;   // [max_wide] 4-wide hierarchy
     int64_t max_wide = 0;
+    int2* wide_frontier = nullptr;    // [2n] (binary node, wide index) frontiers of the collapse
+    uint32_t* wide_counters = nullptr;// [4] rotating frontier sizes, wide nodes allocated
 
     // build scratch (kept for rebuilds)
     float4* rec_user = nullptr;       // [n*4]
@@ -38,7 +40,6 @@ struct irgs_scene_s {
     int32_t* leaf_parent = nullptr;   // [n]
     int32_t* node_parent = nullptr;   // [max(n-1,1)]
     uint32_t* refit_flag = nullptr;   // [max(n-1,1)]
-    uint32_t* wide_rank = nullptr;    // [max(n-1,1)] even-depth flag, then its exclusive scan
 
     irgs::SceneView view() const {
         irgs::SceneView v;

@@ -271,7 +271,7 @@ def test_wide_hierarchy_invariants():
     perm, keys, nodes, boxes = S.export()
     W = S.export_wide()
     n = sc.n
-    assert 1 <= W.shape[0] <= 2 * (n - 1) // 3 + 2
+    assert 1 <= W.shape[0] <= n - 1          # each wide node takes at least one binary internal node
     lo = W[:, 0:12].reshape(-1, 3, 4)       # [node, axis, child]
     hi = W[:, 12:24].reshape(-1, 3, 4)
     ch = W[:, 24:28].view(np.int32)
