@@ -370,7 +370,12 @@ irgs_status irgs_envmap_export(irgs_envmap envmap, float* irr, float* pref, floa
  *                        (0.04 A + B)(N_r.v, R_r)),
  * Pref linear between its two nearest roughness levels, all maps bilinear.
  * out_rgb [P,3]; out_vis [P] and out_ind [P,3] (means of V and of the
- * indirect term over all samples) may be NULL.
+ * indirect term over all samples) may be NULL. By default the samples of
+ * all points are regrouped by direction and origin and traced with one
+ * stack per ray (scratch from the stream-ordered allocator, ~64 bytes per
+ * sample in chunks of at most 2^24); IRGS_FLAG_PER_THREAD selects the fused
+ * kernel (a warp per point tracing its own samples). Both give the same
+ * traces.
  */
 irgs_status irgs_relight(irgs_scene scene, irgs_envmap envmap, const float* x, const float* n,
                          const float* albedo, const float* rough, const float* wo, int64_t n_points,

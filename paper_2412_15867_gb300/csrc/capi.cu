@@ -331,8 +331,8 @@ irgs_status irgs_relight(irgs_scene sc, irgs_envmap m, const float* x, const flo
     if (n_points > 0 && (!x || !n || !albedo || !rough || !wo || !out_rgb)) return IRGS_ERR_INVALID_ARG;
     if (n_points >= (int64_t)UINT32_MAX * 4) return IRGS_ERR_INVALID_ARG;
     if ((s = use_device(sc)) != IRGS_OK) return s;
-    return irgs::launch_relight(sc->view(), m, x, n, albedo, rough, wo, n_points, n_samples, seed, *params, out_rgb,
-                                out_vis, out_ind, static_cast<cudaStream_t>(stream));
+    return irgs::launch_relight(sc->view(), sc->bounds, m, x, n, albedo, rough, wo, n_points, n_samples, seed,
+                                *params, out_rgb, out_vis, out_ind, static_cast<cudaStream_t>(stream));
 }
 
 irgs_status irgs_build_lbvh_noalloc(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,

@@ -26,6 +26,7 @@
 #include "scene.h"
 #include "shade.cuh"
 #include "trace.cuh"
+#include "wave.cuh"
 
 namespace irgs {
 namespace {
@@ -260,6 +261,74 @@ __device__ __forceinline__ float2 lut_lookup(const float* __restrict__ lut, floa
 
 __device__ __forceinline__ f3 ld3r(const float* p, int64_t i) { return mk3(p[3 * i], p[3 * i + 1], p[3 * i + 2]); }
 
+// One environment sample w (density pdf) of a point, given its trace (the
+// blended [albedo, roughness, normal] C and transmittance T): adds the
+// estimate term f L_i (w.n) / pdf to acc[0..2], V to acc[3] and L_ind to
+// acc[4..6].
+__device__ __forceinline__ void relight_sample(const EnvMaps& M, const ShadeFrame& F, f3 a, f3 w, float pdf,
+                                               const float (&C)[7], float T, float (&acc)[7]) {
+    const float V = T, O = 1.f - T;
+    f3 Lind = mk3(0.f, 0.f, 0.f);
+    if (O > 0.f) {
+        const f3 Ar = mul3(mk3(C[0], C[1], C[2]), 1.f / O);
+        const float Rr = C[3] / O;
+        const f3 v = mul3(w, -1.f);
+        f3 Nr = mk3(C[4], C[5], C[6]);
+        const float len2 = dot3(Nr, Nr);
+        Nr = len2 > 1e-24f ? mul3(Nr, rsqrtf(len2)) : v;
+        if (dot3(Nr, v) < 0.f) Nr = mul3(Nr, -1.f);
+        const float mu = fminf(dot3(Nr, v), 1.f);
+        const f3 refl = sub3(mul3(Nr, 2.f * mu), v);
+        const f3 irr = env_lookup(M.irr, kIrrH, kIrrW, Nr);
+        const f3 pf = pref_lookup(M, refl, Rr);
+        const float2 AB = lut_lookup(M.lut, mu, Rr);
+        const float spec = kF0 * AB.x + AB.y;
+        Lind = mul3(add3(mk3(Ar.x * irr.x, Ar.y * irr.y, Ar.z * irr.z), mul3(pf, spec)), O);
+    }
+    acc[3] += V;
+    acc[4] += Lind.x;
+    acc[5] += Lind.y;
+    acc[6] += Lind.z;
+    const float ni = dot3(F.n, w);
+    if (ni <= 0.f) return;
+    const f3 h = normalize3(add3(w, F.wo));
+    const float nh = dot3(F.n, h), oh = dot3(F.wo, h);
+    const float q = ggx_q(F, h, nh);
+    const float D = F.a2 / (kPi * q * q);
+    const float G1i = ni / (ni * (1.f - F.kk) + F.kk);
+    const float fs_cos = D * fresnel(oh) * G1i * F.G1o / (4.f * F.no);   // f_s (w.n)
+    const f3 E = env_lookup(M.env, M.H, M.W, w);
+    const float Li[3] = {V * E.x + Lind.x, V * E.y + Lind.y, V * E.z + Lind.z};
+    const float av[3] = {a.x, a.y, a.z};
+    const float inv_pdf = 1.f / pdf;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] += (av[c] * (1.f / kPi) * ni + fs_cos) * Li[c] * inv_pdf;
+}
+
+// Final per-point sums of a warp (fixed butterfly order).
+__device__ __forceinline__ void relight_write(float (&acc)[7], int lane, int64_t p, int Sn, float* __restrict__ rgb,
+                                              float* __restrict__ vis, float* __restrict__ ind) {
+#pragma unroll
+    for (int k = 0; k < 7; ++k)
+        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+    if (lane == 0) {
+        const float inv = 1.f / (float)Sn;
+        for (int c = 0; c < 3; ++c) rgb[3 * p + c] = acc[c] * inv;
+        if (vis != nullptr) vis[p] = acc[3] * inv;
+        if (ind != nullptr)
+            for (int c = 0; c < 3; ++c) ind[3 * p + c] = acc[4 + c] * inv;
+    }
+}
+
+// Environment sample s of point p (uniforms as in the shading estimate).
+__device__ __forceinline__ bool relight_dir(const EnvMaps& M, int64_t p, int s, int Sn, uint64_t seed, f3& w,
+                                            float& pdf) {
+    const uint64_t i0 = ((uint64_t)p * (uint64_t)Sn + (uint64_t)s) * 2ull;
+    const double u1 = (double)u01_from_bits(splitmix64_at(seed, i0));
+    const double u2 = (double)u01_from_bits(splitmix64_at(seed, i0 + 1));
+    return env_sample(M.row_cdf, M.col_cdf, M.H, M.W, u1, u2, w, pdf);
+}
+
 // One warp per point; lanes take samples s = lane, lane + 32, ...; the traced
 // channels are [albedo (3), roughness, normal (3)].
 template <int K>
@@ -278,62 +347,126 @@ __global__ void __launch_bounds__(kRelightThreads) k_relight(SceneView S, EnvMap
     const ShadeFrame F = shade_frame(ld3r(ng, p), ld3r(wog, p), rg[p]);
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // rgb, V, L_ind
     for (int s = lane; s < Sn; s += 32) {
-        const uint64_t i0 = ((uint64_t)p * (uint64_t)Sn + (uint64_t)s) * 2ull;
-        const double u1 = (double)u01_from_bits(splitmix64_at(seed, i0));
-        const double u2 = (double)u01_from_bits(splitmix64_at(seed, i0 + 1));
         f3 w;
         float pdf;
-        if (!env_sample(M.row_cdf, M.col_cdf, M.H, M.W, u1, u2, w, pdf)) continue;
+        if (!relight_dir(M, p, s, Sn, seed, w, pdf)) continue;
         MarchState<K, 7> st;
         const bool ok = march_forward<K, 7, false>(S, make_ray(x, w), TP, st, nullptr, 0, true);
         if (!ok) atomicOr(S.status, kErrStackOverflow);
-        const float V = st.T, O = 1.f - st.T;
-        f3 Lind = mk3(0.f, 0.f, 0.f);
-        if (O > 0.f) {
-            const f3 Ar = mul3(mk3(st.C[0], st.C[1], st.C[2]), 1.f / O);
-            const float Rr = st.C[3] / O;
-            const f3 v = mul3(w, -1.f);
-            f3 Nr = mk3(st.C[4], st.C[5], st.C[6]);
-            const float len2 = dot3(Nr, Nr);
-            Nr = len2 > 1e-24f ? mul3(Nr, rsqrtf(len2)) : v;
-            if (dot3(Nr, v) < 0.f) Nr = mul3(Nr, -1.f);
-            const float mu = fminf(dot3(Nr, v), 1.f);
-            const f3 refl = sub3(mul3(Nr, 2.f * mu), v);
-            const f3 irr = env_lookup(M.irr, kIrrH, kIrrW, Nr);
-            const f3 pf = pref_lookup(M, refl, Rr);
-            const float2 AB = lut_lookup(M.lut, mu, Rr);
-            const float spec = kF0 * AB.x + AB.y;
-            Lind = mul3(add3(mk3(Ar.x * irr.x, Ar.y * irr.y, Ar.z * irr.z), mul3(pf, spec)), O);
-        }
-        acc[3] += V;
-        acc[4] += Lind.x;
-        acc[5] += Lind.y;
-        acc[6] += Lind.z;
-        const float ni = dot3(F.n, w);
-        if (ni <= 0.f) continue;
-        const f3 h = normalize3(add3(w, F.wo));
-        const float nh = dot3(F.n, h), oh = dot3(F.wo, h);
-        const float q = ggx_q(F, h, nh);
-        const float D = F.a2 / (kPi * q * q);
-        const float G1i = ni / (ni * (1.f - F.kk) + F.kk);
-        const float fs_cos = D * fresnel(oh) * G1i * F.G1o / (4.f * F.no);   // f_s (w.n)
-        const f3 E = env_lookup(M.env, M.H, M.W, w);
-        const float Li[3] = {V * E.x + Lind.x, V * E.y + Lind.y, V * E.z + Lind.z};
-        const float av[3] = {a.x, a.y, a.z};
-        const float inv_pdf = 1.f / pdf;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc[c] += (av[c] * (1.f / kPi) * ni + fs_cos) * Li[c] * inv_pdf;
+        relight_sample(M, F, a, w, pdf, st.C, st.T, acc);
     }
+    relight_write(acc, lane, p, Sn, rgb, vis, ind);
+}
+
+// Wavefront form: samples generated one thread each, regrouped by direction
+// bin and origin, traced in that order with one stack per ray, then
+// estimated per point from the stored traces with the same per-sample
+// arithmetic and reduction order as k_relight.
+__global__ void k_relight_gen(EnvMaps M, const float* __restrict__ xg, int64_t p0, int64_t rays, int Sn,
+                              uint64_t seed, const uint32_t* __restrict__ bounds, float4* __restrict__ dir,
+                              uint32_t* __restrict__ key, int32_t* __restrict__ val) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= rays) return;
+    const int64_t p = p0 + i / Sn;
+    f3 w = mk3(0.f, 0.f, 1.f);
+    float pdf = 0.f;
+    const bool ok = relight_dir(M, p, (int)(i % Sn), Sn, seed, w, pdf);
+    dir[i] = make_float4(w.x, w.y, w.z, ok ? pdf : 0.f);
+    key[i] = ok ? wave_key(ld3r(xg, p), w, bounds) : kInvalidWaveKey;
+    val[i] = (int32_t)i;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kRelightThreads, 6) k_relight_trace(SceneView S, TraceParams P,
+                                                                      const float* __restrict__ xg, int64_t p0,
+                                                                      int Sn, const float4* __restrict__ dir,
+                                                                      const int32_t* __restrict__ order,
+                                                                      int64_t rays, float4* __restrict__ res) {
+    static_assert(kRelightThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
+    const int64_t j = blockIdx.x * (int64_t)kRelightThreads + threadIdx.x;
+    if (j >= rays) return;
+    const int64_t i = order[j];
+    const float4 d4 = dir[i];
+    MarchState<K, 7> st;
+    if (d4.w > 0.f) {
+        const bool ok = march_forward<K, 7, false>(S, make_ray(ld3r(xg, p0 + i / Sn), mk3(d4.x, d4.y, d4.z)), P,
+                                                   st, nullptr, 0, true);
+        if (!ok) atomicOr(S.status, kErrStackOverflow);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 7; ++k)
-        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
-    if (lane == 0) {
-        const float inv = 1.f / (float)Sn;
-        for (int c = 0; c < 3; ++c) rgb[3 * p + c] = acc[c] * inv;
-        if (vis != nullptr) vis[p] = acc[3] * inv;
-        if (ind != nullptr)
-            for (int c = 0; c < 3; ++c) ind[3 * p + c] = acc[4 + c] * inv;
+        for (int c = 0; c < 7; ++c) st.C[c] = 0.f;
+        st.T = 1.f;
     }
+    res[2 * i] = make_float4(st.C[0], st.C[1], st.C[2], st.C[3]);
+    res[2 * i + 1] = make_float4(st.C[4], st.C[5], st.C[6], st.T);
+}
+
+__global__ void __launch_bounds__(kRelightThreads) k_relight_shade(EnvMaps M, const float* __restrict__ ng,
+                                                                   const float* __restrict__ ag,
+                                                                   const float* __restrict__ rg,
+                                                                   const float* __restrict__ wog, int64_t p0,
+                                                                   int64_t np, int Sn, const float4* __restrict__ dir,
+                                                                   const float4* __restrict__ res,
+                                                                   float* __restrict__ rgb, float* __restrict__ vis,
+                                                                   float* __restrict__ ind) {
+    const int lane = threadIdx.x & 31;
+    const int64_t k = blockIdx.x * (int64_t)(kRelightThreads / 32) + (threadIdx.x >> 5);
+    if (k >= np) return;
+    const int64_t p = p0 + k;
+    const f3 a = ld3r(ag, p);
+    const ShadeFrame F = shade_frame(ld3r(ng, p), ld3r(wog, p), rg[p]);
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int s = lane; s < Sn; s += 32) {
+        const int64_t i = k * Sn + s;
+        const float4 d4 = __ldg(dir + i);
+        if (!(d4.w > 0.f)) continue;
+        const float4 r0 = __ldg(res + 2 * i), r1 = __ldg(res + 2 * i + 1);
+        const float C[7] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z};
+        relight_sample(M, F, a, mk3(d4.x, d4.y, d4.z), d4.w, C, r1.w, acc);
+    }
+    relight_write(acc, lane, p, Sn, rgb, vis, ind);
+}
+
+inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
+
+constexpr int64_t kRelightChunkRays = int64_t(1) << 24;
+
+template <int K>
+cudaError_t relight_wave(const SceneView& S, const uint32_t* bounds, const EnvMaps& M, const float* x,
+                         const float* n, const float* a, const float* r, const float* wo, int64_t P, int Sn,
+                         uint64_t seed, const TraceParams& TP, float* rgb, float* vis, float* ind, cudaStream_t st) {
+    const int64_t pc = kRelightChunkRays / Sn > 0 ? kRelightChunkRays / Sn : 1;
+    const int64_t cap = (P < pc ? P : pc) * Sn;
+    const int64_t hw = sort_hist_words(cap);
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t bytes = al(16 * cap) + 4 * al(4 * cap) + al(4 * hw) + al(32 * cap);
+    unsigned char* base = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, st);
+    if (e != cudaSuccess) return e;
+    size_t off = 0;
+    auto take = [&](size_t b) { unsigned char* q = base + off; off += al(b); return q; };
+    float4* dir = reinterpret_cast<float4*>(take(16 * cap));
+    uint32_t* key = reinterpret_cast<uint32_t*>(take(4 * cap));
+    int32_t* val = reinterpret_cast<int32_t*>(take(4 * cap));
+    uint32_t* ktmp = reinterpret_cast<uint32_t*>(take(4 * cap));
+    int32_t* vtmp = reinterpret_cast<int32_t*>(take(4 * cap));
+    uint32_t* hist = reinterpret_cast<uint32_t*>(take(4 * hw));
+    float4* res = reinterpret_cast<float4*>(take(32 * cap));
+    for (int64_t p0 = 0; p0 < P && e == cudaSuccess; p0 += pc) {
+        const int64_t np = P - p0 < pc ? P - p0 : pc;
+        const int64_t rays = np * Sn;
+        k_relight_gen<<<grid_for(rays, 256), 256, 0, st>>>(M, x, p0, rays, Sn, seed, bounds, dir, key, val);
+        e = sort_pairs(key, val, ktmp, vtmp, hist, rays, st);
+        if (e != cudaSuccess) break;
+        k_relight_trace<K><<<grid_for(rays, kRelightThreads), kRelightThreads, 0, st>>>(S, TP, x, p0, Sn, dir, val,
+                                                                                      rays, res);
+        k_relight_shade<<<grid_for(np, kRelightThreads / 32), kRelightThreads, 0, st>>>(M, n, a, r, wo, p0, np, Sn,
+                                                                                       dir, res, rgb, vis, ind);
+        count_launches(3);
+        e = cudaGetLastError();
+    }
+    const cudaError_t ef = cudaFreeAsync(base, st);
+    return e != cudaSuccess ? e : ef;
 }
 
 template <class T>
@@ -402,26 +535,44 @@ irgs_status export_envmap_impl(irgs_envmap m, float* irr, float* pref, float* lu
     return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
 }
 
-irgs_status launch_relight(const SceneView& S, irgs_envmap m, const float* x, const float* n, const float* albedo,
-                           const float* rough, const float* wo, int64_t P, int32_t n_samples, uint64_t seed,
-                           const irgs_trace_params& p, float* rgb, float* vis, float* ind, cudaStream_t st) {
+irgs_status launch_relight(const SceneView& S, const uint32_t* bounds, irgs_envmap m, const float* x,
+                           const float* n, const float* albedo, const float* rough, const float* wo, int64_t P,
+                           int32_t n_samples, uint64_t seed, const irgs_trace_params& p, float* rgb, float* vis,
+                           float* ind, cudaStream_t st) {
     if (P == 0) return IRGS_OK;
     const TraceParams TP = to_params(p);
     const EnvMaps M{m->env, m->irr, m->pref, m->lut, m->row_cdf, m->col_cdf, m->H, m->W};
-    const int64_t blocks = (P + kRelightThreads / 32 - 1) / (kRelightThreads / 32);
-    switch (p.k) {
-        case 8:
-            k_relight<8><<<(unsigned)blocks, kRelightThreads, 0, st>>>(S, M, x, n, albedo, rough, wo, P, n_samples,
-                                                                      seed, TP, rgb, vis, ind);
-            break;
-        case 16:
-            k_relight<16><<<(unsigned)blocks, kRelightThreads, 0, st>>>(S, M, x, n, albedo, rough, wo, P, n_samples,
-                                                                       seed, TP, rgb, vis, ind);
-            break;
-        default: return IRGS_ERR_UNSUPPORTED;
+    cudaError_t e = cudaSuccess;
+    if ((p.flags & IRGS_FLAG_PER_THREAD) != 0u) {
+        // fused: a warp per point tracing its own samples
+        const int64_t blocks = (P + kRelightThreads / 32 - 1) / (kRelightThreads / 32);
+        switch (p.k) {
+            case 8:
+                k_relight<8><<<(unsigned)blocks, kRelightThreads, 0, st>>>(S, M, x, n, albedo, rough, wo, P,
+                                                                          n_samples, seed, TP, rgb, vis, ind);
+                break;
+            case 16:
+                k_relight<16><<<(unsigned)blocks, kRelightThreads, 0, st>>>(S, M, x, n, albedo, rough, wo, P,
+                                                                           n_samples, seed, TP, rgb, vis, ind);
+                break;
+            default: return IRGS_ERR_UNSUPPORTED;
+        }
+        count_launches(1);
+        e = cudaGetLastError();
+    } else {
+        switch (p.k) {
+            case 8:
+                e = relight_wave<8>(S, bounds, M, x, n, albedo, rough, wo, P, n_samples, seed, TP, rgb, vis, ind, st);
+                break;
+            case 16:
+                e = relight_wave<16>(S, bounds, M, x, n, albedo, rough, wo, P, n_samples, seed, TP, rgb, vis, ind,
+                                     st);
+                break;
+            default: return IRGS_ERR_UNSUPPORTED;
+        }
     }
-    count_launches(1);
-    return cudaGetLastError() == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+    if (e == cudaErrorMemoryAllocation) return IRGS_ERR_OOM;
+    return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
 }
 
 }  // namespace irgs

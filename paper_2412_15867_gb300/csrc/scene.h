@@ -83,9 +83,10 @@ irgs_status build_envmap_impl(const float* env, int32_t H, int32_t W, cudaStream
 void free_envmap(irgs_envmap m);
 irgs_status export_envmap_impl(irgs_envmap m, float* irr, float* pref, float* lut, double* row_cdf,
                                double* col_cdf, cudaStream_t st);
-irgs_status launch_relight(const SceneView& sv, irgs_envmap m, const float* x, const float* n, const float* albedo,
-                           const float* rough, const float* wo, int64_t P, int32_t n_samples, uint64_t seed,
-                           const irgs_trace_params& p, float* rgb, float* vis, float* ind, cudaStream_t st);
+irgs_status launch_relight(const SceneView& sv, const uint32_t* bounds, irgs_envmap m, const float* x,
+                           const float* n, const float* albedo, const float* rough, const float* wo, int64_t P,
+                           int32_t n_samples, uint64_t seed, const irgs_trace_params& p, float* rgb, float* vis,
+                           float* ind, cudaStream_t st);
 
 // scene.cu
 irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_t st, irgs_scene* out);

@@ -28,6 +28,7 @@
 #include "shade.cuh"
 #include "trace.cuh"
 #include "trace_bwd.cuh"
+#include "wave.cuh"
 
 namespace irgs {
 namespace {
@@ -35,51 +36,8 @@ namespace {
 constexpr int kWaveThreads = 128;
 constexpr int64_t kWaveChunkRays = int64_t(1) << 24;
 constexpr int kWaveSavedHits = 64;   // 12% of secondary rays blend more than 32 hits, 0.02% more than 64
-constexpr uint32_t kInvalidKey = 0xffffffffu;
 
 __device__ __forceinline__ f3 ld3w(const float* p, int64_t i) { return mk3(p[3 * i], p[3 * i + 1], p[3 * i + 2]); }
-
-// Inverse of the order-preserving float view the scene's bounds are kept in.
-__device__ __forceinline__ float bound_value(uint32_t u) {
-    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
-}
-
-// 8-bit value -> every third bit of a 24-bit word.
-__device__ __forceinline__ uint32_t spread8(uint32_t v) {
-    v &= 0xffu;
-    v = (v | (v << 8)) & 0x0300f00fu;
-    v = (v | (v << 4)) & 0x030c30c3u;
-    v = (v | (v << 2)) & 0x09249249u;
-    return v;
-}
-
-// Regrouping key of a ray: octahedral direction bin (8 x 8) above the
-// Morton code of the origin quantised to 256 cells per axis of the scene's
-// centre bounds (clamped).
-__device__ __forceinline__ uint32_t wave_key(f3 x, f3 d, const uint32_t* __restrict__ bounds) {
-    const float c[3] = {x.x, x.y, x.z};
-    uint32_t q[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float lo = bound_value(bounds[k]), hi = bound_value(bounds[3 + k]);
-        const float ext = hi - lo;
-        float t = ext > 0.f ? (c[k] - lo) / ext : 0.5f;
-        t = t == t ? fminf(fmaxf(t, 0.f), 1.f) : 0.f;
-        q[k] = (uint32_t)fminf(t * 256.f, 255.f);
-    }
-    const uint32_t morton = (spread8(q[0]) << 2) | (spread8(q[1]) << 1) | spread8(q[2]);
-    const float l1 = fabsf(d.x) + fabsf(d.y) + fabsf(d.z);
-    float u = d.x / l1, v = d.y / l1;
-    if (d.z < 0.f) {
-        const float uu = (1.f - fabsf(v)) * (u >= 0.f ? 1.f : -1.f);
-        const float vv = (1.f - fabsf(u)) * (v >= 0.f ? 1.f : -1.f);
-        u = uu;
-        v = vv;
-    }
-    const uint32_t bu = (uint32_t)fminf(fmaxf((u * 0.5f + 0.5f) * 8.f, 0.f), 7.f);
-    const uint32_t bv = (uint32_t)fminf(fmaxf((v * 0.5f + 0.5f) * 8.f, 0.f), 7.f);
-    return ((bu << 3 | bv) << 24) | morton;
-}
 
 // One thread per sample of points [p0, p0 + rays / St): direction (w = 1 if
 // the sample is valid) and its regrouping key (invalid samples sort last).
@@ -94,7 +52,7 @@ __global__ void k_wave_gen(const float* __restrict__ xg, const float* __restrict
     const ShadeFrame F = shade_frame(ld3w(ng, p), ld3w(wog, p), rg[p]);
     const ShadeSample d = draw_sample(F, mode, (uint64_t)p, s, St, nd, seed);
     dir[i] = make_float4(d.wi.x, d.wi.y, d.wi.z, d.valid ? 1.f : 0.f);
-    key[i] = d.valid ? wave_key(ld3w(xg, p), d.wi, bounds) : kInvalidKey;
+    key[i] = d.valid ? wave_key(ld3w(xg, p), d.wi, bounds) : kInvalidWaveKey;
     val[i] = (int32_t)i;
 }
 

@@ -56,12 +56,12 @@ def check(out, ref, frac=0.99):
     return st
 
 
-@pytest.mark.parametrize("k,S", [(16, 64), (8, 13)])
-def test_relight_matches_oracle_object_scene(k, S):
+@pytest.mark.parametrize("k,S,flags", [(16, 64, 0), (8, 13, 0), (16, 64, 1)])
+def test_relight_matches_oracle_object_scene(k, S, flags):
     sc = synth.object_scene(n=20_000, seed=411)
     x, n, a, r, wo = synth.gbuffer_points(48, seed=412)
     env = synth.env_map(seed=413, height=64, width=128)
-    p = irgs.TraceParams(k=k, t_min=1e-3, **MAT)
+    p = irgs.TraceParams(k=k, t_min=1e-3, flags=flags, **MAT)
     S_ = make_scene(irgs, sc)
     E = irgs.EnvMap(dev(env))
     out = irgs.relight(S_, E, dev(x), dev(n), dev(a), dev(r), dev(wo), S, 77, p, want_aux=True)
@@ -99,3 +99,19 @@ def test_relight_argument_checks():
         irgs.relight(S_, E, *args, 0, 0, irgs.TraceParams(k=8, t_min=1e-3, **MAT))
     with pytest.raises(irgs.IrgsError):
         irgs.relight(S_, E, *args, 8, 0, irgs.TraceParams(k=8, t_min=0.0, **MAT))
+
+
+def test_relight_wavefront_and_fused_agree():
+    sc = synth.object_scene(n=10_000, seed=441)
+    x, n, a, r, wo = synth.gbuffer_points(70, seed=442)
+    env = synth.env_map(seed=443, height=32, width=64)
+    S_ = make_scene(irgs, sc)
+    E = irgs.EnvMap(dev(env))
+    args = (dev(x), dev(n), dev(a), dev(r), dev(wo), 45, 3)
+    o1 = irgs.relight(S_, E, *args, irgs.TraceParams(k=16, t_min=1e-3, **MAT), want_aux=True)
+    o2 = irgs.relight(S_, E, *args, irgs.TraceParams(k=16, t_min=1e-3, flags=irgs.FLAG_PER_THREAD, **MAT),
+                      want_aux=True)
+    torch.cuda.synchronize()
+    assert S_.status() == 0
+    for k in o1:
+        assert torch.allclose(o1[k], o2[k], rtol=1e-6, atol=1e-6), k
