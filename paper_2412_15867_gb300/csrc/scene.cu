@@ -170,6 +170,62 @@ __global__ void k_scan_exclusive(uint32_t* __restrict__ a, int64_t m) {
     }
 }
 
+// Multi-block exclusive scan for long arrays: each block scans a tile of
+// kScanTile words in place and records the tile total; the totals are scanned
+// by k_scan_exclusive; a last pass adds each tile's offset.
+constexpr int kScanThreads = 1024;
+constexpr int kScanTile = 4 * kScanThreads;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(uint32_t* __restrict__ a, int64_t m,
+                                                              uint32_t* __restrict__ sums) {
+    __shared__ uint32_t warp_tot[kScanThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + 4 * threadIdx.x;
+    uint32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = base + k < m ? a[base + k] : 0u;
+    const uint32_t t = v[0] + v[1] + v[2] + v[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = t;   // inclusive scan of the thread totals within the warp
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kScanThreads / 32 ? warp_tot[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += y;
+        }
+        if (lane < kScanThreads / 32) warp_tot[lane] = wi - w;   // exclusive warp offsets
+        if (lane == kScanThreads / 32 - 1) sums[blockIdx.x] = wi;
+    }
+    __syncthreads();
+    uint32_t run = warp_tot[warp] + inc - t;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < m) a[base + k] = run;
+        run += v[k];
+    }
+}
+
+__global__ void k_scan_add(uint32_t* __restrict__ a, int64_t m, const uint32_t* __restrict__ sums) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < m) a[i] += sums[i / kScanTile];
+}
+
+// Exclusive scan of m words using `sums` (ceil(m / kScanTile) words) as scratch.
+void scan_long(uint32_t* a, int64_t m, uint32_t* sums, cudaStream_t st) {
+    const int64_t tiles = (m + kScanTile - 1) / kScanTile;
+    k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, st>>>(a, m, sums);
+    k_scan_exclusive<<<1, 1024, 0, st>>>(sums, tiles);
+    k_scan_add<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(a, m, sums);
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(
     const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin, int64_t n, int shift, int tiles,
     const uint32_t* __restrict__ offs, uint32_t* __restrict__ kout, int32_t* __restrict__ vout) {
@@ -550,7 +606,8 @@ static irgs_status enqueue_build(irgs_scene sc, const irgs_surfels* s, cudaStrea
 
 int64_t sort_hist_words(int64_t n) {
     const int64_t tiles = (n + kTile - 1) / kTile;
-    return 256 * (tiles > 0 ? tiles : 1);
+    const int64_t words = 256 * (tiles > 0 ? tiles : 1);
+    return words + (words + kScanTile - 1) / kScanTile;   // digit counts, then the scan's tile sums
 }
 
 cudaError_t sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp, int32_t* vals_tmp, uint32_t* hist,
@@ -563,12 +620,12 @@ cudaError_t sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp, int32_
     uint32_t* kb = keys_tmp; int32_t* vb = vals_tmp;
     for (int shift = 0; shift < 8 * passes; shift += 8) {
         k_sort_hist<<<(unsigned)tiles, 256, 0, st>>>(ka, n, shift, (int)tiles, hist);
-        k_scan_exclusive<<<1, 1024, 0, st>>>(hist, 256 * tiles);
+        scan_long(hist, 256 * tiles, hist + 256 * tiles, st);
         k_sort_scatter<<<(unsigned)tiles, kSortThreads, 0, st>>>(ka, va, n, shift, (int)tiles, hist, kb, vb);
         uint32_t* tk = ka; ka = kb; kb = tk;
         int32_t* tv = va; va = vb; vb = tv;
     }
-    count_launches(3 * passes);
+    count_launches(5 * passes);
     return cudaGetLastError();
 }
 
