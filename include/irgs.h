@@ -107,9 +107,11 @@ uint64_t irgs_kernel_launches(void);
  * Eq. 5 gives the support radius). Each surfel is bounded by the box of its
  * support disk rho <= rho_c, rho_c = min(3, sqrt(2 ln(o / alpha_min))),
  * where rho^2 = u^2 + v^2 of Eq. 7; surfels with o < alpha_min never hit.
- * The library copies the surfels into Morton order and builds a binary LBVH
- * (Morton codes, radix sort, Karras hierarchy, bottom-up box refit) on the
- * device, enqueued on `stream`.
+ * The library copies the surfels into Morton order and builds the BVH on the
+ * device, enqueued on `stream`: Morton codes, radix sort, a binary hierarchy
+ * by locally-ordered clustering of the sorted leaf boxes (the Karras radix
+ * tree instead when clustering would give a tree more than 60 levels high),
+ * and its collapse into a 4-wide hierarchy for traversal.
  *   surfels   : device arrays, read during the call's stream work only.
  *   alpha_min : the smallest alpha cutoff later traces may use (> 0).
  *   out       : receives the new scene handle (caller owns it; free it with

@@ -1,6 +1,7 @@
 // Scene construction: surfel packing and support boxes (K1), Morton codes (K2),
-// stable LSD radix sort (K3), Karras hierarchy emission (K4) and bottom-up box
-// refit (K5). IRGS bounds each 2D Gaussian by a proxy enclosing the region
+// stable LSD radix sort (K3), the binary hierarchy by locally-ordered
+// clustering over the sorted leaves (K4; the Karras hierarchy as fallback),
+// bottom-up box refit (K5) and the 4-wide collapse (K6). IRGS bounds each 2D Gaussian by a proxy enclosing the region
 // where its response reaches alpha_min (Sec. 3.2, Eq. 5) and builds a BVH over
 // the proxies; here the proxy is the axis-aligned box of the support disk and
 // the BVH is a linear BVH built entirely on the device.
@@ -319,10 +320,12 @@ __device__ __forceinline__ int kdelta(const uint32_t* __restrict__ k, int64_t n,
     return __clz(a ^ b);
 }
 
+// With `gate` set it runs only if *gate != 0 (the clustering build's fallback).
 __global__ void k_karras(const uint32_t* __restrict__ keys, int64_t n, Node* __restrict__ nodes,
-                         int32_t* __restrict__ leaf_parent, int32_t* __restrict__ node_parent) {
+                         int32_t* __restrict__ leaf_parent, int32_t* __restrict__ node_parent,
+                         const uint32_t* __restrict__ gate) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
+    if (i >= n - 1 || (gate != nullptr && *gate == 0u)) return;
     int d = (kdelta(keys, n, i, i + 1) - kdelta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
     int dmin = kdelta(keys, n, i, i - d);
     int64_t lmax = 2;
@@ -362,9 +365,10 @@ __device__ __forceinline__ void child_box(const Node* nodes, const float* leaf_b
 }
 
 __global__ void k_refit(int64_t n, const float* __restrict__ leaf_box, const int32_t* __restrict__ leaf_parent,
-                        const int32_t* __restrict__ node_parent, Node* nodes, uint32_t* flags, uint32_t* status) {
+                        const int32_t* __restrict__ node_parent, Node* nodes, uint32_t* flags, uint32_t* status,
+                        const uint32_t* __restrict__ gate) {
     int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (m >= n) return;
+    if (m >= n || (gate != nullptr && *gate == 0u)) return;
     int32_t p = leaf_parent[m];
     // a valid hierarchy is at most 62 levels deep (30 key bits + 32 index bits)
     for (int level = 0; p >= 0; ++level) {
@@ -399,6 +403,376 @@ __global__ void k_tiny_root(int64_t n, const float* __restrict__ leaf_box, Node*
     nodes[0].b = make_float4(b[4], b[5], 0.f, 0.f);
     nodes[0].c = make_float4(0.f, 0.f, 0.f, 0.f);
     nodes[0].d = make_int4(n == 1 ? ~0 : kNoChild, kNoChild, 0, 0);
+}
+
+// ---------------------------------------------------------------------------
+// K4 (default): locally-ordered agglomerative clustering over the sorted
+// leaves (PLOC, Meister and Bittner 2018). In each round every cluster looks
+// at the kPlocRadius clusters on either side in Morton order and picks the
+// one whose union box has the smallest surface area; mutually chosen pairs
+// merge into a new internal node. Equal areas are ordered by (distance in
+// the order, parity of the lower index, lower index): a strict order on
+// pairs, so the best pair of a round is always mutual (every round merges)
+// and runs of equal boxes pair up as (0,1), (2,3), ... Node ids follow
+// (round, position), so the tree is the same on every run; the root is made
+// last and gets id 0. A cluster is (id, lo, hi) with its subtree height in
+// lo.w. The rounds run over all clusters until at most kPlocFinishCap are
+// left; one block then merges the rest in shared memory. A tree higher than
+// kPlocMaxHeight (possible only for contrived inputs) is replaced by the
+// Karras hierarchy, whose depth the 4-wide collapse and the refit assume.
+//
+// Working memory: the build's user-order buffers, dead after the gather:
+// cluster boxes in rec_user (4 x n float4: lo and hi, two copies), cluster ids
+// in keys_tmp / vals_tmp, per-tile kept lists in box_user (n int2), and the
+// round counters and tile counts in hist.
+constexpr int kPlocRadius = 16;
+constexpr int kPlocBlock = 1024;
+constexpr int kPlocFinishCap = kPlocBlock;
+constexpr int kPlocMaxRounds = 64;
+constexpr int kPlocMaxHeight = 60;
+// state words: cluster count before each round, then nodes made before each
+// round, then the fallback flag
+constexpr int kPlocMade = kPlocMaxRounds + 1;
+constexpr int kPlocFallback = 2 * (kPlocMaxRounds + 1);
+constexpr int kPlocStateWords = kPlocFallback + 1;
+constexpr int kPlocTileWords = 136;   // tile counts start here in hist
+
+__device__ __forceinline__ float union_area(const float4& alo, const float4& ahi, const float4& blo,
+                                            const float4& bhi) {
+    const float dx = fmaxf(ahi.x, bhi.x) - fminf(alo.x, blo.x);
+    const float dy = fmaxf(ahi.y, bhi.y) - fminf(alo.y, blo.y);
+    const float dz = fmaxf(ahi.z, bhi.z) - fminf(alo.z, blo.z);
+    const float a = dx * dy + dy * dz + dz * dx;
+    return isnan(a) ? INFINITY : a;
+}
+
+// Nearest neighbour of cluster i among [i - R, i + R] of [0, count); boxes
+// of cluster g at s_lo / s_hi[g - base].
+__device__ __forceinline__ int64_t ploc_nearest(int64_t i, int64_t count, const float4* s_lo, const float4* s_hi,
+                                                int64_t base) {
+    const float4 lo = s_lo[i - base], hi = s_hi[i - base];
+    float bc = INFINITY;
+    int bd = 0;
+    int64_t bm = 0, bj = -1;
+    for (int o = -kPlocRadius; o <= kPlocRadius; ++o) {
+        const int64_t j = i + o;
+        if (o == 0 || j < 0 || j >= count) continue;
+        const float c = union_area(lo, hi, s_lo[j - base], s_hi[j - base]);
+        const int d = o < 0 ? -o : o;
+        const int64_t m = o < 0 ? j : i;
+        bool better = bj < 0 || c < bc;
+        if (bj >= 0 && c == bc) {
+            if (d != bd) better = d < bd;
+            else if ((m & 1) != (bm & 1)) better = (m & 1) < (bm & 1);
+            else better = m < bm;
+        }
+        if (better) { bc = c; bd = d; bm = m; bj = j; }
+    }
+    return bj;
+}
+
+// Exclusive scan of one value per thread over the block (blockDim.x a
+// multiple of 32); s_warp holds 33 words. Returns the prefix, *total the sum.
+__device__ __forceinline__ uint32_t block_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = lane < nw ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, off);
+            if (lane >= off) wi += y;
+        }
+        if (lane < nw) s_warp[lane] = wi - w;
+        if (lane == nw - 1) s_warp[32] = wi;
+    }
+    __syncthreads();
+    const uint32_t r = s_warp[warp] + inc - v;
+    *total = s_warp[32];
+    __syncthreads();
+    return r;
+}
+
+// Internal node k with children a, b (ids as in Node::d) and their boxes;
+// returns the merged cluster's box (height in lo.w).
+__device__ __forceinline__ void ploc_node(int32_t k, int32_t a, int32_t b, const float4& alo, const float4& ahi,
+                                          const float4& blo, const float4& bhi, Node* nodes, int32_t* leaf_parent,
+                                          int32_t* node_parent, float4& lo, float4& hi) {
+    nodes[k].a = make_float4(alo.x, alo.y, alo.z, ahi.x);
+    nodes[k].b = make_float4(ahi.y, ahi.z, blo.x, blo.y);
+    nodes[k].c = make_float4(blo.z, bhi.x, bhi.y, bhi.z);
+    nodes[k].d = make_int4(a, b, 0, 0);
+    if (a < 0) leaf_parent[~a] = k; else node_parent[a] = k;
+    if (b < 0) leaf_parent[~b] = k; else node_parent[b] = k;
+    lo = make_float4(fminf(alo.x, blo.x), fminf(alo.y, blo.y), fminf(alo.z, blo.z), fmaxf(alo.w, blo.w) + 1.f);
+    hi = make_float4(fmaxf(ahi.x, bhi.x), fmaxf(ahi.y, bhi.y), fmaxf(ahi.z, bhi.z), 0.f);
+}
+
+__global__ void k_ploc_init(int64_t n, const float* __restrict__ leaf_box, int32_t* __restrict__ cid,
+                            float4* __restrict__ clo, float4* __restrict__ chi, uint32_t* __restrict__ state,
+                            int32_t* __restrict__ node_parent) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < kPlocStateWords) state[i] = i == 0 ? (uint32_t)n : 0u;
+    if (i == 0) node_parent[0] = -1;
+    if (i >= n) return;
+    const float* b = leaf_box + 6 * i;
+    cid[i] = ~(int32_t)i;
+    clo[i] = make_float4(b[0], b[1], b[2], 0.f);
+    chi[i] = make_float4(b[3], b[4], b[5], 0.f);
+}
+
+// One round, block b: nearest neighbours of its clusters (and of R clusters
+// on either side, whose choices decide mutuality), then the block's kept
+// clusters in order as (source index, partner or -1) in kept[b * block ...],
+// their number and the number of merges in tile_cnt[2b], [2b + 1].
+__global__ void __launch_bounds__(kPlocBlock) k_ploc_round(int r, const uint32_t* __restrict__ state,
+                                                           const float4* __restrict__ clo,
+                                                           const float4* __restrict__ chi, int2* __restrict__ kept,
+                                                           uint32_t* __restrict__ tile_cnt) {
+    constexpr int H = 2 * kPlocRadius;
+    __shared__ float4 s_lo[kPlocBlock + 2 * H], s_hi[kPlocBlock + 2 * H];
+    __shared__ int32_t s_nn[kPlocBlock + 2 * kPlocRadius];
+    __shared__ uint32_t s_warp[33];
+    const int64_t count = state[r];
+    const int64_t b0 = (int64_t)blockIdx.x * kPlocBlock;
+    if (count <= kPlocFinishCap || b0 >= count) return;
+    const int64_t base = b0 - H;
+    for (int t = threadIdx.x; t < kPlocBlock + 2 * H; t += kPlocBlock) {
+        const int64_t g = base + t;
+        if (g >= 0 && g < count) {
+            s_lo[t] = clo[g];
+            s_hi[t] = chi[g];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < kPlocBlock + 2 * kPlocRadius; t += kPlocBlock) {
+        const int64_t g = b0 - kPlocRadius + t;
+        s_nn[t] = (g >= 0 && g < count) ? (int32_t)ploc_nearest(g, count, s_lo, s_hi, base) : -1;
+    }
+    __syncthreads();
+    const int64_t i = b0 + threadIdx.x;
+    uint32_t keep = 0u, maker = 0u;
+    int32_t j = -1;
+    if (i < count) {
+        const int32_t c = s_nn[threadIdx.x + kPlocRadius];
+        const bool mutual = c >= 0 && s_nn[c - (b0 - kPlocRadius)] == (int32_t)i;
+        keep = (mutual && c < i) ? 0u : 1u;
+        maker = (mutual && c > i) ? 1u : 0u;
+        j = maker ? c : -1;
+    }
+    uint32_t tot;
+    const uint32_t pre = block_scan(keep | (maker << 16), s_warp, &tot);
+    if (keep) kept[b0 + (pre & 0xffffu)] = make_int2((int32_t)i, j);
+    if (threadIdx.x == 0) {
+        tile_cnt[2 * blockIdx.x] = tot & 0xffffu;
+        tile_cnt[2 * blockIdx.x + 1] = tot >> 16;
+    }
+}
+
+// Compaction of round r into the other cluster buffer; merges become nodes
+// numbered by (nodes made before the round + merges before them).
+__global__ void __launch_bounds__(kPlocBlock) k_ploc_compact(
+    int r, int64_t n, uint32_t* __restrict__ state, const uint32_t* __restrict__ tile_cnt,
+    const int2* __restrict__ kept, const int32_t* __restrict__ cid, const float4* __restrict__ clo,
+    const float4* __restrict__ chi, int32_t* __restrict__ cid2, float4* __restrict__ clo2, float4* __restrict__ chi2,
+    Node* __restrict__ nodes, int32_t* __restrict__ leaf_parent, int32_t* __restrict__ node_parent,
+    uint32_t* status) {
+    __shared__ uint32_t s_warp[33];
+    __shared__ uint32_t s_red[2][32];
+    const int64_t count = state[r];
+    const uint32_t made = state[kPlocMade + r];
+    if (count <= kPlocFinishCap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            state[r + 1] = (uint32_t)count;
+            state[kPlocMade + r + 1] = made;
+        }
+        return;
+    }
+    const int64_t b0 = (int64_t)blockIdx.x * kPlocBlock;
+    if (b0 >= count) return;
+    // kept clusters and merges of the tiles before this one
+    uint32_t ko = 0u, mo = 0u;
+    for (int64_t t = threadIdx.x; t < blockIdx.x; t += blockDim.x) {
+        ko += tile_cnt[2 * t];
+        mo += tile_cnt[2 * t + 1];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        ko += __shfl_xor_sync(0xffffffffu, ko, off);
+        mo += __shfl_xor_sync(0xffffffffu, mo, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_red[0][warp] = ko;
+        s_red[1][warp] = mo;
+    }
+    __syncthreads();
+    ko = 0u;
+    mo = 0u;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        ko += s_red[0][w];
+        mo += s_red[1][w];
+    }
+    const uint32_t nk = tile_cnt[2 * blockIdx.x];
+    const int t = threadIdx.x;
+    const int2 e = (uint32_t)t < nk ? kept[b0 + t] : make_int2(-1, -1);
+    uint32_t tot;
+    const uint32_t rank = block_scan((uint32_t)t < nk && e.y >= 0 ? 1u : 0u, s_warp, &tot);
+    if ((uint32_t)t < nk) {
+        const int64_t dst = (int64_t)ko + t;
+        if (e.y >= 0) {
+            const int64_t idx = (int64_t)made + mo + rank;
+            if (idx > n - 2) {
+                atomicOr(status, kErrBadTree);
+            } else {
+                const int32_t k = (int32_t)(n - 2 - idx);
+                float4 lo, hi;
+                ploc_node(k, cid[e.x], cid[e.y], clo[e.x], chi[e.x], clo[e.y], chi[e.y], nodes, leaf_parent,
+                          node_parent, lo, hi);
+                cid2[dst] = k;
+                clo2[dst] = lo;
+                chi2[dst] = hi;
+            }
+        } else {
+            cid2[dst] = cid[e.x];
+            clo2[dst] = clo[e.x];
+            chi2[dst] = chi[e.x];
+        }
+    }
+    if ((int64_t)(b0 + kPlocBlock) >= count && threadIdx.x == 0) {
+        state[r + 1] = ko + nk;
+        state[kPlocMade + r + 1] = made + mo + tot;
+    }
+}
+
+// One block: the clusters left after the rounds (pairs of neighbours first
+// while more than kPlocFinishCap remain, which only contrived inputs leave),
+// then rounds in shared memory down to the root; a root higher than
+// kPlocMaxHeight raises the fallback flag.
+__global__ void __launch_bounds__(kPlocBlock) k_ploc_finish(int rounds, int64_t n, uint32_t* __restrict__ state,
+                                                            int32_t* cid0, float4* clo0, float4* chi0, int32_t* cid1,
+                                                            float4* clo1, float4* chi1, Node* __restrict__ nodes,
+                                                            int32_t* __restrict__ leaf_parent,
+                                                            int32_t* __restrict__ node_parent, uint32_t* status) {
+    __shared__ float4 s_lo[kPlocFinishCap], s_hi[kPlocFinishCap];
+    __shared__ int32_t s_id[kPlocFinishCap], s_nn[kPlocFinishCap];
+    __shared__ uint32_t s_warp[33];
+    // the rounds that ran are a prefix; after e of them the clusters are in buffer e & 1
+    int e = 0;
+    while (e < rounds && state[e] > (uint32_t)kPlocFinishCap) ++e;
+    int64_t c = state[e];
+    int64_t made = state[kPlocMade + e];
+    int src = e & 1;
+    for (int level = 0; c > kPlocFinishCap && level < 64; ++level) {
+        const int32_t* sid = src ? cid1 : cid0;
+        const float4* slo = src ? clo1 : clo0;
+        const float4* shi = src ? chi1 : chi0;
+        int32_t* did = src ? cid0 : cid1;
+        float4* dlo = src ? clo0 : clo1;
+        float4* dhi = src ? chi0 : chi1;
+        const int64_t half = c / 2;
+        for (int64_t t = threadIdx.x; t < (c + 1) / 2; t += blockDim.x) {
+            if (t < half) {
+                const int64_t idx = made + t;
+                if (idx > n - 2) {
+                    atomicOr(status, kErrBadTree);
+                    continue;
+                }
+                const int32_t k = (int32_t)(n - 2 - idx);
+                float4 lo, hi;
+                ploc_node(k, sid[2 * t], sid[2 * t + 1], slo[2 * t], shi[2 * t], slo[2 * t + 1], shi[2 * t + 1],
+                          nodes, leaf_parent, node_parent, lo, hi);
+                did[t] = k;
+                dlo[t] = lo;
+                dhi[t] = hi;
+            } else {
+                did[t] = sid[c - 1];
+                dlo[t] = slo[c - 1];
+                dhi[t] = shi[c - 1];
+            }
+        }
+        made += half;
+        c = (c + 1) / 2;
+        src ^= 1;
+        __syncthreads();
+    }
+    if (c > kPlocFinishCap) {   // cannot happen: 64 halvings
+        if (threadIdx.x == 0) atomicOr(status, kErrBadTree);
+        return;
+    }
+    {
+        const int32_t* sid = src ? cid1 : cid0;
+        const float4* slo = src ? clo1 : clo0;
+        const float4* shi = src ? chi1 : chi0;
+        for (int t = threadIdx.x; t < c; t += blockDim.x) {
+            s_id[t] = sid[t];
+            s_lo[t] = slo[t];
+            s_hi[t] = shi[t];
+        }
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    for (int round = 0; c > 1 && round < kPlocFinishCap; ++round) {
+        const int32_t nn = t < c ? (int32_t)ploc_nearest(t, c, s_lo, s_hi, 0) : -1;
+        s_nn[t] = nn;
+        __syncthreads();
+        bool keep = false, maker = false;
+        int32_t id = 0;
+        float4 lo = make_float4(0.f, 0.f, 0.f, 0.f), hi = lo, plo = lo, phi = lo;
+        int32_t pid = 0;
+        if (t < c) {
+            const bool mutual = nn >= 0 && s_nn[nn] == t;
+            keep = !(mutual && nn < t);
+            maker = mutual && nn > t;
+            id = s_id[t];
+            lo = s_lo[t];
+            hi = s_hi[t];
+            if (maker) {
+                pid = s_id[nn];
+                plo = s_lo[nn];
+                phi = s_hi[nn];
+            }
+        }
+        uint32_t tot;
+        const uint32_t pre = block_scan((keep ? 1u : 0u) | (maker ? 0x10000u : 0u), s_warp, &tot);
+        if (maker) {
+            const int64_t idx = made + (pre >> 16);
+            if (idx > n - 2) {
+                atomicOr(status, kErrBadTree);
+            } else {
+                const int32_t k = (int32_t)(n - 2 - idx);
+                float4 mlo, mhi;
+                ploc_node(k, id, pid, lo, hi, plo, phi, nodes, leaf_parent, node_parent, mlo, mhi);
+                id = k;
+                lo = mlo;
+                hi = mhi;
+            }
+        }
+        if (keep) {
+            s_id[pre & 0xffffu] = id;
+            s_lo[pre & 0xffffu] = lo;
+            s_hi[pre & 0xffffu] = hi;
+        }
+        made += tot >> 16;
+        c = tot & 0xffffu;
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (c != 1 || made != n - 1 || s_id[0] != 0) {
+            atomicOr(status, kErrBadTree);
+            state[kPlocFallback] = 1u;
+        } else if (s_lo[0].w > (float)kPlocMaxHeight) {
+            state[kPlocFallback] = 1u;
+        }
+    }
 }
 
 __device__ __forceinline__ void node_child(const Node& nd, int s, int32_t& c, float b[6]) {
@@ -535,6 +909,44 @@ void free_scene(irgs_scene sc) {
     delete sc;
 }
 
+// Rounds of the clustering build for n leaves: about four per halving of the
+// cluster count down to kPlocFinishCap, plus margin (rounds past that point
+// return at once).
+static int ploc_rounds(int64_t n) {
+    int r = 8;
+    for (int64_t c = n; c > kPlocFinishCap; c = (c + 1) / 2) r += 4;
+    return r < kPlocMaxRounds ? r : kPlocMaxRounds;
+}
+
+// Enqueue the clustering build of the binary hierarchy (n > 1) over the
+// sorted leaf boxes; returns the device word that is nonzero when the
+// Karras hierarchy has to replace it.
+static const uint32_t* enqueue_ploc(irgs_scene sc, cudaStream_t st) {
+    const int64_t n = sc->n;
+    int32_t* cid[2] = {reinterpret_cast<int32_t*>(sc->keys_tmp), sc->vals_tmp};
+    float4* lo[2] = {sc->rec_user, sc->rec_user + 2 * n};
+    float4* hi[2] = {sc->rec_user + n, sc->rec_user + 3 * n};
+    int2* kept = reinterpret_cast<int2*>(sc->box_user);
+    uint32_t* state = sc->hist;
+    uint32_t* tile_cnt = sc->hist + kPlocTileWords;
+    const int rounds = ploc_rounds(n);
+    const unsigned tiles = (unsigned)((n + kPlocBlock - 1) / kPlocBlock);
+    const int64_t init = n > kPlocStateWords ? n : kPlocStateWords;
+    k_ploc_init<<<blocks_for(init, 256), 256, 0, st>>>(n, sc->leaf_box, cid[0], lo[0], hi[0], state,
+                                                        sc->node_parent);
+    for (int r = 0; r < rounds; ++r) {
+        const int s = r & 1, d = s ^ 1;
+        k_ploc_round<<<tiles, kPlocBlock, 0, st>>>(r, state, lo[s], hi[s], kept, tile_cnt);
+        k_ploc_compact<<<tiles, kPlocBlock, 0, st>>>(r, n, state, tile_cnt, kept, cid[s], lo[s], hi[s], cid[d],
+                                                     lo[d], hi[d], sc->nodes, sc->leaf_parent, sc->node_parent,
+                                                     sc->status);
+    }
+    k_ploc_finish<<<1, kPlocBlock, 0, st>>>(rounds, n, state, cid[0], lo[0], hi[0], cid[1], lo[1], hi[1], sc->nodes,
+                                            sc->leaf_parent, sc->node_parent, sc->status);
+    count_launches(2 + 2 * rounds);
+    return state + kPlocFallback;
+}
+
 // Enqueue the greedy 4-wide collapse of the scene's binary hierarchy (n > 1).
 static void enqueue_wide(irgs_scene sc, cudaStream_t st) {
     const int64_t n = sc->n;
@@ -584,13 +996,16 @@ static irgs_status enqueue_build(irgs_scene sc, const irgs_surfels* s, cudaStrea
         if (F > 0)
             k_gather_feat<<<blocks_for(n * F, T), T, 0, st>>>(sc->perm, n, F, s->features, sc->feat);
         if (n > 1) {
-            k_karras<<<blocks_for(n - 1, T), T, 0, st>>>(sc->keys, n, sc->nodes, sc->leaf_parent, sc->node_parent);
+            const uint32_t* gate = enqueue_ploc(sc, st);
+            k_karras<<<blocks_for(n - 1, T), T, 0, st>>>(sc->keys, n, sc->nodes, sc->leaf_parent, sc->node_parent,
+                                                         gate);
             k_refit<<<blocks_for(n, T), T, 0, st>>>(n, sc->leaf_box, sc->leaf_parent, sc->node_parent, sc->nodes,
-                                                    sc->refit_flag, sc->status);
+                                                    sc->refit_flag, sc->status, gate);
         }
     }
     if (n <= 1) k_tiny_root<<<1, 1, 0, st>>>(n, sc->leaf_box, sc->nodes);
-    // boxes, morton, 4 x (hist, scan, scatter), gather = 15; + features; + karras/refit or the tiny root
+    // boxes, morton, 4 x (hist, scan, scatter), gather = 15; + features; + the fallback karras/refit (the
+    // clustering counts its own) or the tiny root
     count_launches(n == 0 ? 1 : 15 + (F > 0) + (n == 1 ? 1 : 2));
     if (sc->wide != nullptr) {
         if (n > 1) {
@@ -722,7 +1137,7 @@ irgs_status refit_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t 
             k_gather_feat<<<blocks_for(n * F, T), T, 0, st>>>(sc->perm, n, F, s->features, sc->feat);
         if (n > 1)
             k_refit<<<blocks_for(n, T), T, 0, st>>>(n, sc->leaf_box, sc->leaf_parent, sc->node_parent, sc->nodes,
-                                                    sc->refit_flag, sc->status);
+                                                    sc->refit_flag, sc->status, nullptr);
     }
     if (n <= 1) k_tiny_root<<<1, 1, 0, st>>>(n, sc->leaf_box, sc->nodes);
     if (n > 1) {

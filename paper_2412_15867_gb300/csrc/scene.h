@@ -30,7 +30,8 @@ struct irgs_scene_s {
     int2* wide_frontier = nullptr;    // [2n] (binary node, wide index) frontiers of the collapse
     uint32_t* wide_counters = nullptr;// [4] rotating frontier sizes, wide nodes allocated
 
-    // build scratch (kept for rebuilds)
+    // build scratch (kept for rebuilds); after the gather, rec_user, box_user,
+    // keys_tmp, vals_tmp and hist serve as the clustering build's working memory
     float4* rec_user = nullptr;       // [n*4]
     float* box_user = nullptr;        // [n*6]
     uint32_t* keys_tmp = nullptr;     // [n]
