@@ -51,7 +51,7 @@ FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # Captured on the 10-camera case (6.4M rays; the ~90 MB scene read is ~5% of
 # it, so the per-ray figure slightly overstates a 64M-ray launch).
 TRAFFIC = {
-    "k_trace_forward<16,10>": {"bytes_per_ray": (703.7e6 + 1011.7e6) / 6.4e6, "src_hash": "d6edaed66e81"},
+    "k_trace_forward<16,10>": {"bytes_per_ray": (690.3e6 + 1011.4e6) / 6.4e6, "src_hash": "115b63668ea7"},
 }
 
 
