@@ -140,10 +140,13 @@ __device__ __forceinline__ void backward_hit(const SceneView& S, const Ray& ray,
     }
     st.D = __fmaf_rn(w, tau, st.D);
     Sj = fmaf(gD, Df - st.D, Sj);
-    const float dA = st.T * v - (Sj - gO * Tfin) / (1.0f - a);
+    // gradients need no correctly rounded quotients: one 2-ulp reciprocal
+    // (__fdividef) per divisor; every divisor here is a normal number
+    const float dA = st.T * v - (Sj - gO * Tfin) * __fdividef(1.0f, 1.0f - a);
 
     const float2 sc = __ldg(&S.scale[m]);
     const float4 q = __ldg(&S.q_raw[m]);
+    const float isx = __fdividef(1.0f, sc.x), isy = __fdividef(1.0f, sc.y);
     GradRow<FB> gv;
     const bool clamped = hg.a_raw >= P.alpha_max;
     const float g_o = clamped ? 0.f : dA * hg.G;
@@ -152,14 +155,14 @@ __device__ __forceinline__ void backward_hit(const SceneView& S, const Ray& ray,
     const f3 tus = mk3(r1.x, r1.y, r1.z), tvs = mk3(r2.x, r2.y, r2.z), nn = mk3(r3.x, r3.y, r3.z);
     const f3 ge = add3(mul3(tus, gu), mul3(tvs, gvv));
     const float gtau = w * gD + dot3(ge, ray.d);
-    const float s_t = gtau / hg.den;
+    const float s_t = gtau * __fdividef(1.0f, hg.den);
     const f3 gmu = sub3(mul3(nn, s_t), ge);
     const f3 gn = mul3(hg.e, -s_t);
-    const f3 gtu = mul3(hg.e, gu / sc.x);
-    const f3 gtv = mul3(hg.e, gvv / sc.y);
+    const f3 gtu = mul3(hg.e, gu * isx);
+    const f3 gtv = mul3(hg.e, gvv * isy);
     // raw quaternion: derivative of the rotation columns, then of q / |q|
-    const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-    const float qw = q.x / qn, qx = q.y / qn, qy = q.z / qn, qz = q.w / qn;
+    const float iqn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    const float qw = q.x * iqn, qx = q.y * iqn, qy = q.z * iqn, qz = q.w * iqn;
     const float hw = 2.f * (qz * gtu.y - qy * gtu.z - qz * gtv.x + qx * gtv.z + qy * gn.x - qx * gn.y);
     const float hx = 2.f * (qy * gtu.y + qz * gtu.z + qy * gtv.x - 2.f * qx * gtv.y + qw * gtv.z + qz * gn.x -
                             qw * gn.y - 2.f * qx * gn.z);
@@ -170,12 +173,12 @@ __device__ __forceinline__ void backward_hit(const SceneView& S, const Ray& ray,
     const float proj = qw * hw + qx * hx + qy * hy + qz * hz;
     gv.v[0] = gmu.x; gv.v[1] = gmu.y; gv.v[2] = gmu.z;
     gv.v[3] = g_o;
-    gv.v[4] = (hw - qw * proj) / qn;
-    gv.v[5] = (hx - qx * proj) / qn;
-    gv.v[6] = (hy - qy * proj) / qn;
-    gv.v[7] = (hz - qz * proj) / qn;
-    gv.v[8] = -gu * hg.u / sc.x;
-    gv.v[9] = -gvv * hg.v / sc.y;
+    gv.v[4] = (hw - qw * proj) * iqn;
+    gv.v[5] = (hx - qx * proj) * iqn;
+    gv.v[6] = (hy - qy * proj) * iqn;
+    gv.v[7] = (hz - qz * proj) * iqn;
+    gv.v[8] = -gu * hg.u * isx;
+    gv.v[9] = -gvv * hg.v * isy;
     gv.v[10] = 0.f;
     gv.v[11] = 0.f;
 #pragma unroll
@@ -229,13 +232,31 @@ __device__ __forceinline__ void listed_backward(const SceneView& S, const Ray& r
                                                 float* __restrict__ acc_rows, float* rows) {
     BwdAcc<FB> st;
     st.init();
+    if (nh_total <= 0) return;
+    // The lookups run ahead of the hit being processed: the id of hit j + 2
+    // and the Morton slot of hit j + 1 are in flight while hit j is. An id
+    // outside [0, n) is not a list the forward wrote for this scene: the hits
+    // before it are processed, then the ray stops with an error bit.
+    int32_t u = __ldg(ids);
+    if (u < 0 || u >= S.n) {
+        atomicOr(S.status, kErrBadHitList);
+        return;
+    }
+    int32_t m_next = __ldg(&S.inv_perm[u]);
+    u = nh_total > 1 ? __ldg(ids + 1) : 0;
     for (int j = 0; j < nh_total; ++j) {
-        const int32_t u = __ldg(ids + j);
-        if (u < 0 || u >= S.n) {   // not a list the forward wrote for this scene
+        const int32_t m = m_next;
+        bool bad = false;
+        if (j + 1 < nh_total) {
+            if (u < 0 || u >= S.n) bad = true;
+            else m_next = __ldg(&S.inv_perm[u]);
+        }
+        u = j + 2 < nh_total ? __ldg(ids + j + 2) : 0;
+        backward_hit<FB>(S, ray, P, m, st, Cf, Df, Tfin, gC, gD, gO, acc_rows, rows);
+        if (bad) {
             atomicOr(S.status, kErrBadHitList);
             return;
         }
-        backward_hit<FB>(S, ray, P, __ldg(&S.inv_perm[u]), st, Cf, Df, Tfin, gC, gD, gO, acc_rows, rows);
     }
 }
 
