@@ -268,6 +268,28 @@ def run_ours(args):
     torch.cuda.synchronize()
     refit_ms = ra.elapsed_time(rb) / 5
 
+    # ---- the radix-tree hierarchy on the same surfels and rays, for comparison
+    # (rebuild and forward, two runs each after one warm-up; the timed step
+    # above uses the clustered hierarchy)
+    hier = None
+    if rank == 0:
+        rscene = irgs.Scene(*surf, alpha_min=1 / 255, hierarchy="radix")
+        irgs.trace_forward(rscene, ro, rd, p, max_hit_ids=args.saved_hits, out=out)
+        hb = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        hb[0].record(stream)
+        for _ in range(2):
+            rscene.update()
+        hb[1].record(stream)
+        for _ in range(2):
+            irgs.trace_forward(rscene, ro, rd, p, max_hit_ids=args.saved_hits, out=out)
+        hb[2].record(stream)
+        torch.cuda.synchronize()
+        if rscene.status() != 0:
+            raise RuntimeError("device error on the radix-tree scene")
+        hier = {"clustered": {"build_ms": build_ms, "fwd_ms": fwd_ms},
+                "radix": {"build_ms": hb[0].elapsed_time(hb[1]) / 2, "fwd_ms": hb[1].elapsed_time(hb[2]) / 2}}
+        rscene.close()
+
     # ---- 2D Gaussian rasterisation of the same cameras (the G-buffer pass of stage II)
     raster = None
     if not args.no_raster and rank == 0:
@@ -406,12 +428,12 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "surfels": sc.n, "rays_per_step_per_gpu": R,
                        "cameras": args.cams, "resolution": args.res, "k": 16, "feat_count": F,
                        "alpha_min": 1 / 255, "T_min": 1e-4,
-                       "step": "LBVH rebuild + forward trace (saving hit lists) + backward trace from the lists",
+                       "step": "BVH rebuild (Morton sort, clustered binary tree, 4-wide collapse) + forward trace (saving hit lists) + backward trace from the lists",
                        "saved_hits": args.saved_hits,
                        "ray_order": "8x4 pixel tiles per camera", "traversal": "warp-coherent",
                        "l2": "inputs larger than L2 (1.5 GB of rays per step)"},
             "fwd_mrays_s": R / (fwd_ms * 1e-3) / 1e6, "bwd_mrays_s": R / (bwd_ms * 1e-3) / 1e6,
-            "build_ms": build_ms, "refit_ms": refit_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+            "build_ms": build_ms, "refit_ms": refit_ms, "fwd_ms": fwd_ms, "bwd_ms": bwd_ms, "hierarchies": hier,
             "mean_hits_per_ray": float(nh.float().mean()), "max_hits_per_ray": int(nh.max()),
             "replayed_ray_frac": float((nh > args.saved_hits).float().mean()) if args.saved_hits > 0 else 1.0,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),

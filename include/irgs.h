@@ -123,6 +123,20 @@ irgs_status irgs_build_scene(const irgs_surfels* surfels, float alpha_min, void*
                              irgs_scene* out);
 
 /*
+ * irgs_build_scene with a choice of binary hierarchy (Sec. 3.2, the BVH over
+ * the bounding proxies). build_flags = 0 is irgs_build_scene: locally-ordered
+ * clustering of the sorted leaves, the radix tree only as its fallback.
+ * IRGS_BUILD_RADIX_TREE builds the Karras (2012) radix tree over the sorted
+ * Morton codes (equal codes split by index) and refits its boxes bottom-up:
+ * faster to build, slower to trace. Traces give identical results on
+ * either tree. The choice is kept for irgs_update_scene. Other bits of
+ * build_flags: IRGS_ERR_INVALID_ARG; the rest as for irgs_build_scene.
+ */
+#define IRGS_BUILD_RADIX_TREE 1u
+irgs_status irgs_build_scene_ex(const irgs_surfels* surfels, float alpha_min, uint32_t build_flags, void* stream,
+                                irgs_scene* out);
+
+/*
  * Rebuild an existing scene in place from new surfel values (same n and
  * num_features): the BVH update that a training loop runs every iteration
  * because the geometry changes (Sec. 4).

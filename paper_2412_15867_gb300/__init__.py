@@ -79,7 +79,10 @@ class Scene:
     The tensors it was built from are kept so that `trace` can route
     gradients to them; the library itself only keeps its own copies."""
 
-    def __init__(self, means, quats, scales, opacity, features=None, alpha_min: float = 1.0 / 255.0):
+    HIERARCHIES = {"clustered": 0, "radix": 1}   # IRGS_BUILD_RADIX_TREE = 1
+
+    def __init__(self, means, quats, scales, opacity, features=None, alpha_min: float = 1.0 / 255.0,
+                 hierarchy: str = "clustered"):
         self.means = _dev_f32(means, "means", 3)
         n = self.means.shape[0]
         self.quats = _dev_f32(quats, "quats", 4)
@@ -93,16 +96,19 @@ class Scene:
         for name, t in (("quats", self.quats), ("scales", self.scales), ("features", self.features)):
             if t.shape[0] != n:
                 raise ValueError(f"{name} has {t.shape[0]} rows, means has {n}")
+        if hierarchy not in self.HIERARCHIES:
+            raise ValueError(f"hierarchy must be one of {sorted(self.HIERARCHIES)}")
         self.device = self.means.device
         self.alpha_min = float(alpha_min)
+        self.hierarchy = hierarchy
         self.num_features = int(self.features.shape[1])
         self.n = int(n)
         L = _lib.lib()
         s = self._surfels()
         h = C.c_void_p()
         with torch.cuda.device(self.device):
-            _lib.check(L.irgs_build_scene(C.byref(s), self.alpha_min, _stream(self.device), C.byref(h)),
-                       "irgs_build_scene")
+            _lib.check(L.irgs_build_scene_ex(C.byref(s), self.alpha_min, self.HIERARCHIES[hierarchy],
+                                             _stream(self.device), C.byref(h)), "irgs_build_scene_ex")
         self._h = h
 
     def _surfels(self) -> _lib.Surfels:

@@ -50,6 +50,7 @@ _SIGS = {
                                P, P, P, P]),
     "irgs_kernel_launches": (C.c_uint64, []),
     "irgs_build_scene": (C.c_int, [C.POINTER(Surfels), C.c_float, P, C.POINTER(P)]),
+    "irgs_build_scene_ex": (C.c_int, [C.POINTER(Surfels), C.c_float, C.c_uint32, P, C.POINTER(P)]),
     "irgs_update_scene": (C.c_int, [P, C.POINTER(Surfels), P]),
     "irgs_destroy_scene": (C.c_int, [P]),
     "irgs_scene_info": (C.c_int, [P, P, P, P, P]),

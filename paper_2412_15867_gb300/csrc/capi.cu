@@ -89,7 +89,13 @@ int32_t irgs_abi_version(void) { return IRGS_ABI_VERSION; }
 uint64_t irgs_kernel_launches(void) { return irgs::g_launches.load(std::memory_order_relaxed); }
 
 irgs_status irgs_build_scene(const irgs_surfels* s, float alpha_min, void* stream, irgs_scene* out) {
+    return irgs_build_scene_ex(s, alpha_min, 0u, stream, out);
+}
+
+irgs_status irgs_build_scene_ex(const irgs_surfels* s, float alpha_min, uint32_t build_flags, void* stream,
+                                irgs_scene* out) {
     if (s == nullptr || out == nullptr) return IRGS_ERR_INVALID_ARG;
+    if ((build_flags & ~IRGS_BUILD_RADIX_TREE) != 0u) return IRGS_ERR_INVALID_ARG;
     if (s->n < 0 || s->n >= INT32_MAX) return IRGS_ERR_INVALID_ARG;
     if (s->num_features < 0 || s->num_features > 64) return IRGS_ERR_INVALID_ARG;
     if (!finite(alpha_min) || !(alpha_min > 0.f) || !(alpha_min < 1.f)) return IRGS_ERR_INVALID_ARG;
@@ -104,7 +110,7 @@ irgs_status irgs_build_scene(const irgs_surfels* s, float alpha_min, void* strea
         }
         if (cudaSetDevice(at.device) != cudaSuccess) return IRGS_ERR_CUDA;
     }
-    return irgs::build_scene_impl(s, alpha_min, static_cast<cudaStream_t>(stream), out);
+    return irgs::build_scene_impl(s, alpha_min, build_flags, static_cast<cudaStream_t>(stream), out);
 }
 
 irgs_status irgs_update_scene(irgs_scene sc, const irgs_surfels* s, void* stream) {

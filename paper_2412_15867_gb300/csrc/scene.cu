@@ -996,7 +996,8 @@ static irgs_status enqueue_build(irgs_scene sc, const irgs_surfels* s, cudaStrea
         if (F > 0)
             k_gather_feat<<<blocks_for(n * F, T), T, 0, st>>>(sc->perm, n, F, s->features, sc->feat);
         if (n > 1) {
-            const uint32_t* gate = enqueue_ploc(sc, st);
+            // the radix tree runs when asked for, else only if the clustering raises its fallback flag
+            const uint32_t* gate = (sc->build_flags & IRGS_BUILD_RADIX_TREE) ? nullptr : enqueue_ploc(sc, st);
             k_karras<<<blocks_for(n - 1, T), T, 0, st>>>(sc->keys, n, sc->nodes, sc->leaf_parent, sc->node_parent,
                                                          gate);
             k_refit<<<blocks_for(n, T), T, 0, st>>>(n, sc->leaf_box, sc->leaf_parent, sc->node_parent, sc->nodes,
@@ -1051,7 +1052,8 @@ cudaError_t scan_exclusive(uint32_t* a, int64_t m, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_t st, irgs_scene* out) {
+irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, uint32_t build_flags, cudaStream_t st,
+                             irgs_scene* out) {
     const int64_t n = s->n;
     const int32_t F = s->num_features;
     irgs_scene sc = new (std::nothrow) irgs_scene_s();
@@ -1060,6 +1062,7 @@ irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_
     sc->n = n;
     sc->F = F;
     sc->alpha_min = alpha_min;
+    sc->build_flags = build_flags;
     const int64_t nn = n > 1 ? n - 1 : 1;
     const int64_t tiles = (n + kTile - 1) / kTile;
     int64_t& B = sc->bytes;

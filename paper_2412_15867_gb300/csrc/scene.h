@@ -12,6 +12,7 @@ struct irgs_scene_s {
     int64_t n = 0;
     int32_t F = 0;
     float alpha_min = 0.f;
+    uint32_t build_flags = 0;         // IRGS_BUILD_* of the hierarchy
     int64_t bytes = 0;
 
     // persistent scene data (Morton order)
@@ -90,7 +91,8 @@ irgs_status launch_relight(const SceneView& sv, const uint32_t* bounds, irgs_env
                            float* ind, cudaStream_t st);
 
 // scene.cu
-irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, cudaStream_t st, irgs_scene* out);
+irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, uint32_t build_flags, cudaStream_t st,
+                             irgs_scene* out);
 irgs_status update_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t st);
 irgs_status refit_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t st);
 irgs_status build_lbvh_noalloc_impl(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,

@@ -38,6 +38,7 @@ def test_null_arguments_rejected_without_gpu(L):
     assert L.irgs_build_scene(C.byref(s), 1 / 255, None, C.byref(h)) == 1
     s = _lib.Surfels(None, None, None, None, None, 0, 0)
     assert L.irgs_build_scene(C.byref(s), 0.0, None, C.byref(h)) == 1     # alpha_min must be > 0
+    assert L.irgs_build_scene_ex(C.byref(s), 1 / 255, 2, None, C.byref(h)) == 1   # unknown build flag
     p = _lib.TraceParamsC(16, 1 / 255, 0.99, 1e-4, 0.0, math.inf, 0, 3, 0)
     assert L.irgs_trace_forward(None, None, None, 0, C.byref(p), None, None, None, None, None, 0, None) == 1
     assert L.irgs_trace_backward(None, None, None, 0, C.byref(p), None, None, None, None, None, 0,

@@ -5,8 +5,10 @@ leaves, with the Karras radix tree as the fallback for trees too high.
 Checked on the exported hierarchy: every leaf and node reached once, every
 node box exactly the union of its children's boxes, the same tree from two
 builds, a lower total node surface area than the radix tree over the same
-sorted keys, balanced pairing of identical surfels, and the fallback on a
-contrived chain (whose traces must still match the oracle)."""
+sorted keys, balanced pairing of identical surfels, the fallback on a
+contrived chain (whose traces must still match the oracle), and the
+radix-tree build option: the Karras split of every node's range, and
+traces identical to those on the clustered tree."""
 import math
 
 import numpy as np
@@ -136,3 +138,58 @@ def test_a_chain_too_high_falls_back_to_the_radix_tree():
         assert np.all(np.abs(a - ref[k].reshape(256, -1))[ok] <= 1e-4), k
     assert np.array_equal(out["n_hits"].cpu().numpy()[ok], ref["n_hits"][ok])
     assert int(out["n_hits"].sum()) > 0
+
+
+def leaf_ranges(nodes, n):
+    """(first, last) leaf index under every internal node of the exported tree."""
+    ch = nodes[:, 12:14].view(np.int32)
+    first = np.zeros(max(n - 1, 1), np.int64)
+    last = np.zeros(max(n - 1, 1), np.int64)
+    order, stack = [], [0]
+    while stack:
+        i = stack.pop()
+        order.append(i)
+        stack += [c for c in ch[i] if c >= 0]
+    for i in reversed(order):
+        r = [(~c, ~c) if c < 0 else (first[c], last[c]) for c in ch[i]]
+        first[i], last[i] = r[0][0], r[1][1]
+        assert r[0][1] + 1 == r[1][0]          # children cover adjacent ranges, left first
+    return ch, first, last
+
+
+def test_radix_tree_option_builds_the_karras_tree_and_traces_identically():
+    sc = synth.object_scene(n=20_000, seed=511)
+    sc = sc.subset(np.concatenate([np.arange(sc.n), np.arange(300)]))     # equal Morton codes occur
+    arrays = [dev(a) for a in sc.arrays()]
+    R = irgs.Scene(*arrays, hierarchy="radix")
+    Cl = irgs.Scene(*arrays)
+    pr, kr, nr, br = R.export()
+    pc, kc, nc, bc = Cl.export()
+    assert np.array_equal(pr, pc) and np.array_equal(kr, kc) and np.array_equal(br, bc)
+    n = sc.n
+    height, _, tight = walk(nr, br)
+    assert tight and height <= 62
+    # every node splits its range where the radix tree does: at the highest
+    # bit in which the extended keys (Morton code, then index) of its ends differ
+    ch, first, last = leaf_ranges(nr, n)
+    k = kr.astype(np.int64) * (1 << 32) + np.arange(n)
+    for i in range(n - 1):
+        f, l = first[i], last[i]
+        b = int(k[f] ^ k[l]).bit_length() - 1
+        split = f + int(np.count_nonzero(((k[f:l + 1] >> b) & 1) == 0)) - 1
+        c0 = ch[i, 0]
+        assert (~c0 if c0 < 0 else last[c0]) == split, i
+    ro, rd = synth.camera_batch_rays(synth.hemisphere_cameras(2, seed=512), 64, 48, tile=(8, 4))
+    for flags in (0, irgs.FLAG_PER_THREAD):
+        p = irgs.TraceParams(k=16, feat_count=10, flags=flags)
+        a = irgs.trace_forward(R, dev(ro), dev(rd), p, max_hit_ids=64)
+        b = irgs.trace_forward(Cl, dev(ro), dev(rd), p, max_hit_ids=64)
+        for key in ("feat", "depth", "opacity", "n_hits", "hit_ids"):
+            assert torch.equal(a[key], b[key]), (flags, key)
+    # the choice survives an in-place rebuild
+    R.update(means=arrays[0] + 0.01)
+    _, _, nr2, br2 = R.export()
+    _, first2, last2 = leaf_ranges(nr2, n)
+    assert walk(nr2, br2)[2]
+    with pytest.raises(ValueError):
+        irgs.Scene(*arrays, hierarchy="octree")
