@@ -288,9 +288,20 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
         bool h[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) h[k] = c[k] != kNoChild && tn[k] <= tf[k] && tf[k] >= lo_c && tn[k] <= hi_c;
+        {
+            // lanes of a warp walk different nodes here: each tests its own
+            // needed leaves in one loop, so lanes run their i-th leaf test
+            // together whatever slot it sits in (slot order kept per lane)
+            unsigned mask = 0u;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (h[k] && c[k] < 0) leaf_insert<KB, STATS>(S, ray, P, ~c[k], last_key, last_m, kb, t_hi, ts);
+            for (int k = 0; k < 4; ++k) mask |= (h[k] && c[k] < 0) ? (1u << k) : 0u;
+            while (mask != 0u) {
+                const int k = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                const int ck = k == 0 ? c[0] : k == 1 ? c[1] : k == 2 ? c[2] : c[3];
+                leaf_insert<KB, STATS>(S, ray, P, ~ck, last_key, last_m, kb, t_hi, ts);
+            }
+        }
         hi_c = t_hi + tslack(t_hi);
         // internal children still in reach: descend into the nearest, push the rest far first
         float t[4];
