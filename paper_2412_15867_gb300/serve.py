@@ -66,7 +66,7 @@ def _sigs():
 
 
 def make_camera(eye, width: int, height: int, target=(0.0, 0.0, 0.0), fov_deg: float = 60.0,
-                tile=(8, 4)) -> Camera:
+                tile=(4, 8)) -> Camera:
     """Pinhole look-at camera (z up; x up when looking along z)."""
     eye = np.asarray(eye, np.float64)
     fwd = np.asarray(target, np.float64) - eye
