@@ -31,10 +31,11 @@ def env():
     return dev(synth.env_map(seed=403, height=64, width=128))
 
 
-def test_camera_rays_match_the_pinhole_model():
-    cam = serve.make_camera((3.0, -1.0, 2.0), 64, 32, fov_deg=50.0)
+@pytest.mark.parametrize("tile", [(4, 8), (8, 4), (1, 1)])
+def test_camera_rays_match_the_pinhole_model(tile):
+    cam = serve.make_camera((3.0, -1.0, 2.0), 64, 32, fov_deg=50.0, tile=tile)
     o, d = serve.camera_rays(cam)
-    ro, rd = synth.look_at_rays((3.0, -1.0, 2.0), (0, 0, 0), 64, 32, fov_deg=50.0, tile=(8, 4))
+    ro, rd = synth.look_at_rays((3.0, -1.0, 2.0), (0, 0, 0), 64, 32, fov_deg=50.0, tile=tile)
     np.testing.assert_allclose(d.cpu().numpy(), rd, atol=3e-7)
     np.testing.assert_allclose(o.cpu().numpy(), ro, atol=0)
 
