@@ -12,7 +12,7 @@ forward and backward per second (Mrays/s), inputs resident on the device.
 The Monte Carlo rendering-equation configuration (1M surfels, 640k points x
 64 samples = 41M secondary rays) is timed in the same run under "mc".
 
-`--impl reference` times the FP64 CPU oracle (the reference of this build)
+`--impl reference` times the FP64 CPU oracle (there is no reference implementation to run)
 on bounded samples of the same workload, on the host cores.
 
 Run with torchrun for N > 1: each rank traces its own 100-camera batch
