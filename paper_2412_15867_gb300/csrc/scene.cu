@@ -1052,6 +1052,15 @@ cudaError_t scan_exclusive(uint32_t* a, int64_t m, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+int64_t scan_long_words(int64_t m) { return (m + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t scan_exclusive_long(uint32_t* a, int64_t m, uint32_t* sums, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    scan_long(a, m, sums, st);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
 irgs_status build_scene_impl(const irgs_surfels* s, float alpha_min, uint32_t build_flags, cudaStream_t st,
                              irgs_scene* out) {
     const int64_t n = s->n;

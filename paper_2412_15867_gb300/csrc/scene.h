@@ -106,6 +106,10 @@ cudaError_t sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp, int32_
                        int64_t n, cudaStream_t st, int key_bits = 32);
 // In-place exclusive prefix sum of m words (one block; for up to a few million).
 cudaError_t scan_exclusive(uint32_t* a, int64_t m, cudaStream_t st);
+// In-place exclusive prefix sum of m words by tiles (any m); sums holds
+// scan_long_words(m) words of scratch.
+int64_t scan_long_words(int64_t m);
+cudaError_t scan_exclusive_long(uint32_t* a, int64_t m, uint32_t* sums, cudaStream_t st);
 
 // trace_fwd.cu
 irgs_status launch_trace_forward(const SceneView& sv, const float* ro, const float* rd, int64_t R,

@@ -458,6 +458,40 @@ struct MarchState {
     int nh;
 };
 
+// Blend the round's buffered hits in order (Eq. 2, Eq. 8) until the
+// transmittance drops below T_min (the crossing hit included). Returns true
+// when the ray is done: terminated, or fewer than K hits were left; else
+// (last_key, last_m) move to the buffer's last entry for the next round.
+template <int K, int FB, class KB>
+__device__ __forceinline__ bool blend_round(const SceneView& S, const TraceParams& P, const KB& kb,
+                                            MarchState<K, FB>& st, int32_t* ids, int max_ids, uint64_t& last_key,
+                                            int32_t& last_m) {
+    bool done = false;
+    for (int j = 0; j < kb.cnt && !done; ++j) {
+        const float a = kb.a_at(j);
+        const int32_t m = kb.m_at(j);
+        const float w = __fmul_rn(st.T, a);
+        const float* f = S.feat + (int64_t)m * S.F + P.off;
+#pragma unroll
+        for (int c = 0; c < FB; ++c)
+            if (c < P.fc) st.C[c] = __fmaf_rn(w, __ldg(f + c), st.C[c]);
+        st.D = __fmaf_rn(w, key_depth(kb.key_at(j)), st.D);
+        st.T = __fmul_rn(st.T, __fsub_rn(1.0f, a));
+        if (ids != nullptr && st.nh < max_ids) ids[st.nh] = __float_as_int(__ldg(&S.rec[(int64_t)m * kRecF4 + 2].w));
+        st.nh++;
+        if (st.T < P.T_min) done = true;
+    }
+    if (!done) {
+        if (kb.cnt < K) {
+            done = true;
+        } else {
+            last_key = kb.tail_key;
+            last_m = kb.tail_m;
+        }
+    }
+    return done;
+}
+
 // WARP = true: all 32 lanes of the warp call this together (lanes without a
 // ray pass live = false) and traverse warp-coherently.
 template <int K, int FB, bool WARP, bool STATS = false>
@@ -483,31 +517,7 @@ __device__ __forceinline__ bool march_forward(const SceneView& S, const Ray& ray
         else
             ok &= collect_round<decltype(kb), STATS>(S, ray, P, last_key, last_m, kb, ts);
         if (done) continue;
-        for (int j = 0; j < kb.cnt && !done; ++j) {
-            {
-                const float a = kb.a_at(j);
-                const int32_t m = kb.m_at(j);
-                const float w = __fmul_rn(st.T, a);
-                const float* f = S.feat + (int64_t)m * S.F + P.off;
-#pragma unroll
-                for (int c = 0; c < FB; ++c)
-                    if (c < P.fc) st.C[c] = __fmaf_rn(w, __ldg(f + c), st.C[c]);
-                st.D = __fmaf_rn(w, key_depth(kb.key_at(j)), st.D);
-                st.T = __fmul_rn(st.T, __fsub_rn(1.0f, a));
-                if (ids != nullptr && st.nh < max_ids)
-                    ids[st.nh] = __float_as_int(__ldg(&S.rec[(int64_t)m * kRecF4 + 2].w));
-                st.nh++;
-                if (st.T < P.T_min) done = true;
-            }
-        }
-        if (!done) {
-            if (kb.cnt < K) {
-                done = true;
-            } else {
-                last_key = kb.tail_key;
-                last_m = kb.tail_m;
-            }
-        }
+        done = blend_round<K, FB>(S, P, kb, st, ids, max_ids, last_key, last_m);
     }
     return ok;
 }

@@ -247,6 +247,26 @@ def test_traversal_modes_give_identical_results():
         irgs.trace_forward(S, dev(ro), dev(rd), irgs.TraceParams(flags=4))
 
 
+def test_compacted_rounds_equal_per_ray_march():
+    """Batches of 2^20 rays or more take the compacted rounds (rays still
+    marching after round 1, 2 and 3 are regrouped into full warps; the rest
+    run to completion): every output, the hit lists included, equals the
+    per-ray march bit for bit, also for rays that need 4 rounds or more."""
+    sc = synth.object_scene(n=300_000, seed=1001)
+    ro, rd = synth.camera_batch_rays(synth.hemisphere_cameras(2, seed=17), 800, 700, tile=(4, 8))
+    assert ro.shape[0] >= 1 << 20
+    S = make_scene(irgs, sc)
+    pw = irgs.TraceParams(k=16, feat_count=10)
+    a = irgs.trace_forward(S, dev(ro), dev(rd), pw, max_hit_ids=96)
+    b = irgs.trace_forward(S, dev(ro), dev(rd), pw.with_(flags=irgs.FLAG_PER_THREAD), max_hit_ids=96)
+    torch.cuda.synchronize()
+    assert S.status() == 0
+    nh = a["n_hits"].cpu().numpy()
+    assert (nh > 48).any() and (nh > 16).mean() > 0.3     # rounds 4+ (run to completion) and the compacted rounds both occur
+    for key in a:
+        assert torch.equal(a[key], b[key]), key
+
+
 def test_trace_stats_counters_are_consistent():
     sc = synth.object_scene(n=20_000, seed=17)
     ro, rd = synth.camera_batch_rays(synth.hemisphere_cameras(1, seed=17), 64, 64, tile=(8, 4))
