@@ -51,7 +51,7 @@ FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # Captured on the 10-camera case (6.4M rays; the ~90 MB scene read is ~5% of
 # it, so the per-ray figure slightly overstates a 64M-ray launch).
 TRAFFIC = {
-    "k_trace_forward<16,10>": {"bytes_per_ray": (689.9e6 + 1012.1e6) / 6.4e6, "src_hash": "0c52ab4d7d1d"},
+    "k_trace_round<16,10,*>": {"bytes_per_ray": None, "src_hash": None},
 }
 
 
@@ -316,13 +316,15 @@ def run_ours(args):
         flops = algorithmic_flops(nh, 16, sc.n, F, backward=True, saved_hits=args.saved_hits)
         src = ["trace.cuh", "trace_bwd.cuh", "trace_bwd.cu", "common.cuh", "scene.cu"]
     else:
-        kname, kms = "k_trace_forward<16,10>", fwd_ms
+        # the forward pass: for batches of 2^20 rays or more its compacted
+        # k-buffer rounds (4 launches) and the compaction between them
+        kname, kms = "k_trace_round<16,10,*>", fwd_ms
         flops = algorithmic_flops(nh, 16, sc.n, F)
         src = ["trace.cuh", "trace_fwd.cu", "common.cuh", "scene.cu"]
     achieved = flops / (kms * 1e-3) / 1e12
     khash = _kernel_hash(src)
     tr = TRAFFIC.get(kname)
-    traffic = tr["bytes_per_ray"] * R if (tr and tr.get("src_hash") == khash) else None
+    traffic = tr["bytes_per_ray"] * R if (tr and tr.get("bytes_per_ray") and tr.get("src_hash") == khash) else None
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "flops_per_launch": flops, "launch_ms": kms,
