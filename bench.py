@@ -51,7 +51,9 @@ FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # Captured on the 10-camera case (6.4M rays; the ~90 MB scene read is ~5% of
 # it, so the per-ray figure slightly overstates a 64M-ray launch).
 TRAFFIC = {
-    "k_trace_round<16,10,*>": {"bytes_per_ray": None, "src_hash": None},
+    # the four round launches of one forward (6.4M-ray capture): read 428.9 + 919.9 + 358.2 + 87.1 MB,
+    # written 756.3 + 561.3 + 125.0 + 11.7 MB
+    "k_trace_round<16,10,*>": {"bytes_per_ray": (1794.1e6 + 1454.3e6) / 6.4e6, "src_hash": "95bbb9a8fa9d"},
 }
 
 
