@@ -139,7 +139,7 @@ __global__ void k_round_list(const uint32_t* __restrict__ pos, int64_t R, int32_
 
 // Batches at least this large take the compacted rounds.
 constexpr int64_t kRoundMinRays = int64_t(1) << 20;
-constexpr int kCompactedRounds = 3;   // rounds 1..3 compacted, the rest run to completion
+constexpr int kCompactedRounds = 3;   // regroup after rounds 1, 2 and 3; rounds 4+ run to completion
 
 template <int K, int FB>
 cudaError_t launch_rounds(const SceneView& S, const float* ro, const float* rd, int64_t R, const TraceParams& P,
