@@ -90,6 +90,83 @@ __global__ void __launch_bounds__(kWaveThreads, 6) k_wave_trace(SceneView S, Tra
     }
 }
 
+// The same traces in compacted rounds: round 1 on every ray of the order;
+// rays still marching store their state (C, D, T, hit count, next key) at
+// their sorted position and are regrouped, keeping the sorted order, for
+// rounds 2 and 3; the rest run to completion. Per ray the rounds and their
+// arithmetic are march_forward's (per lane), so the results are the same.
+enum WaveRound { kWaveFirst = 0, kWaveNext = 1, kWaveLast = 2 };
+constexpr int kWaveStateF4 = 3;   // C[3], D, T, hit count, next key (2 words), next Morton index
+
+template <int K, bool SAVE, int MODE>
+__global__ void __launch_bounds__(kWaveThreads, 6) k_wave_round(
+    SceneView S, TraceParams P, const float* __restrict__ xg, int64_t p0, int St, const float4* __restrict__ dir,
+    const int32_t* __restrict__ order, int64_t rays, float4* __restrict__ res, int32_t* __restrict__ nh,
+    int32_t* __restrict__ ids, int max_ids, const int32_t* __restrict__ list, const uint32_t* __restrict__ count,
+    float4* __restrict__ state, uint32_t* __restrict__ flags) {
+    static_assert(kWaveThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
+    const int64_t t = blockIdx.x * (int64_t)kWaveThreads + threadIdx.x;
+    const int64_t n = MODE == kWaveFirst ? rays : (int64_t)*count;
+    if (t >= n) return;
+    const int64_t j = MODE == kWaveFirst ? t : (int64_t)list[t];
+    const int64_t i = order[j];
+    const float4 d4 = dir[i];
+    if (MODE == kWaveFirst && d4.w == 0.f) {   // every sample gets an entry, so no reader sees unwritten scratch
+        res[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (SAVE) nh[i] = 0;
+        return;
+    }
+    const Ray ray = make_ray(ld3w(xg, p0 + i / St), mk3(d4.x, d4.y, d4.z));
+    MarchState<K, 3> st;
+    uint64_t last_key = depth_key(P.t_min, 0.f);
+    int32_t last_m = INT32_MAX;
+    if (MODE == kWaveFirst) {
+        st.C[0] = st.C[1] = st.C[2] = 0.f;
+        st.D = 0.f;
+        st.T = 1.f;
+        st.nh = 0;
+    } else {
+        const float4 a = state[j * kWaveStateF4], b = state[j * kWaveStateF4 + 1], c = state[j * kWaveStateF4 + 2];
+        st.C[0] = a.x; st.C[1] = a.y; st.C[2] = a.z;
+        st.D = a.w;
+        st.T = b.x;
+        st.nh = __float_as_int(b.y);
+        last_key = ((uint64_t)__float_as_uint(b.w) << 32) | (uint64_t)__float_as_uint(b.z);
+        last_m = __float_as_int(c.x);
+    }
+    int32_t* my_ids = SAVE ? ids + i * (int64_t)max_ids : nullptr;
+    KBuffer<K, trace_threads<K>()> kb;
+    kb.bind();
+    bool ok = true, done = false;
+    do {
+        ok &= collect_round(S, ray, P, last_key, last_m, kb);
+        done = blend_round<K, 3>(S, P, kb, st, my_ids, max_ids, last_key, last_m);
+    } while (MODE == kWaveLast && !done);
+    if (!ok) atomicOr(S.status, kErrStackOverflow);
+    if (done) {
+        res[i] = make_float4(st.C[0], st.C[1], st.C[2], st.T);
+        if (SAVE) {
+            nh[i] = st.nh;
+            if (st.nh < max_ids) my_ids[st.nh] = -1;
+        }
+    } else {
+        state[j * kWaveStateF4] = make_float4(st.C[0], st.C[1], st.C[2], st.D);
+        state[j * kWaveStateF4 + 1] = make_float4(st.T, __int_as_float(st.nh), __uint_as_float((uint32_t)last_key),
+                                                  __uint_as_float((uint32_t)(last_key >> 32)));
+        state[j * kWaveStateF4 + 2] = make_float4(__int_as_float(last_m), 0.f, 0.f, 0.f);
+        flags[j] = 1u;
+    }
+}
+
+// pos[0..m] = exclusive prefix of the continue flags: list[pos[j]] = j for
+// every continuing ray, *count = pos[m].
+__global__ void k_wave_list(const uint32_t* __restrict__ pos, int64_t m, int32_t* __restrict__ list,
+                            uint32_t* __restrict__ count) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j == 0) *count = pos[m];
+    if (j < m && pos[j + 1] != pos[j]) list[pos[j]] = (int32_t)j;
+}
+
 // Per-point estimate from the stored traces (warp per point).
 template <int K>
 __global__ void __launch_bounds__(kWaveThreads) k_wave_shade(SceneView S, const float* __restrict__ xg,
@@ -208,6 +285,10 @@ struct WaveScratch {
     int32_t* nh = nullptr;
     int32_t* ids = nullptr;
     float4* up = nullptr;
+    uint32_t* flags = nullptr;   // [rays + 1] continue flags, then their prefix sums
+    int32_t* list = nullptr;     // [rays] continuing rays (sorted positions)
+    uint32_t* count = nullptr;   // [1] and the scan's tile sums after it
+    float4* state = nullptr;     // [rays * kWaveStateF4] march state between rounds
     unsigned char* base = nullptr;
 
     cudaError_t alloc(int64_t rays, bool backward, cudaStream_t st) {
@@ -221,6 +302,9 @@ struct WaveScratch {
         const size_t o_dir = take(sizeof(float4) * rays), o_key = take(4 * rays), o_val = take(4 * rays);
         const size_t o_kt = take(4 * rays), o_vt = take(4 * rays), o_hist = take(4 * hw);
         const size_t o_res = take(sizeof(float4) * rays);
+        const size_t o_flags = take(4 * (rays + 1)), o_list = take(4 * rays);
+        const size_t o_count = take(4 * (1 + scan_long_words(rays + 1)));
+        const size_t o_state = take(sizeof(float4) * kWaveStateF4 * rays);
         size_t o_nh = 0, o_ids = 0, o_up = 0;
         if (backward) {
             o_nh = take(4 * rays);
@@ -236,6 +320,10 @@ struct WaveScratch {
         val_tmp = reinterpret_cast<int32_t*>(base + o_vt);
         hist = reinterpret_cast<uint32_t*>(base + o_hist);
         res = reinterpret_cast<float4*>(base + o_res);
+        flags = reinterpret_cast<uint32_t*>(base + o_flags);
+        list = reinterpret_cast<int32_t*>(base + o_list);
+        count = reinterpret_cast<uint32_t*>(base + o_count);
+        state = reinterpret_cast<float4*>(base + o_state);
         if (backward) {
             nh = reinterpret_cast<int32_t*>(base + o_nh);
             ids = reinterpret_cast<int32_t*>(base + o_ids);
@@ -249,6 +337,48 @@ struct WaveScratch {
 int64_t chunk_points(int St) {
     const int64_t pc = kWaveChunkRays / St;
     return pc > 0 ? pc : 1;
+}
+
+// Trace the sorted rays of one chunk into w.res (and, with SAVE, the hit
+// counts and lists): compacted rounds when the scene has surfels.
+template <int K, bool SAVE>
+cudaError_t wave_trace(const SceneView& S, const TraceParams& TP, const float* x, int64_t p0, int St, int64_t rays,
+                       WaveScratch& w, cudaStream_t st) {
+    int32_t* ids = SAVE ? w.ids : nullptr;
+    int32_t* nh = SAVE ? w.nh : nullptr;
+    const int max_ids = SAVE ? kWaveSavedHits : 0;
+    if (S.n == 0) {
+        k_wave_trace<K, SAVE><<<grid_for(rays, kWaveThreads), kWaveThreads, 0, st>>>(S, TP, x, p0, St, w.dir, w.val,
+                                                                                    rays, w.res, nh, ids, max_ids);
+        count_launches(1);
+        return cudaGetLastError();
+    }
+    const unsigned g = grid_for(rays, kWaveThreads);
+    cudaError_t e = cudaMemsetAsync(w.flags, 0, sizeof(uint32_t) * (rays + 1), st);
+    if (e != cudaSuccess) return e;
+    k_wave_round<K, SAVE, kWaveFirst><<<g, kWaveThreads, 0, st>>>(S, TP, x, p0, St, w.dir, w.val, rays, w.res, nh, ids,
+                                                                  max_ids, w.list, w.count, w.state, w.flags);
+    count_launches(1);
+    for (int round = 2; round <= 4 && e == cudaSuccess; ++round) {
+        e = scan_exclusive_long(w.flags, rays + 1, w.count + 1, st);
+        if (e != cudaSuccess) break;
+        k_wave_list<<<grid_for(rays, 256), 256, 0, st>>>(w.flags, rays, w.list, w.count);
+        count_launches(1);
+        if (round < 4) {
+            e = cudaMemsetAsync(w.flags, 0, sizeof(uint32_t) * (rays + 1), st);
+            if (e != cudaSuccess) break;
+            k_wave_round<K, SAVE, kWaveNext><<<g, kWaveThreads, 0, st>>>(S, TP, x, p0, St, w.dir, w.val, rays, w.res,
+                                                                         nh, ids, max_ids, w.list, w.count, w.state,
+                                                                         w.flags);
+        } else {
+            k_wave_round<K, SAVE, kWaveLast><<<g, kWaveThreads, 0, st>>>(S, TP, x, p0, St, w.dir, w.val, rays, w.res,
+                                                                         nh, ids, max_ids, w.list, w.count, w.state,
+                                                                         w.flags);
+        }
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 template <int K>
@@ -268,11 +398,11 @@ cudaError_t wave_forward(const SceneView& S, const uint32_t* bounds, const float
                                                         w.key, w.val);
         e = sort_pairs(w.key, w.val, w.key_tmp, w.val_tmp, w.hist, rays, st);
         if (e != cudaSuccess) break;
-        k_wave_trace<K, false><<<grid_for(rays, kWaveThreads), kWaveThreads, 0, st>>>(
-            S, TP, x, p0, St, w.dir, w.val, rays, w.res, nullptr, nullptr, 0);
+        e = wave_trace<K, false>(S, TP, x, p0, St, rays, w, st);
+        if (e != cudaSuccess) break;
         k_wave_shade<K><<<grid_for(np, kWaveThreads / 32), kWaveThreads, 0, st>>>(
             S, x, n, a, r, wo, p0, np, env, H, W, nd, ns, mode, seed, TP, w.res, rgb, vis, ind);
-        count_launches(3);
+        count_launches(2);
         e = cudaGetLastError();
     }
     const cudaError_t ef = w.release(st);
@@ -304,15 +434,15 @@ cudaError_t wave_backward(const SceneView& S, const int32_t* perm, const uint32_
         e = sort_pairs(w.key, w.val, w.key_tmp, w.val_tmp, w.hist, rays, st);
         if (e != cudaSuccess) break;
         const unsigned g = grid_for(rays, kWaveThreads);
-        k_wave_trace<K, true><<<g, kWaveThreads, 0, st>>>(S, TP, x, p0, St, w.dir, w.val, rays, w.res, w.nh, w.ids,
-                                                          kWaveSavedHits);
+        e = wave_trace<K, true>(S, TP, x, p0, St, rays, w, st);
+        if (e != cudaSuccess) break;
         k_wave_grad_point<<<grid_for(np, kWaveThreads / 32), kWaveThreads, 0, st>>>(
             n, a, r, wo, p0, np, env, H, W, nd, ns, mode, seed, w.res, g_rgb, g_albedo, g_rough, g_env, w.up);
         k_wave_backward<K, true><<<g, kWaveThreads, 0, st>>>(S, TP, x, p0, St, w.dir, w.val, rays, w.res, w.nh,
                                                              w.ids, kWaveSavedHits, w.up, acc_rows);
         k_wave_backward<K, false><<<g, kWaveThreads, 0, st>>>(S, TP, x, p0, St, w.dir, w.val, rays, w.res, w.nh,
                                                               w.ids, kWaveSavedHits, w.up, acc_rows);
-        count_launches(5);
+        count_launches(4);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && S.n > 0) {
