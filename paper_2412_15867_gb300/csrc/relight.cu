@@ -401,6 +401,94 @@ __global__ void __launch_bounds__(kRelightThreads, 6) k_relight_trace(SceneView 
     res[2 * i + 1] = make_float4(st.C[4], st.C[5], st.C[6], st.T);
 }
 
+// The same traces in compacted rounds: round 1 on every sorted ray; rays
+// still marching store their state (C[7], D, T, hit count, next key) at
+// their sorted position and are regrouped, in sorted order, for rounds 2
+// and 3; the rest run to completion. Per ray the rounds and their
+// arithmetic are march_forward's (per lane), so the results are the same.
+enum RelightRound { kRelFirst = 0, kRelNext = 1, kRelLast = 2 };
+constexpr int kRelightStateF4 = 4;
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(kRelightThreads, 6) k_relight_round(
+    SceneView S, TraceParams P, const float* __restrict__ xg, int64_t p0, int Sn, const float4* __restrict__ dir,
+    const int32_t* __restrict__ order, int64_t rays, float4* __restrict__ res, const int32_t* __restrict__ list,
+    const uint32_t* __restrict__ count, float4* __restrict__ state, uint32_t* __restrict__ flags) {
+    static_assert(kRelightThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
+    const int64_t t = blockIdx.x * (int64_t)kRelightThreads + threadIdx.x;
+    const int64_t n = MODE == kRelFirst ? rays : (int64_t)*count;
+    if (t >= n) return;
+    const int64_t j = MODE == kRelFirst ? t : (int64_t)list[t];
+    const int64_t i = order[j];
+    const float4 d4 = dir[i];
+    MarchState<K, 7> st;
+    uint64_t last_key = depth_key(P.t_min, 0.f);
+    int32_t last_m = INT32_MAX;
+    if (MODE == kRelFirst) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) st.C[c] = 0.f;
+        st.D = 0.f;
+        st.T = 1.f;
+        st.nh = 0;
+        if (!(d4.w > 0.f)) {
+            res[2 * i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            res[2 * i + 1] = make_float4(0.f, 0.f, 0.f, 1.f);
+            return;
+        }
+    } else {
+        float w[16];
+#pragma unroll
+        for (int q = 0; q < kRelightStateF4; ++q) {
+            const float4 v = state[j * kRelightStateF4 + q];
+            w[4 * q] = v.x; w[4 * q + 1] = v.y; w[4 * q + 2] = v.z; w[4 * q + 3] = v.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 7; ++c) st.C[c] = w[c];
+        st.D = w[7];
+        st.T = w[8];
+        st.nh = __float_as_int(w[9]);
+        last_key = ((uint64_t)__float_as_uint(w[11]) << 32) | (uint64_t)__float_as_uint(w[10]);
+        last_m = __float_as_int(w[12]);
+    }
+    const Ray ray = make_ray(ld3r(xg, p0 + i / Sn), mk3(d4.x, d4.y, d4.z));
+    KBuffer<K, trace_threads<K>()> kb;
+    kb.bind();
+    bool ok = true, done = false;
+    do {
+        ok &= collect_round(S, ray, P, last_key, last_m, kb);
+        done = blend_round<K, 7>(S, P, kb, st, nullptr, 0, last_key, last_m);
+    } while (MODE == kRelLast && !done);
+    if (!ok) atomicOr(S.status, kErrStackOverflow);
+    if (done) {
+        res[2 * i] = make_float4(st.C[0], st.C[1], st.C[2], st.C[3]);
+        res[2 * i + 1] = make_float4(st.C[4], st.C[5], st.C[6], st.T);
+    } else {
+        float w[16];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) w[c] = st.C[c];
+        w[7] = st.D;
+        w[8] = st.T;
+        w[9] = __int_as_float(st.nh);
+        w[10] = __uint_as_float((uint32_t)last_key);
+        w[11] = __uint_as_float((uint32_t)(last_key >> 32));
+        w[12] = __int_as_float(last_m);
+        w[13] = w[14] = w[15] = 0.f;
+#pragma unroll
+        for (int q = 0; q < kRelightStateF4; ++q)
+            state[j * kRelightStateF4 + q] = make_float4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        flags[j] = 1u;
+    }
+}
+
+// pos[0..m] = exclusive prefix of the continue flags: list[pos[j]] = j for
+// every continuing ray, *count = pos[m].
+__global__ void k_relight_list(const uint32_t* __restrict__ pos, int64_t m, int32_t* __restrict__ list,
+                               uint32_t* __restrict__ count) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j == 0) *count = pos[m];
+    if (j < m && pos[j + 1] != pos[j]) list[pos[j]] = (int32_t)j;
+}
+
 __global__ void __launch_bounds__(kRelightThreads) k_relight_shade(EnvMaps M, const float* __restrict__ ng,
                                                                    const float* __restrict__ ag,
                                                                    const float* __restrict__ rg,
@@ -439,7 +527,9 @@ cudaError_t relight_wave(const SceneView& S, const uint32_t* bounds, const EnvMa
     const int64_t cap = (P < pc ? P : pc) * Sn;
     const int64_t hw = sort_hist_words(cap);
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t bytes = al(16 * cap) + 4 * al(4 * cap) + al(4 * hw) + al(32 * cap);
+    const int64_t sums = scan_long_words(cap + 1);
+    const size_t bytes = al(16 * cap) + 4 * al(4 * cap) + al(4 * hw) + al(32 * cap) + al(4 * (cap + 1)) +
+                         al(4 * cap) + al(4 * (1 + sums)) + al(16 * kRelightStateF4 * cap);
     unsigned char* base = nullptr;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, st);
     if (e != cudaSuccess) return e;
@@ -452,17 +542,48 @@ cudaError_t relight_wave(const SceneView& S, const uint32_t* bounds, const EnvMa
     int32_t* vtmp = reinterpret_cast<int32_t*>(take(4 * cap));
     uint32_t* hist = reinterpret_cast<uint32_t*>(take(4 * hw));
     float4* res = reinterpret_cast<float4*>(take(32 * cap));
+    uint32_t* flags = reinterpret_cast<uint32_t*>(take(4 * (cap + 1)));
+    int32_t* list = reinterpret_cast<int32_t*>(take(4 * cap));
+    uint32_t* count = reinterpret_cast<uint32_t*>(take(4 * (1 + sums)));
+    float4* state = reinterpret_cast<float4*>(take(16 * kRelightStateF4 * cap));
     for (int64_t p0 = 0; p0 < P && e == cudaSuccess; p0 += pc) {
         const int64_t np = P - p0 < pc ? P - p0 : pc;
         const int64_t rays = np * Sn;
         k_relight_gen<<<grid_for(rays, 256), 256, 0, st>>>(M, x, p0, rays, Sn, seed, bounds, dir, key, val);
         e = sort_pairs(key, val, ktmp, vtmp, hist, rays, st);
         if (e != cudaSuccess) break;
-        k_relight_trace<K><<<grid_for(rays, kRelightThreads), kRelightThreads, 0, st>>>(S, TP, x, p0, Sn, dir, val,
-                                                                                      rays, res);
+        if (S.n == 0) {
+            k_relight_trace<K><<<grid_for(rays, kRelightThreads), kRelightThreads, 0, st>>>(S, TP, x, p0, Sn, dir,
+                                                                                          val, rays, res);
+            count_launches(1);
+        } else {
+            const unsigned g = grid_for(rays, kRelightThreads);
+            e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (rays + 1), st);
+            if (e != cudaSuccess) break;
+            k_relight_round<K, kRelFirst><<<g, kRelightThreads, 0, st>>>(S, TP, x, p0, Sn, dir, val, rays, res, list,
+                                                                          count, state, flags);
+            count_launches(1);
+            for (int round = 2; round <= 4 && e == cudaSuccess; ++round) {
+                e = scan_exclusive_long(flags, rays + 1, count + 1, st);
+                if (e != cudaSuccess) break;
+                k_relight_list<<<grid_for(rays, 256), 256, 0, st>>>(flags, rays, list, count);
+                count_launches(1);
+                if (round < 4) {
+                    e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (rays + 1), st);
+                    if (e != cudaSuccess) break;
+                    k_relight_round<K, kRelNext><<<g, kRelightThreads, 0, st>>>(S, TP, x, p0, Sn, dir, val, rays, res,
+                                                                                 list, count, state, flags);
+                } else {
+                    k_relight_round<K, kRelLast><<<g, kRelightThreads, 0, st>>>(S, TP, x, p0, Sn, dir, val, rays, res,
+                                                                                 list, count, state, flags);
+                }
+                count_launches(1);
+            }
+            if (e != cudaSuccess) break;
+        }
         k_relight_shade<<<grid_for(np, kRelightThreads / 32), kRelightThreads, 0, st>>>(M, n, a, r, wo, p0, np, Sn,
                                                                                        dir, res, rgb, vis, ind);
-        count_launches(3);
+        count_launches(2);
         e = cudaGetLastError();
     }
     const cudaError_t ef = cudaFreeAsync(base, st);
