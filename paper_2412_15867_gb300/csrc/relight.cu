@@ -480,15 +480,6 @@ __global__ void __launch_bounds__(kRelightThreads, 6) k_relight_round(
     }
 }
 
-// pos[0..m] = exclusive prefix of the continue flags: list[pos[j]] = j for
-// every continuing ray, *count = pos[m].
-__global__ void k_relight_list(const uint32_t* __restrict__ pos, int64_t m, int32_t* __restrict__ list,
-                               uint32_t* __restrict__ count) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j == 0) *count = pos[m];
-    if (j < m && pos[j + 1] != pos[j]) list[pos[j]] = (int32_t)j;
-}
-
 __global__ void __launch_bounds__(kRelightThreads) k_relight_shade(EnvMaps M, const float* __restrict__ ng,
                                                                    const float* __restrict__ ag,
                                                                    const float* __restrict__ rg,
@@ -564,10 +555,8 @@ cudaError_t relight_wave(const SceneView& S, const uint32_t* bounds, const EnvMa
                                                                           count, state, flags);
             count_launches(1);
             for (int round = 2; round <= 4 && e == cudaSuccess; ++round) {
-                e = scan_exclusive_long(flags, rays + 1, count + 1, st);
+                e = flags_to_list(flags, rays, count + 1, list, count, st);
                 if (e != cudaSuccess) break;
-                k_relight_list<<<grid_for(rays, 256), 256, 0, st>>>(flags, rays, list, count);
-                count_launches(1);
                 if (round < 4) {
                     e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (rays + 1), st);
                     if (e != cudaSuccess) break;

@@ -1054,6 +1054,26 @@ cudaError_t scan_exclusive(uint32_t* a, int64_t m, cudaStream_t st) {
 
 int64_t scan_long_words(int64_t m) { return (m + kScanTile - 1) / kScanTile + 1; }
 
+namespace {
+// pos[0..m] = exclusive prefix of 0/1 flags: list[pos[j]] = j for every
+// flagged j, *count = pos[m].
+__global__ void k_flag_list(const uint32_t* __restrict__ pos, int64_t m, int32_t* __restrict__ list,
+                            uint32_t* __restrict__ count) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j == 0) *count = pos[m];
+    if (j < m && pos[j + 1] != pos[j]) list[pos[j]] = (int32_t)j;
+}
+}  // namespace
+
+cudaError_t flags_to_list(uint32_t* flags, int64_t m, uint32_t* sums, int32_t* list, uint32_t* count,
+                          cudaStream_t st) {
+    cudaError_t e = scan_exclusive_long(flags, m + 1, sums, st);
+    if (e != cudaSuccess) return e;
+    k_flag_list<<<(unsigned)((m + 255) / 256 > 0 ? (m + 255) / 256 : 1), 256, 0, st>>>(flags, m, list, count);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t scan_exclusive_long(uint32_t* a, int64_t m, uint32_t* sums, cudaStream_t st) {
     if (m <= 0) return cudaSuccess;
     scan_long(a, m, sums, st);

@@ -110,6 +110,11 @@ cudaError_t scan_exclusive(uint32_t* a, int64_t m, cudaStream_t st);
 // scan_long_words(m) words of scratch.
 int64_t scan_long_words(int64_t m);
 cudaError_t scan_exclusive_long(uint32_t* a, int64_t m, uint32_t* sums, cudaStream_t st);
+// The flagged indices of flags[0..m) (0/1 words; flags[m] must be 0) in
+// order: list[0..count) and *count (device). flags is overwritten by its
+// prefix sums; sums holds scan_long_words(m + 1) words.
+cudaError_t flags_to_list(uint32_t* flags, int64_t m, uint32_t* sums, int32_t* list, uint32_t* count,
+                          cudaStream_t st);
 
 // trace_fwd.cu
 irgs_status launch_trace_forward(const SceneView& sv, const float* ro, const float* rd, int64_t R,

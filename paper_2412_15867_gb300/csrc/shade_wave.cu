@@ -158,15 +158,6 @@ __global__ void __launch_bounds__(kWaveThreads, 6) k_wave_round(
     }
 }
 
-// pos[0..m] = exclusive prefix of the continue flags: list[pos[j]] = j for
-// every continuing ray, *count = pos[m].
-__global__ void k_wave_list(const uint32_t* __restrict__ pos, int64_t m, int32_t* __restrict__ list,
-                            uint32_t* __restrict__ count) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j == 0) *count = pos[m];
-    if (j < m && pos[j + 1] != pos[j]) list[pos[j]] = (int32_t)j;
-}
-
 // Per-point estimate from the stored traces (warp per point).
 template <int K>
 __global__ void __launch_bounds__(kWaveThreads) k_wave_shade(SceneView S, const float* __restrict__ xg,
@@ -360,10 +351,8 @@ cudaError_t wave_trace(const SceneView& S, const TraceParams& TP, const float* x
                                                                   max_ids, w.list, w.count, w.state, w.flags);
     count_launches(1);
     for (int round = 2; round <= 4 && e == cudaSuccess; ++round) {
-        e = scan_exclusive_long(w.flags, rays + 1, w.count + 1, st);
+        e = flags_to_list(w.flags, rays, w.count + 1, w.list, w.count, st);
         if (e != cudaSuccess) break;
-        k_wave_list<<<grid_for(rays, 256), 256, 0, st>>>(w.flags, rays, w.list, w.count);
-        count_launches(1);
         if (round < 4) {
             e = cudaMemsetAsync(w.flags, 0, sizeof(uint32_t) * (rays + 1), st);
             if (e != cudaSuccess) break;

@@ -128,15 +128,6 @@ __global__ void __launch_bounds__(trace_threads<K>(), K <= 16 ? 6 : 4) k_trace_r
     }
 }
 
-// pos[0..R] = exclusive prefix of the continue flags: list[pos[r]] = r for
-// every continuing ray, *count = pos[R].
-__global__ void k_round_list(const uint32_t* __restrict__ pos, int64_t R, int32_t* __restrict__ list,
-                             uint32_t* __restrict__ count) {
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r == 0) *count = pos[R];
-    if (r < R && pos[r + 1] != pos[r]) list[pos[r]] = (int32_t)r;
-}
-
 // Batches at least this large take the compacted rounds.
 constexpr int64_t kRoundMinRays = int64_t(1) << 20;
 constexpr int kCompactedRounds = 3;   // regroup after rounds 1, 2 and 3; rounds 4+ run to completion
@@ -161,17 +152,14 @@ cudaError_t launch_rounds(const SceneView& S, const float* ro, const float* rd, 
     uint32_t* scan_sums = count + 1;
     float4* state = reinterpret_cast<float4*>(base + state_off);
     const unsigned grid = (unsigned)((R + threads - 1) / threads);
-    const unsigned lgrid = (unsigned)((R + 255) / 256);
     e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (R + 1), st);
     if (e == cudaSuccess) {
         k_trace_round<K, FB, kRoundFirst><<<grid, threads, 0, st>>>(S, ro, rd, R, P, feat, depth, opac, nhits, ids,
                                                                      max_ids, list, count, state, flags);
         count_launches(1);
         for (int round = 2; round <= kCompactedRounds + 1 && e == cudaSuccess; ++round) {
-            e = scan_exclusive_long(flags, R + 1, scan_sums, st);
+            e = flags_to_list(flags, R, scan_sums, list, count, st);
             if (e != cudaSuccess) break;
-            k_round_list<<<lgrid, 256, 0, st>>>(flags, R, list, count);
-            count_launches(1);
             if (round <= kCompactedRounds) {
                 e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (R + 1), st);
                 if (e != cudaSuccess) break;
