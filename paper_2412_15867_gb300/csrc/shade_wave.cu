@@ -21,7 +21,7 @@
 // order from their hit lists (rays with longer lists replay the march).
 //
 // Rays are processed in chunks of whole points, at most kWaveChunkRays rays
-// each, so the scratch (~330 bytes per ray with the gradient) stays bounded.
+// each, so the scratch (~390 bytes per ray with the gradient) stays bounded.
 #include <cuda_runtime.h>
 
 #include "scene.h"
