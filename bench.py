@@ -53,7 +53,7 @@ FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 TRAFFIC = {
     # the four round launches of one forward (6.4M-ray capture): read 428.9 + 919.9 + 358.2 + 87.1 MB,
     # written 756.3 + 561.3 + 125.0 + 11.7 MB
-    "k_trace_round<16,10,*>": {"bytes_per_ray": (1794.1e6 + 1454.3e6) / 6.4e6, "src_hash": "39795c8052f9"},
+    "k_trace_round<16,10,*>": {"bytes_per_ray": (1794.1e6 + 1454.3e6) / 6.4e6, "src_hash": "99bbb098cc97"},
 }
 
 

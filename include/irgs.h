@@ -222,8 +222,9 @@ irgs_status irgs_scene_export_wide(irgs_scene scene, float* nodes, int64_t cap, 
  * k = 16 and at least 2^20 rays, rays still marching after each of the
  * first three k-buffer rounds are regrouped into full warps; that takes
  * 56 to 104 bytes per ray of scratch (72 at 4..10 channels), allocated and
- * freed stream-ordered (cudaMallocAsync) on `stream` (IRGS_ERR_OOM if that
- * fails). Results are the same either way.
+ * freed stream-ordered (cudaMallocAsync) on `stream`; if that allocation
+ * fails the rays are marched without regrouping. Results are the same
+ * either way.
  */
 irgs_status irgs_trace_forward(irgs_scene scene, const float* ray_o, const float* ray_d,
                                int64_t n_rays, const irgs_trace_params* params,

@@ -183,8 +183,13 @@ cudaError_t launch(const SceneView& S, const float* ro, const float* rd, int64_t
                    float* feat, float* depth, float* opac, int32_t* nhits, int32_t* ids, int max_ids,
                    cudaStream_t st) {
     if constexpr (WARP && K == 16) {
-        if (R >= kRoundMinRays && S.n > 0)
-            return launch_rounds<K, FB>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st);
+        // the ray list holds int32 indices; without room for the scratch the
+        // single-kernel march below does the same work
+        if (R >= kRoundMinRays && R < INT32_MAX && S.n > 0) {
+            const cudaError_t e = launch_rounds<K, FB>(S, ro, rd, R, P, feat, depth, opac, nhits, ids, max_ids, st);
+            if (e != cudaErrorMemoryAllocation) return e;
+            cudaGetLastError();   // clear the failed allocation
+        }
     }
     constexpr int threads = trace_threads<K>();
     const int64_t blocks = (R + threads - 1) / threads;
