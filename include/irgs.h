@@ -34,7 +34,7 @@
 extern "C" {
 #endif
 
-#define IRGS_ABI_VERSION 2
+#define IRGS_ABI_VERSION 3
 #define IRGS_MAX_FEATURES 16   /* blended channels per trace call */
 
 typedef enum {
@@ -434,7 +434,9 @@ typedef enum { IRGS_JOB_RENDER = 0, IRGS_JOB_RELIGHT = 1 } irgs_job_kind;
  *            rgb [P, 3] (Eq. 15 with n_diffuse cosine + n_spec GGX samples
  *            per pixel against env [env_h, env_w, 3], random stream `seed`,
  *            stream point = pixel index p; background pixels get 0).
- * P = width x height of the camera. */
+ * P = width x height of the camera. Render and G-buffer tiles trace the
+ * camera's ray of pixel p, or, when ray_o and ray_d are both non-NULL, the
+ * caller's ray p of ray_o / ray_d [P, 3] (the camera then only sets P). */
 typedef struct {
     int32_t kind;           /* irgs_job_kind (informational)          */
     int32_t scene;          /* index into the server's scenes         */
@@ -448,6 +450,8 @@ typedef struct {
     float* opacity;
     float* gbuffer;
     float* rgb;
+    const float* ray_o;     /* optional explicit rays [P, 3] (both or neither) */
+    const float* ray_d;
 } irgs_job;
 
 typedef enum { IRGS_TILE_RENDER = 0, IRGS_TILE_GBUFFER = 1, IRGS_TILE_SHADE = 2 } irgs_tile_kind;
@@ -552,10 +556,22 @@ irgs_status irgs_rasterize(irgs_scene scene, const irgs_camera* cam, const irgs_
  * capture. All calls share the one array and it keeps the last call's
  * contents; calls whose work overlaps on the GPU (other streams, other host
  * threads) race on it, so serialise them. Work is enqueued on `stream`.
+ * Errors the kernels detect (a hierarchy that fails a consistency bound)
+ * land in a status word inside the array: read it with
+ * irgs_build_lbvh_noalloc_status before the next build.
  */
 #define IRGS_NOALLOC_MAX_SURFELS 32768
 irgs_status irgs_build_lbvh_noalloc(const irgs_surfels* surfels, float alpha_min, int32_t* perm,
                                     uint32_t* keys, float* nodes, float* leaf_boxes, void* stream);
+
+/* Device-side outcome of the last irgs_build_lbvh_noalloc on `device`: waits
+ * for `stream` (the build's stream), then copies the build's status word out
+ * of the shared array into *bits (NULL to skip) without clearing it. Returns
+ * IRGS_OK if it is 0, else IRGS_ERR_DEVICE with the bits of
+ * irgs_scene_status (2: the hierarchy failed a consistency bound, so the
+ * nodes must not be used). The next build on that device overwrites the
+ * word, so read it before starting another. Allocates nothing. */
+irgs_status irgs_build_lbvh_noalloc_status(int32_t device, void* stream, uint32_t* bits);
 
 #ifdef __cplusplus
 }

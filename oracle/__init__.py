@@ -98,6 +98,9 @@ def _load():
     lib.oracle_trace.restype = C.c_int
     lib.oracle_trace.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P, P, C.c_int64,
                                  P, P, P, P, P, P, P, P, C.c_int32, P, C.c_int]
+    lib.oracle_trace_alternatives.restype = C.c_int
+    lib.oracle_trace_alternatives.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P, P, C.c_int64,
+                                              P, P, C.c_int32, P, P, P, P, P, C.c_int]
     lib.oracle_trace_grad.restype = C.c_int
     lib.oracle_trace_grad.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P, P, C.c_int64,
                                       P, P, P, P, P, P, P, P, P, C.c_int]
@@ -183,6 +186,32 @@ def trace(scene, ray_o, ray_d, params: Params = Params(), margins: Margins | Non
         raise ValueError("oracle_trace rejected its arguments")
     if max_ids > 0:
         out["ids"], out["tau"] = ids, tau
+    return out
+
+
+def trace_alternatives(scene, ray_o, ray_d, params: Params = Params(), margins: Margins = Margins(),
+                       max_alts: int = 256, n_threads: int = 0):
+    """Admissible outcomes of each ray (see oracle_trace_alternatives in
+    irgs_oracle.c): a candidate within a margin of a discontinuity in or out,
+    runs of near-equal depths in any order, the T_min stop on either side.
+    Returns feat [R,A,Fc], depth [R,A], opacity [R,A], n_hits [R,A] and
+    count [R] (outcomes filled; -1 = too many to enumerate, where only the
+    definition's own answer, outcome 0, is filled)."""
+    lib = _load()
+    means, quats, scales, opacity, feats = _surfel_arrays(scene)
+    o, d = _f32(ray_o).reshape(-1, 3), _f32(ray_d).reshape(-1, 3)
+    R, n, F = o.shape[0], means.shape[0], feats.shape[1]
+    fc, A = params.feat_count, int(max_alts)
+    out = {"feat": np.zeros((R, A, fc), np.float64), "depth": np.zeros((R, A), np.float64),
+           "opacity": np.zeros((R, A), np.float64), "n_hits": np.zeros((R, A), np.int32),
+           "count": np.zeros(R, np.int32)}
+    p, m = params.c(), margins.c()
+    rc = lib.oracle_trace_alternatives(_ptr(means), _ptr(quats), _ptr(scales), _ptr(opacity), _ptr(feats),
+                                       n, F, _ptr(o), _ptr(d), R, C.byref(p), C.byref(m), A,
+                                       _ptr(out["feat"]), _ptr(out["depth"]), _ptr(out["opacity"]),
+                                       _ptr(out["n_hits"]), _ptr(out["count"]), int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_trace_alternatives rejected its arguments")
     return out
 
 

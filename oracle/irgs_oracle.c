@@ -324,6 +324,258 @@ int oracle_trace(const float* means, const float* quats, const float* scales, co
 }
 
 /* ---------------------------------------------------------------------- */
+/* Admissible outcomes of a ray whose exact answer lies within a margin of  */
+/* a discontinuity. A correct FP32 tracer may decide such a candidate, such */
+/* an order or such a stop either way; every outcome those decisions give   */
+/* is composited here by the plain definition (Eq. 2, Eq. 8):               */
+/*   - a candidate within a margin of the alpha cutoff, the support edge,   */
+/*     an end of the ray interval or the grazing threshold is in or out;    */
+/*   - a run of hits whose successive depths differ by less than the tie    */
+/*     margin is blended in any order;                                      */
+/*   - where the transmittance after a hit lies within T_rel of T_min, the  */
+/*     march stops there or goes on (the threshold moved by 2 T_rel).       */
+/* Candidates beyond the farthest possible stop (all optional candidates    */
+/* out, the lower threshold) cannot change the result and are dropped.     */
+/* ---------------------------------------------------------------------- */
+typedef struct { double tau, alpha; int64_t id; int optional, def_in; } alt64;
+
+static int alt_cmp(const void* a, const void* b)
+{
+    const alt64* x = (const alt64*)a;
+    const alt64* y = (const alt64*)b;
+    if (x->tau < y->tau) return -1;
+    if (x->tau > y->tau) return 1;
+    return (x->id < y->id) ? -1 : (x->id > y->id);
+}
+
+/* Blend the listed entries (order[] indexes L; entries with use[] == 0 are
+ * skipped) until T < Tstop. *near_T is set when T after a blended hit lies
+ * within T_rel of T_min. Returns the number of blended hits. */
+static int64_t alt_composite(const alt64* L, const int64_t* order, const unsigned char* use, int64_t n,
+                             const float* feats, int32_t F_total, const oracle_params* P, double Tstop,
+                             double T_rel, double* C, double* D, double* Tfin, int* near_T)
+{
+    double T = 1.0;
+    int64_t nc = 0;
+    for (int c = 0; c < P->feat_count; ++c) C[c] = 0.0;
+    *D = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const alt64* h = &L[order[i]];
+        if (!use[order[i]]) continue;
+        double w = T * h->alpha;
+        const float* f = feats ? feats + h->id * (int64_t)F_total + P->feat_offset : NULL;
+        for (int c = 0; c < P->feat_count; ++c) C[c] += w * (double)f[c];
+        *D += w * h->tau;
+        T *= (1.0 - h->alpha);
+        ++nc;
+        if (near_T && fabs(T - P->T_min) < T_rel * P->T_min) *near_T = 1;
+        if (T < Tstop) break;
+    }
+    *Tfin = T;
+    return nc;
+}
+
+static double factorial_d(int k)
+{
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= (double)i;
+    return f;
+}
+
+/* For R rays: the admissible outcomes (feat [R, max_alts, feat_count],
+ * depth / opacity [R, max_alts], n_hits [R, max_alts]) and their number
+ * count[R] (-1: more than max_alts outcomes, or a run of more than 5 ties or
+ * more than 12 optional candidates; left unresolved). The first outcome is
+ * always the definition's own answer. Returns 0, or -1 on bad arguments. */
+int oracle_trace_alternatives(const float* means, const float* quats, const float* scales, const float* opacity,
+                              const float* feats, int64_t n, int32_t F_total,
+                              const float* ray_o, const float* ray_d, int64_t R,
+                              const oracle_params* P, const oracle_margins* M, int32_t max_alts,
+                              double* out_feat, double* out_depth, double* out_opacity, int32_t* out_nhits,
+                              int32_t* out_count, int n_threads)
+{
+    if (n < 0 || R < 0 || !P || !M || max_alts < 1) return -1;
+    if (P->feat_count > 0 && (P->feat_offset < 0 || P->feat_offset + P->feat_count > F_total)) return -1;
+    surfel64* s = (surfel64*)malloc(sizeof(surfel64) * (size_t)(n > 0 ? n : 1));
+    if (!s) return -1;
+    load_surfels(means, quats, scales, opacity, n, P->alpha_min, s);
+    nthreads_set(n_threads);
+    const int fc = P->feat_count;
+    int err = 0;
+#pragma omp parallel
+    {
+        size_t cap = (size_t)(n > 0 ? n : 1);
+        alt64* L = (alt64*)malloc(sizeof(alt64) * cap);
+        int64_t* base = (int64_t*)malloc(sizeof(int64_t) * cap);
+        int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * cap);
+        unsigned char* use = (unsigned char*)malloc(cap);
+        double* C = (double*)malloc(sizeof(double) * (size_t)(fc > 0 ? fc : 1));
+        if (!L || !base || !ord || !use || !C) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(dynamic, 4)
+            for (int64_t r = 0; r < R; ++r) {
+                double o[3] = {ray_o[3 * r], ray_o[3 * r + 1], ray_o[3 * r + 2]};
+                double d[3] = {ray_d[3 * r], ray_d[3 * r + 1], ray_d[3 * r + 2]};
+                double dn = sqrt(dot3(d, d));
+                int64_t nl = 0;
+                for (int64_t i = 0; i < n; ++i) {
+                    const surfel64* S = &s[i];
+                    cand64 c;
+                    if (S->rc2 < 0.0) continue;
+                    int meets = intersect(S, o, d, &c);
+                    if (c.den == 0.0) continue;
+                    int near_graze = fabs(c.den) < 2e-8 * dn;
+                    if (!meets && fabs(c.den) < 0.5e-8 * dn) continue;
+                    double rc2 = S->rc2 > 1e-12 ? S->rc2 : 1e-12;
+                    /* rejected whichever way a rounding goes */
+                    if (c.rho2 > S->rc2 + M->rho_rel * rc2) continue;
+                    if (c.alpha_raw < P->alpha_min - M->alpha_abs) continue;
+                    if (!(c.tau > P->t_min - M->t_abs) || !(c.tau < P->t_max + M->t_abs)) continue;
+                    double alpha = c.alpha_raw < P->alpha_max ? c.alpha_raw : P->alpha_max;
+                    int accepted = meets && c.rho2 <= S->rc2 && alpha >= P->alpha_min
+                                   && c.tau > P->t_min && c.tau < P->t_max;
+                    int ambiguous = !meets || near_graze || fabs(c.rho2 - S->rc2) < M->rho_rel * rc2
+                                    || fabs(c.alpha_raw - P->alpha_min) < M->alpha_abs
+                                    || fabs(c.tau - P->t_min) < M->t_abs
+                                    || (isfinite(P->t_max) && fabs(c.tau - P->t_max) < M->t_abs);
+                    if (!accepted && !ambiguous) continue;
+                    L[nl].tau = c.tau;
+                    L[nl].alpha = alpha;
+                    L[nl].id = i;
+                    L[nl].optional = ambiguous;
+                    L[nl].def_in = accepted;
+                    nl++;
+                }
+                qsort(L, (size_t)nl, sizeof(alt64), alt_cmp);
+                for (int64_t i = 0; i < nl; ++i) base[i] = i;
+                /* farthest stop: every optional candidate out, the lower threshold */
+                for (int64_t i = 0; i < nl; ++i) use[i] = (unsigned char)!L[i].optional;
+                double D, Tf;
+                double Tlo = P->T_min * (1.0 - 2.0 * M->T_rel);
+                int64_t far = 0;
+                {
+                    double T = 1.0;
+                    int64_t i = 0;
+                    for (; i < nl; ++i) {
+                        if (!use[i]) continue;
+                        T *= (1.0 - L[i].alpha);
+                        if (T < Tlo) break;
+                    }
+                    far = i < nl ? i : nl - 1;   /* index of the farthest possible stop hit */
+                }
+                int64_t kept = nl;
+                if (nl > 0) {
+                    kept = far + 1;
+                    while (kept < nl) {
+                        double t = fabs(L[kept - 1].tau) > 1.0 ? fabs(L[kept - 1].tau) : 1.0;
+                        if (fabs(L[kept].tau - L[kept - 1].tau) < M->tie_abs * t) kept++;
+                        else break;
+                    }
+                }
+                /* optional candidates and runs of near-equal depths among the kept entries */
+                int n_opt = 0;
+                int opt_idx[12];
+                int64_t run_start[64];
+                int run_len[64];
+                int n_runs = 0;
+                int unresolved = 0;
+                for (int64_t i = 0; i < kept; ++i) {
+                    if (L[i].optional) {
+                        if (n_opt < 12) opt_idx[n_opt] = (int)i;
+                        n_opt++;
+                    }
+                }
+                for (int64_t i = 0; i + 1 < kept;) {
+                    int64_t j = i;
+                    while (j + 1 < kept) {
+                        double t = fabs(L[j].tau) > 1.0 ? fabs(L[j].tau) : 1.0;
+                        if (fabs(L[j + 1].tau - L[j].tau) < M->tie_abs * t) j++;
+                        else break;
+                    }
+                    if (j > i) {
+                        if (n_runs < 64 && j - i + 1 <= 5) {
+                            run_start[n_runs] = i;
+                            run_len[n_runs] = (int)(j - i + 1);
+                        }
+                        n_runs++;
+                        if (j - i + 1 > 5) unresolved = 1;
+                    }
+                    i = j + 1;
+                }
+                double n_var = ldexp(1.0, n_opt > 12 ? 12 : n_opt);
+                for (int q = 0; q < n_runs && q < 64; ++q) n_var *= factorial_d(run_len[q]);
+                if (n_opt > 12 || n_runs > 64 || n_var > (double)max_alts) unresolved = 1;
+                int32_t cnt = 0;
+                double* of = out_feat + (size_t)r * max_alts * (fc > 0 ? fc : 0);
+                double* od = out_depth + (size_t)r * max_alts;
+                double* oo = out_opacity + (size_t)r * max_alts;
+                int32_t* on = out_nhits + (size_t)r * max_alts;
+                for (int64_t v = 0; v < (unresolved ? 1 : (int64_t)n_var); ++v) {
+                    /* selection: bit b of v flips the definition's decision on
+                     * optional candidate b (v = 0 is the definition's answer) */
+                    for (int64_t i = 0; i < kept; ++i) use[i] = (unsigned char)L[i].def_in;
+                    int64_t rest = v;
+                    if (!unresolved) {
+                        for (int b = 0; b < n_opt; ++b) {
+                            if (rest & 1) use[opt_idx[b]] = (unsigned char)!L[opt_idx[b]].def_in;
+                            rest >>= 1;
+                        }
+                    }
+                    /* order: each run of near-equal depths permuted by its
+                     * Lehmer code (code 0 = the definition's (tau, id) order) */
+                    for (int64_t i = 0; i < kept; ++i) ord[i] = base[i];
+                    if (!unresolved) {
+                        for (int q = 0; q < n_runs; ++q) {
+                            int len = run_len[q];
+                            double f = factorial_d(len);
+                            int64_t code = rest % (int64_t)f;
+                            rest /= (int64_t)f;
+                            int avail[5];
+                            for (int a = 0; a < len; ++a) avail[a] = a;
+                            int left = len;
+                            for (int a = 0; a < len; ++a) {
+                                int64_t fa = (int64_t)factorial_d(len - 1 - a);
+                                int pick = (int)(code / fa);
+                                code %= fa;
+                                ord[run_start[q] + a] = run_start[q] + avail[pick];
+                                for (int z = pick; z + 1 < left; ++z) avail[z] = avail[z + 1];
+                                left--;
+                            }
+                        }
+                    }
+                    int nearT = 0;
+                    int64_t nc = alt_composite(L, ord, use, kept, feats, F_total, P, P->T_min, M->T_rel, C, &D,
+                                               &Tf, &nearT);
+                    double thr[3] = {P->T_min, P->T_min * (1.0 + 2.0 * M->T_rel), P->T_min * (1.0 - 2.0 * M->T_rel)};
+                    int nthr = nearT ? 3 : 1;
+                    for (int t = 0; t < nthr; ++t) {
+                        if (t > 0)
+                            nc = alt_composite(L, ord, use, kept, feats, F_total, P, thr[t], M->T_rel, C, &D, &Tf,
+                                               NULL);
+                        if (cnt >= max_alts) {
+                            unresolved = 1;
+                            break;
+                        }
+                        for (int c = 0; c < fc; ++c) of[(size_t)cnt * fc + c] = C[c];
+                        od[cnt] = D;
+                        oo[cnt] = 1.0 - Tf;
+                        on[cnt] = (int32_t)nc;
+                        cnt++;
+                    }
+                    if (unresolved && v > 0) break;
+                }
+                out_count[r] = unresolved ? -1 : cnt;
+            }
+        }
+        free(L); free(base); free(ord); free(use); free(C);
+    }
+    free(s);
+    return err ? -1 : 0;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Analytic gradient (the differentiable tracer of Sec. 3.3).              */
 /* ---------------------------------------------------------------------- */
 

@@ -63,6 +63,7 @@ _SIGS = {
     "irgs_trace_backward": (C.c_int, [P, P, P, C.c_int64, C.POINTER(TraceParamsC), P, P, P, P, P,
                                       C.c_int32, P, P, P, P, P, P, P, P, P]),
     "irgs_build_lbvh_noalloc": (C.c_int, [C.POINTER(Surfels), C.c_float, P, P, P, P, P]),
+    "irgs_build_lbvh_noalloc_status": (C.c_int, [C.c_int32, P, C.POINTER(C.c_uint32)]),
     "irgs_shade_mc": (C.c_int, [P, P, P, P, P, P, C.c_int64, P, C.c_int32, C.c_int32, C.c_int32,
                                 C.c_int32, C.c_uint64, C.POINTER(TraceParamsC), P, P, P, P]),
     "irgs_shade_mc_backward": (C.c_int, [P, P, P, P, P, P, C.c_int64, P, C.c_int32, C.c_int32, C.c_int32,

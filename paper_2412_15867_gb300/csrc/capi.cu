@@ -39,8 +39,8 @@ irgs_status check_params(const irgs_scene sc, const irgs_trace_params* p, bool s
     return IRGS_OK;
 }
 
-irgs_status use_device(const irgs_scene sc) {
-    return cudaSetDevice(sc->device) == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+irgs_status use_device(irgs::DeviceGuard& g, const irgs_scene sc) {
+    return g.set(sc->device) ? IRGS_OK : IRGS_ERR_CUDA;
 }
 
 // Shading runs as one fused kernel (a warp per point tracing its own
@@ -102,14 +102,15 @@ irgs_status irgs_build_scene_ex(const irgs_surfels* s, float alpha_min, uint32_t
     if (s->n > 0 && (!s->means || !s->quats || !s->scales || !s->opacity)) return IRGS_ERR_INVALID_ARG;
     if (s->n > 0 && s->num_features > 0 && !s->features) return IRGS_ERR_INVALID_ARG;
     if (s->num_features == 0 && s->features) return IRGS_ERR_INVALID_ARG;
+    cudaPointerAttributes at;
     if (s->n > 0) {
-        cudaPointerAttributes at;
         if (cudaPointerGetAttributes(&at, s->means) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
             cudaGetLastError();
             return IRGS_ERR_INVALID_ARG;
         }
-        if (cudaSetDevice(at.device) != cudaSuccess) return IRGS_ERR_CUDA;
     }
+    irgs::DeviceGuard dg;
+    if (s->n > 0 && !dg.set(at.device)) return IRGS_ERR_CUDA;
     return irgs::build_scene_impl(s, alpha_min, build_flags, static_cast<cudaStream_t>(stream), out);
 }
 
@@ -118,7 +119,8 @@ irgs_status irgs_update_scene(irgs_scene sc, const irgs_surfels* s, void* stream
     if (s->n != sc->n || s->num_features != sc->F) return IRGS_ERR_INVALID_ARG;
     if (s->n > 0 && (!s->means || !s->quats || !s->scales || !s->opacity)) return IRGS_ERR_INVALID_ARG;
     if (s->n > 0 && s->num_features > 0 && !s->features) return IRGS_ERR_INVALID_ARG;
-    irgs_status st = use_device(sc);
+    irgs::DeviceGuard dg;
+    irgs_status st = use_device(dg, sc);
     if (st != IRGS_OK) return st;
     return irgs::update_scene_impl(sc, s, static_cast<cudaStream_t>(stream));
 }
@@ -128,14 +130,16 @@ irgs_status irgs_refit_scene(irgs_scene sc, const irgs_surfels* s, void* stream)
     if (s->n != sc->n || s->num_features != sc->F) return IRGS_ERR_INVALID_ARG;
     if (s->n > 0 && (!s->means || !s->quats || !s->scales || !s->opacity)) return IRGS_ERR_INVALID_ARG;
     if (s->n > 0 && s->num_features > 0 && !s->features) return IRGS_ERR_INVALID_ARG;
-    irgs_status st = use_device(sc);
+    irgs::DeviceGuard dg;
+    irgs_status st = use_device(dg, sc);
     if (st != IRGS_OK) return st;
     return irgs::refit_scene_impl(sc, s, static_cast<cudaStream_t>(stream));
 }
 
 irgs_status irgs_destroy_scene(irgs_scene sc) {
     if (sc == nullptr) return IRGS_OK;
-    cudaSetDevice(sc->device);
+    irgs::DeviceGuard dg;
+    dg.set(sc->device);
     cudaDeviceSynchronize();
     irgs::free_scene(sc);
     return IRGS_OK;
@@ -152,7 +156,8 @@ irgs_status irgs_scene_info(irgs_scene sc, int64_t* n, int32_t* F, float* alpha_
 
 irgs_status irgs_scene_status(irgs_scene sc, void* stream, uint32_t* bits) {
     if (sc == nullptr) return IRGS_ERR_INVALID_ARG;
-    if (use_device(sc) != IRGS_OK) return IRGS_ERR_CUDA;
+    irgs::DeviceGuard dg;
+    if (use_device(dg, sc) != IRGS_OK) return IRGS_ERR_CUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint32_t h = 0;
     if (cudaStreamSynchronize(st) != cudaSuccess) return IRGS_ERR_CUDA;
@@ -164,7 +169,8 @@ irgs_status irgs_scene_status(irgs_scene sc, void* stream, uint32_t* bits) {
 
 irgs_status irgs_scene_export(irgs_scene sc, int32_t* perm, uint32_t* keys, float* nodes, float* leaf_boxes) {
     if (sc == nullptr) return IRGS_ERR_INVALID_ARG;
-    if (use_device(sc) != IRGS_OK) return IRGS_ERR_CUDA;
+    irgs::DeviceGuard dg;
+    if (use_device(dg, sc) != IRGS_OK) return IRGS_ERR_CUDA;
     if (cudaDeviceSynchronize() != cudaSuccess) return IRGS_ERR_CUDA;
     const int64_t n = sc->n, nn = n > 1 ? n - 1 : 1;
     cudaError_t e = cudaSuccess;
@@ -178,7 +184,8 @@ irgs_status irgs_scene_export(irgs_scene sc, int32_t* perm, uint32_t* keys, floa
 
 irgs_status irgs_scene_export_wide(irgs_scene sc, float* nodes, int64_t cap, int64_t* n_wide) {
     if (sc == nullptr || cap < 0) return IRGS_ERR_INVALID_ARG;
-    if (use_device(sc) != IRGS_OK) return IRGS_ERR_CUDA;
+    irgs::DeviceGuard dg;
+    if (use_device(dg, sc) != IRGS_OK) return IRGS_ERR_CUDA;
     if (cudaDeviceSynchronize() != cudaSuccess) return IRGS_ERR_CUDA;
     int64_t nw = 1;
     if (sc->n > 1) {
@@ -206,7 +213,8 @@ irgs_status irgs_trace_forward(irgs_scene sc, const float* ray_o, const float* r
     if (n_rays > 0 && params->feat_count > 0 && !out_feat) return IRGS_ERR_INVALID_ARG;
     if (out_hit_ids && max_hit_ids <= 0) return IRGS_ERR_INVALID_ARG;
     if (n_rays >= (int64_t)UINT32_MAX * 128) return IRGS_ERR_INVALID_ARG;
-    if ((s = use_device(sc)) != IRGS_OK) return s;
+    irgs::DeviceGuard dg;
+    if ((s = use_device(dg, sc)) != IRGS_OK) return s;
     return irgs::launch_trace_forward(sc->view(), ray_o, ray_d, n_rays, *params, out_feat, out_depth, out_opacity,
                                       out_nhits, out_hit_ids, out_hit_ids ? max_hit_ids : 0,
                                       static_cast<cudaStream_t>(stream));
@@ -220,7 +228,8 @@ irgs_status irgs_trace_stats(irgs_scene sc, const float* ray_o, const float* ray
     if (params->k != 16 || params->feat_count > 10) return IRGS_ERR_UNSUPPORTED;
     if (n_rays > 0 && (!ray_o || !ray_d || !out_stats)) return IRGS_ERR_INVALID_ARG;
     if (n_rays >= (int64_t)UINT32_MAX * 128) return IRGS_ERR_INVALID_ARG;
-    if ((s = use_device(sc)) != IRGS_OK) return s;
+    irgs::DeviceGuard dg;
+    if ((s = use_device(dg, sc)) != IRGS_OK) return s;
     return irgs::launch_trace_stats(sc->view(), ray_o, ray_d, n_rays, *params, out_stats,
                                     static_cast<cudaStream_t>(stream));
 }
@@ -241,7 +250,8 @@ irgs_status irgs_trace_backward(irgs_scene sc, const float* ray_o, const float* 
     if (sc->n > 0 && sc->F > 0 && params->feat_count > 0 && !g_features) return IRGS_ERR_INVALID_ARG;
     if (hit_ids != nullptr && max_hit_ids <= 0) return IRGS_ERR_INVALID_ARG;
     if (n_rays >= (int64_t)UINT32_MAX * 128) return IRGS_ERR_INVALID_ARG;
-    if ((s = use_device(sc)) != IRGS_OK) return s;
+    irgs::DeviceGuard dg;
+    if ((s = use_device(dg, sc)) != IRGS_OK) return s;
     return irgs::launch_trace_backward(sc->view(), sc->perm, ray_o, ray_d, n_rays, *params, out_feat, out_depth,
                                        out_opacity, out_nhits, hit_ids, max_hit_ids, g_feat, g_depth, g_opacity,
                                        g_means, g_quats, g_scales, g_opacity_param, g_features,
@@ -255,7 +265,8 @@ irgs_status irgs_shade_mc(irgs_scene sc, const float* x, const float* n, const f
     irgs_status s = check_shade(sc, params, n_points, env, env_h, env_w, n_diffuse, n_spec);
     if (s != IRGS_OK) return s;
     if (n_points > 0 && (!x || !n || !albedo || !rough || !wo || !out_rgb)) return IRGS_ERR_INVALID_ARG;
-    if ((s = use_device(sc)) != IRGS_OK) return s;
+    irgs::DeviceGuard dg;
+    if ((s = use_device(dg, sc)) != IRGS_OK) return s;
     if (fused_shading(params))
         return irgs::launch_shade_mc(sc->view(), x, n, albedo, rough, wo, n_points, env, env_h, env_w, n_diffuse,
                                      n_spec, seed, *params, out_rgb, out_vis, out_ind,
@@ -276,7 +287,8 @@ irgs_status irgs_shade_mc_backward(irgs_scene sc, const float* x, const float* n
     if (n_points > 0 && (!x || !n || !albedo || !rough || !wo || !g_rgb || !g_albedo || !g_rough))
         return IRGS_ERR_INVALID_ARG;
     if (sc->n > 0 && (!g_means || !g_quats || !g_scales || !g_opacity || !g_features)) return IRGS_ERR_INVALID_ARG;
-    if ((s = use_device(sc)) != IRGS_OK) return s;
+    irgs::DeviceGuard dg;
+    if ((s = use_device(dg, sc)) != IRGS_OK) return s;
     if (fused_shading(params))
         return irgs::launch_shade_mc_backward(sc->view(), sc->perm, x, n, albedo, rough, wo, n_points, env, env_h,
                                               env_w, n_diffuse, n_spec, seed, *params, g_rgb, g_albedo, g_rough,
@@ -297,7 +309,8 @@ irgs_status irgs_rasterize(irgs_scene sc, const irgs_camera* cam, const irgs_tra
     if (cam->width <= 0 || cam->height <= 0 || !(cam->tan_half_fov > 0.f)) return IRGS_ERR_INVALID_ARG;
     if ((int64_t)cam->width * cam->height > ((int64_t)1 << 31) - 1) return IRGS_ERR_INVALID_ARG;
     if (!out_depth || !out_opacity || (params->feat_count > 0 && !out_feat)) return IRGS_ERR_INVALID_ARG;
-    if ((s = use_device(sc)) != IRGS_OK) return s;
+    irgs::DeviceGuard dg;
+    if ((s = use_device(dg, sc)) != IRGS_OK) return s;
     return irgs::launch_rasterize(sc->view(), sc->leaf_box, *cam, *params, out_feat, out_depth, out_opacity,
                                   out_nhits, static_cast<cudaStream_t>(stream));
 }
@@ -310,7 +323,8 @@ irgs_status irgs_envmap_create(const float* env, int32_t H, int32_t W, void* str
 
 irgs_status irgs_envmap_destroy(irgs_envmap m) {
     if (m == nullptr) return IRGS_OK;
-    cudaSetDevice(m->device);
+    irgs::DeviceGuard dg;
+    dg.set(m->device);
     cudaDeviceSynchronize();
     irgs::free_envmap(m);
     return IRGS_OK;
@@ -319,7 +333,8 @@ irgs_status irgs_envmap_destroy(irgs_envmap m) {
 irgs_status irgs_envmap_export(irgs_envmap m, float* irr, float* pref, float* lut, double* row_cdf,
                                double* col_cdf, void* stream) {
     if (m == nullptr) return IRGS_ERR_INVALID_ARG;
-    if (cudaSetDevice(m->device) != cudaSuccess) return IRGS_ERR_CUDA;
+    irgs::DeviceGuard dg;
+    if (!dg.set(m->device)) return IRGS_ERR_CUDA;
     return irgs::export_envmap_impl(m, irr, pref, lut, row_cdf, col_cdf, static_cast<cudaStream_t>(stream));
 }
 
@@ -336,7 +351,8 @@ irgs_status irgs_relight(irgs_scene sc, irgs_envmap m, const float* x, const flo
     if (m->device != sc->device) return IRGS_ERR_INVALID_ARG;
     if (n_points > 0 && (!x || !n || !albedo || !rough || !wo || !out_rgb)) return IRGS_ERR_INVALID_ARG;
     if (n_points >= (int64_t)UINT32_MAX * 4) return IRGS_ERR_INVALID_ARG;
-    if ((s = use_device(sc)) != IRGS_OK) return s;
+    irgs::DeviceGuard dg;
+    if ((s = use_device(dg, sc)) != IRGS_OK) return s;
     return irgs::launch_relight(sc->view(), sc->bounds, m, x, n, albedo, rough, wo, n_points, n_samples, seed,
                                 *params, out_rgb, out_vis, out_ind, static_cast<cudaStream_t>(stream));
 }
@@ -354,9 +370,22 @@ irgs_status irgs_build_lbvh_noalloc(const irgs_surfels* s, float alpha_min, int3
         cudaGetLastError();
         return IRGS_ERR_INVALID_ARG;
     }
-    if (cudaSetDevice(at.device) != cudaSuccess) return IRGS_ERR_CUDA;
+    irgs::DeviceGuard dg;
+    if (!dg.set(at.device)) return IRGS_ERR_CUDA;
     return irgs::build_lbvh_noalloc_impl(s, alpha_min, perm, keys, nodes, leaf_boxes,
                                          static_cast<cudaStream_t>(stream));
+}
+
+irgs_status irgs_build_lbvh_noalloc_status(int32_t device, void* stream, uint32_t* bits) {
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return IRGS_ERR_CUDA;
+    }
+    if (device < 0 || device >= count) return IRGS_ERR_INVALID_ARG;
+    irgs::DeviceGuard dg;
+    if (!dg.set(device)) return IRGS_ERR_CUDA;
+    return irgs::lbvh_noalloc_status_impl(static_cast<cudaStream_t>(stream), bits);
 }
 
 }  // extern "C"

@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kRelightThreads, 6) k_relight_round(
     const float4 d4 = dir[i];
     MarchState<K, 7> st;
     uint64_t last_key = depth_key(P.t_min, 0.f);
-    int32_t last_m = INT32_MAX;
+    int32_t last_u = INT32_MAX;
     if (MODE == kRelFirst) {
 #pragma unroll
         for (int c = 0; c < 7; ++c) st.C[c] = 0.f;
@@ -448,15 +448,15 @@ __global__ void __launch_bounds__(kRelightThreads, 6) k_relight_round(
         st.T = w[8];
         st.nh = __float_as_int(w[9]);
         last_key = ((uint64_t)__float_as_uint(w[11]) << 32) | (uint64_t)__float_as_uint(w[10]);
-        last_m = __float_as_int(w[12]);
+        last_u = __float_as_int(w[12]);
     }
     const Ray ray = make_ray(ld3r(xg, p0 + i / Sn), mk3(d4.x, d4.y, d4.z));
     KBuffer<K, trace_threads<K>()> kb;
     kb.bind();
     bool ok = true, done = false;
     do {
-        ok &= collect_round(S, ray, P, last_key, last_m, kb);
-        done = blend_round<K, 7>(S, P, kb, st, nullptr, 0, last_key, last_m);
+        ok &= collect_round(S, ray, P, last_key, last_u, kb);
+        done = blend_round<K, 7>(S, P, kb, st, nullptr, 0, last_key, last_u);
     } while (MODE == kRelLast && !done);
     if (!ok) atomicOr(S.status, kErrStackOverflow);
     if (done) {
@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(kRelightThreads, 6) k_relight_round(
         w[9] = __int_as_float(st.nh);
         w[10] = __uint_as_float((uint32_t)last_key);
         w[11] = __uint_as_float((uint32_t)(last_key >> 32));
-        w[12] = __int_as_float(last_m);
+        w[12] = __int_as_float(last_u);
         w[13] = w[14] = w[15] = 0.f;
 #pragma unroll
         for (int q = 0; q < kRelightStateF4; ++q)

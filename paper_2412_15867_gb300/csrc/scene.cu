@@ -1225,24 +1225,16 @@ void* noalloc_scratch(int device) {
 
 }  // namespace
 
-irgs_status build_lbvh_noalloc_impl(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,
-                                    float* nodes, float* leaf_boxes, cudaStream_t st) {
-    int device = 0;
-    if (cudaGetDevice(&device) != cudaSuccess) return IRGS_ERR_CUDA;
-    unsigned char* base = static_cast<unsigned char*>(noalloc_scratch(device));
-    if (base == nullptr) return IRGS_ERR_CUDA;
-    const int64_t n = s->n, M = kNoallocMax;
+// The scratch array's carve-out for one allocation-free build: the scene
+// view's work buffers and its device status word. Returns the bytes used.
+size_t noalloc_carve(unsigned char* base, irgs_scene_s& sc) {
+    const int64_t M = kNoallocMax;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         unsigned char* p = base + off;
         off += align_up(bytes);
         return p;
     };
-    irgs_scene_s sc;   // a view onto caller buffers and the scratch array
-    sc.device = device;
-    sc.n = n;
-    sc.F = 0;
-    sc.alpha_min = alpha_min;
     sc.rec_user = reinterpret_cast<float4*>(take(sizeof(float4) * 4 * M));
     sc.rec = reinterpret_cast<float4*>(take(sizeof(float4) * 4 * M));
     sc.box_user = reinterpret_cast<float*>(take(sizeof(float) * 6 * M));
@@ -1256,13 +1248,42 @@ irgs_status build_lbvh_noalloc_impl(const irgs_surfels* s, float alpha_min, int3
     sc.hist = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * 256 * kNoallocTiles));
     sc.bounds = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * 6));
     sc.status = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t)));
+    return off;
+}
+
+irgs_status build_lbvh_noalloc_impl(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,
+                                    float* nodes, float* leaf_boxes, cudaStream_t st) {
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return IRGS_ERR_CUDA;
+    unsigned char* base = static_cast<unsigned char*>(noalloc_scratch(device));
+    if (base == nullptr) return IRGS_ERR_CUDA;
+    irgs_scene_s sc;   // a view onto caller buffers and the scratch array
+    sc.device = device;
+    sc.n = s->n;
+    sc.F = 0;
+    sc.alpha_min = alpha_min;
+    const size_t used = noalloc_carve(base, sc);
     sc.keys = keys;
     sc.perm = perm;
     sc.nodes = reinterpret_cast<Node*>(nodes);
     sc.leaf_box = leaf_boxes;
-    if (off > kNoallocBytes) return IRGS_ERR_CUDA;   // carve-out mismatch (cannot happen)
+    if (used > kNoallocBytes) return IRGS_ERR_CUDA;   // carve-out mismatch (cannot happen)
     if (cudaMemsetAsync(sc.status, 0, sizeof(uint32_t), st) != cudaSuccess) return IRGS_ERR_CUDA;
     return enqueue_build(&sc, s, st);
+}
+
+irgs_status lbvh_noalloc_status_impl(cudaStream_t st, uint32_t* bits) {
+    int device = 0;
+    if (cudaGetDevice(&device) != cudaSuccess) return IRGS_ERR_CUDA;
+    unsigned char* base = static_cast<unsigned char*>(noalloc_scratch(device));
+    if (base == nullptr) return IRGS_ERR_CUDA;
+    irgs_scene_s sc;
+    noalloc_carve(base, sc);
+    uint32_t h = 0;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return IRGS_ERR_CUDA;
+    if (cudaMemcpy(&h, sc.status, sizeof(uint32_t), cudaMemcpyDeviceToHost) != cudaSuccess) return IRGS_ERR_CUDA;
+    if (bits) *bits = h;
+    return h == 0u ? IRGS_OK : IRGS_ERR_DEVICE;
 }
 
 }  // namespace irgs

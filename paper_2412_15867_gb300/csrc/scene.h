@@ -75,6 +75,33 @@ struct irgs_envmap_s {
 
 namespace irgs {
 
+// Restores the calling thread's current device when an entry point that
+// switched to its scene's device returns (a C library call must not change
+// which device the caller's later CUDA calls go to).
+class DeviceGuard {
+  public:
+    DeviceGuard() {
+        if (cudaGetDevice(&prev_) != cudaSuccess) {
+            cudaGetLastError();
+            prev_ = -1;
+        }
+    }
+    ~DeviceGuard() {
+        if (switched_ && prev_ >= 0) cudaSetDevice(prev_);
+    }
+    DeviceGuard(const DeviceGuard&) = delete;
+    DeviceGuard& operator=(const DeviceGuard&) = delete;
+    bool set(int device) {
+        if (device == prev_) return true;
+        switched_ = true;
+        return cudaSetDevice(device) == cudaSuccess;
+    }
+
+  private:
+    int prev_ = -1;
+    bool switched_ = false;
+};
+
 // raster.cu
 irgs_status launch_rasterize(const SceneView& sv, const float* leaf_box, const irgs_camera& cam,
                              const irgs_trace_params& p, float* feat, float* depth, float* opac, int32_t* nhits,
@@ -97,6 +124,7 @@ irgs_status update_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t
 irgs_status refit_scene_impl(irgs_scene sc, const irgs_surfels* s, cudaStream_t st);
 irgs_status build_lbvh_noalloc_impl(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,
                                     float* nodes, float* leaf_boxes, cudaStream_t st);
+irgs_status lbvh_noalloc_status_impl(cudaStream_t st, uint32_t* bits);
 void free_scene(irgs_scene sc);
 // Stable LSD radix sort of (keys, vals) pairs by the low key_bits bits of
 // the keys (8-bit passes, rounded up to an even count; the result ends in

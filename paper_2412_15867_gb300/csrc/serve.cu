@@ -6,7 +6,8 @@
 // CUDA graph and replayed with new table contents.
 //
 // Work per tile kind (IRGS Eq. 8 for the traces, Eq. 13-15 for shading):
-//   render  : camera rays -> Trace -> feat / depth / opacity per pixel;
+//   render  : camera rays (or the request's own rays) -> Trace -> feat /
+//             depth / opacity per pixel;
 //   gbuffer : camera rays -> Trace of the material channels (albedo,
 //             roughness, normal) -> per-pixel G-buffer normalised by the
 //             opacity (Eq. 9): x = o + (D/O) d, n, a, r, w_o = -d;
@@ -101,7 +102,12 @@ __global__ void __launch_bounds__(kServeThreads) k_serve(ServeArgs A) {
                 const bool live = i < tile.count;
                 const int64_t p = (int64_t)tile.first + (live ? i : 0);
                 f3 o, d;
-                camera_ray(job.cam, p, o, d);
+                if (job.ray_o != nullptr) {
+                    o = mk3(job.ray_o[3 * p], job.ray_o[3 * p + 1], job.ray_o[3 * p + 2]);
+                    d = mk3(job.ray_d[3 * p], job.ray_d[3 * p + 1], job.ray_d[3 * p + 2]);
+                } else {
+                    camera_ray(job.cam, p, o, d);
+                }
                 const Ray ray = make_ray(o, d);
                 MarchState<kServeK, 10> st;
                 const bool ok = march_forward<kServeK, 10, true>(S, ray, P, st, nullptr, 0, live);
@@ -216,7 +222,8 @@ irgs_status irgs_server_create(const irgs_scene* scenes, int32_t n_scenes, int32
     irgs_server s = new (std::nothrow) irgs_server_s();
     if (!s) return IRGS_ERR_OOM;
     s->device = scenes[0]->device;
-    if (cudaSetDevice(s->device) != cudaSuccess) {
+    irgs::DeviceGuard dg;
+    if (!dg.set(s->device)) {
         delete s;
         return IRGS_ERR_CUDA;
     }
@@ -282,6 +289,7 @@ irgs_status irgs_server_step(irgs_server s, int32_t n_jobs, int32_t n_tiles, int
         if (jb.cam.tile_w <= 0 || jb.cam.tile_h <= 0 || jb.cam.width % jb.cam.tile_w || jb.cam.height % jb.cam.tile_h ||
             (int64_t)tl.first + tl.count > P)
             return IRGS_ERR_INVALID_ARG;
+        if ((jb.ray_o == nullptr) != (jb.ray_d == nullptr)) return IRGS_ERR_INVALID_ARG;
         if (tl.kind == IRGS_TILE_RENDER && (!jb.depth || !jb.opacity || (s->render.fc > 0 && !jb.feat)))
             return IRGS_ERR_INVALID_ARG;
         if (tl.kind == IRGS_TILE_GBUFFER && !jb.gbuffer) return IRGS_ERR_INVALID_ARG;
@@ -293,7 +301,8 @@ irgs_status irgs_server_step(irgs_server s, int32_t n_jobs, int32_t n_tiles, int
     int32_t* hdr = reinterpret_cast<int32_t*>(s->host_stage);
     hdr[0] = n_jobs;
     hdr[1] = n_tiles;
-    if (cudaSetDevice(s->device) != cudaSuccess) return IRGS_ERR_CUDA;
+    irgs::DeviceGuard dg;
+    if (!dg.set(s->device)) return IRGS_ERR_CUDA;
     cudaStream_t caller = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaEventRecord(s->ev_in, caller);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, s->ev_in, 0);
@@ -327,7 +336,8 @@ irgs_status irgs_server_step(irgs_server s, int32_t n_jobs, int32_t n_tiles, int
 
 irgs_status irgs_server_destroy(irgs_server s) {
     if (!s) return IRGS_OK;
-    cudaSetDevice(s->device);
+    irgs::DeviceGuard dg;
+    dg.set(s->device);
     cudaStreamSynchronize(s->stream);
     irgs::server_free(s);
     return IRGS_OK;

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kWaveThreads, 6) k_wave_trace(SceneView S, Tra
 // rounds 2 and 3; the rest run to completion. Per ray the rounds and their
 // arithmetic are march_forward's (per lane), so the results are the same.
 enum WaveRound { kWaveFirst = 0, kWaveNext = 1, kWaveLast = 2 };
-constexpr int kWaveStateF4 = 3;   // C[3], D, T, hit count, next key (2 words), next Morton index
+constexpr int kWaveStateF4 = 3;   // C[3], D, T, hit count, next key (2 words), next user index
 
 template <int K, bool SAVE, int MODE>
 __global__ void __launch_bounds__(kWaveThreads, 6) k_wave_round(
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kWaveThreads, 6) k_wave_round(
     const Ray ray = make_ray(ld3w(xg, p0 + i / St), mk3(d4.x, d4.y, d4.z));
     MarchState<K, 3> st;
     uint64_t last_key = depth_key(P.t_min, 0.f);
-    int32_t last_m = INT32_MAX;
+    int32_t last_u = INT32_MAX;
     if (MODE == kWaveFirst) {
         st.C[0] = st.C[1] = st.C[2] = 0.f;
         st.D = 0.f;
@@ -132,15 +132,15 @@ __global__ void __launch_bounds__(kWaveThreads, 6) k_wave_round(
         st.T = b.x;
         st.nh = __float_as_int(b.y);
         last_key = ((uint64_t)__float_as_uint(b.w) << 32) | (uint64_t)__float_as_uint(b.z);
-        last_m = __float_as_int(c.x);
+        last_u = __float_as_int(c.x);
     }
     int32_t* my_ids = SAVE ? ids + i * (int64_t)max_ids : nullptr;
     KBuffer<K, trace_threads<K>()> kb;
     kb.bind();
     bool ok = true, done = false;
     do {
-        ok &= collect_round(S, ray, P, last_key, last_m, kb);
-        done = blend_round<K, 3>(S, P, kb, st, my_ids, max_ids, last_key, last_m);
+        ok &= collect_round(S, ray, P, last_key, last_u, kb);
+        done = blend_round<K, 3>(S, P, kb, st, my_ids, max_ids, last_key, last_u);
     } while (MODE == kWaveLast && !done);
     if (!ok) atomicOr(S.status, kErrStackOverflow);
     if (done) {
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kWaveThreads, 6) k_wave_round(
         state[j * kWaveStateF4] = make_float4(st.C[0], st.C[1], st.C[2], st.D);
         state[j * kWaveStateF4 + 1] = make_float4(st.T, __int_as_float(st.nh), __uint_as_float((uint32_t)last_key),
                                                   __uint_as_float((uint32_t)(last_key >> 32)));
-        state[j * kWaveStateF4 + 2] = make_float4(__int_as_float(last_m), 0.f, 0.f, 0.f);
+        state[j * kWaveStateF4 + 2] = make_float4(__int_as_float(last_u), 0.f, 0.f, 0.f);
         flags[j] = 1u;
     }
 }

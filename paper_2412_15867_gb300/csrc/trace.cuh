@@ -167,14 +167,21 @@ __device__ __forceinline__ Node load_node(const Node* nodes, int i) {
     return nd;
 }
 
-// k-buffer of the K nearest hits after `last`, sorted by (key, Morton index),
+// User index of the surfel in Morton slot m (carried in its record's r2.w).
+__device__ __forceinline__ int32_t uid_of(const float4* rec, int32_t m) {
+    return __float_as_int(__ldg(&rec[(int64_t)m * kRecF4 + 2].w));
+}
+
+// k-buffer of the K nearest hits after `last`, sorted by (key, user index),
 // kept in shared memory as 16-byte entries {key (8 B), Morton index, alpha}:
 // slot j of thread t lives at [j * THREADS + t], so a warp touching the same
 // slot reads consecutive 16-byte words, and one shift step of the insertion
 // is one 128-bit load and one 128-bit store. Insertion shifts only the
 // entries behind the new one (hits mostly arrive front to back, so the shift
 // is usually short); the last entry is cached in registers for the cheap
-// "does it fit" test and the traversal's far bound.
+// "does it fit" test and the traversal's far bound. Two hits with the same
+// exact depth key are ordered by user index, which is read from the
+// record only on that (rare) tie.
 template <int K, int THREADS>
 struct KBuffer {
     static constexpr int kThreads = THREADS;
@@ -196,16 +203,17 @@ struct KBuffer {
     __device__ __forceinline__ uint64_t key_at(int j) const { return key_of(e[j * THREADS]); }
     __device__ __forceinline__ int32_t m_at(int j) const { return (int32_t)e[j * THREADS].z; }
     __device__ __forceinline__ float a_at(int j) const { return __uint_as_float(e[j * THREADS].w); }
-    __device__ __forceinline__ bool fits(uint64_t k, int32_t mm) const {
-        return cnt < K || k < tail_key || (k == tail_key && mm < tail_m);
+    // does the hit (k, user index u) belong before the full buffer's last entry?
+    __device__ __forceinline__ bool fits(uint64_t k, int32_t u, const float4* rec) const {
+        return cnt < K || k < tail_key || (k == tail_key && u < uid_of(rec, tail_m));
     }
-    // insert (k, mm, aa); the caller checked fits()
-    __device__ __forceinline__ void insert(uint64_t k, int32_t mm, float aa) {
+    // insert (k, Morton index mm, user index u, alpha aa); the caller checked fits()
+    __device__ __forceinline__ void insert(uint64_t k, int32_t mm, int32_t u, float aa, const float4* rec) {
         int j = (cnt < K ? cnt : K - 1) - 1;
         while (j >= 0) {
             const uint4 v = e[j * THREADS];
             const uint64_t kj = key_of(v);
-            if (!(k < kj || (k == kj && mm < (int32_t)v.z))) break;
+            if (!(k < kj || (k == kj && u < uid_of(rec, (int32_t)v.z)))) break;
             e[(j + 1) * THREADS] = v;
             --j;
         }
@@ -231,11 +239,12 @@ struct TraceStats {
     int rounds, nodes, leaves, inserts;
 };
 
-// Test surfel m against the ray and insert it into the k-buffer if it lies
-// strictly after (last_key, last_m) and before the buffer's last entry.
+// Test surfel m against the ray and insert it into the k-buffer if its
+// (key, user index) lies strictly after (last_key, last_u) and before the
+// buffer's last entry.
 template <class KB, bool STATS = false>
 __device__ __forceinline__ void leaf_insert(const SceneView& S, const Ray& ray, const TraceParams& P, int32_t m,
-                                            uint64_t last_key, int32_t last_m, KB& kb, float& t_hi,
+                                            uint64_t last_key, int32_t last_u, KB& kb, float& t_hi,
                                             TraceStats* ts = nullptr) {
     if (STATS) ts->leaves++;
     const float4* R = S.rec + (int64_t)m * kRecF4;
@@ -248,20 +257,21 @@ __device__ __forceinline__ void leaf_insert(const SceneView& S, const Ray& ray, 
     if (!surfel_hit<false>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a, nullptr, lo, hi)) return;
     const uint64_t key = depth_key(kh, kl);
     const bool past_min = kh > P.t_min || (kh == P.t_min && kl > 0.f);
-    const bool after = past_min && (key > last_key || (key == last_key && m > last_m));
+    const int32_t u = __float_as_int(r2.w);
+    const bool after = past_min && (key > last_key || (key == last_key && u > last_u));
     const bool before = kh < P.t_max || (kh == P.t_max && kl < 0.f);
-    if (after && before && kb.fits(key, m)) {
+    if (after && before && kb.fits(key, u, S.rec)) {
         if (STATS) ts->inserts++;
-        kb.insert(key, m, a);
+        kb.insert(key, m, u, a, S.rec);
         if (kb.full()) t_hi = key_depth(kb.tail_key);
     }
 }
 
-// One round: gather the K nearest hits strictly after (last_key, last_m).
+// One round: gather the K nearest hits strictly after (last_key, last_u).
 // Returns false if the traversal stack overflowed.
 template <class KB, bool STATS = false>
 __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray, const TraceParams& P,
-                                              uint64_t last_key, int32_t last_m, KB& kb,
+                                              uint64_t last_key, int32_t last_u, KB& kb,
                                               TraceStats* ts = nullptr) {
     int stack_n[kStackSize];
     float stack_t[kStackSize];
@@ -299,7 +309,7 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
                 const int k = __ffs(mask) - 1;
                 mask &= mask - 1u;
                 const int ck = k == 0 ? c[0] : k == 1 ? c[1] : k == 2 ? c[2] : c[3];
-                leaf_insert<KB, STATS>(S, ray, P, ~ck, last_key, last_m, kb, t_hi, ts);
+                leaf_insert<KB, STATS>(S, ray, P, ~ck, last_key, last_u, kb, t_hi, ts);
             }
         }
         hi_c = t_hi + tslack(t_hi);
@@ -368,7 +378,7 @@ constexpr unsigned kFullWarp = 0xffffffffu;
 // together (inactive lanes pass active = false).
 template <class KB, bool STATS = false>
 __device__ __forceinline__ bool collect_round_warp(const SceneView& S, const Ray& ray, const TraceParams& P,
-                                                   uint64_t last_key, int32_t last_m, KB& kb, bool active,
+                                                   uint64_t last_key, int32_t last_u, KB& kb, bool active,
                                                    TraceStats* ts = nullptr) {
     kb.clear();
     const int lane = threadIdx.x & 31;
@@ -397,7 +407,7 @@ __device__ __forceinline__ bool collect_round_warp(const SceneView& S, const Ray
             h[k] = active && c[k] != kNoChild && tn[k] <= tf[k] && tf[k] >= lo_c && tn[k] <= hi_c;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (h[k] && c[k] < 0) leaf_insert<KB, STATS>(S, ray, P, ~c[k], last_key, last_m, kb, t_hi, ts);
+            if (h[k] && c[k] < 0) leaf_insert<KB, STATS>(S, ray, P, ~c[k], last_key, last_u, kb, t_hi, ts);
         hi_c = t_hi + tslack(t_hi);
         // internal children some lane still needs; order them by the entry
         // depth seen by the first lane that needs each
@@ -461,11 +471,12 @@ struct MarchState {
 // Blend the round's buffered hits in order (Eq. 2, Eq. 8) until the
 // transmittance drops below T_min (the crossing hit included). Returns true
 // when the ray is done: terminated, or fewer than K hits were left; else
-// (last_key, last_m) move to the buffer's last entry for the next round.
+// (last_key, last_u) move to the buffer's last entry (its key and user
+// index) for the next round.
 template <int K, int FB, class KB>
 __device__ __forceinline__ bool blend_round(const SceneView& S, const TraceParams& P, const KB& kb,
                                             MarchState<K, FB>& st, int32_t* ids, int max_ids, uint64_t& last_key,
-                                            int32_t& last_m) {
+                                            int32_t& last_u) {
     bool done = false;
     for (int j = 0; j < kb.cnt && !done; ++j) {
         const float a = kb.a_at(j);
@@ -486,7 +497,7 @@ __device__ __forceinline__ bool blend_round(const SceneView& S, const TraceParam
             done = true;
         } else {
             last_key = kb.tail_key;
-            last_m = kb.tail_m;
+            last_u = uid_of(S.rec, kb.tail_m);
         }
     }
     return done;
@@ -506,18 +517,18 @@ __device__ __forceinline__ bool march_forward(const SceneView& S, const Ray& ray
     bool ok = true;
     if (S.n == 0) return ok;
     uint64_t last_key = depth_key(P.t_min, 0.f);
-    int32_t last_m = INT32_MAX;
+    int32_t last_u = INT32_MAX;
     KBuffer<K, trace_threads<K>()> kb;
     kb.bind();
     bool done = !live;
     while (WARP ? __any_sync(kFullWarp, !done) : !done) {
         if (STATS && !done) ts->rounds++;
         if (WARP)
-            ok &= collect_round_warp<decltype(kb), STATS>(S, ray, P, last_key, last_m, kb, !done, ts);
+            ok &= collect_round_warp<decltype(kb), STATS>(S, ray, P, last_key, last_u, kb, !done, ts);
         else
-            ok &= collect_round<decltype(kb), STATS>(S, ray, P, last_key, last_m, kb, ts);
+            ok &= collect_round<decltype(kb), STATS>(S, ray, P, last_key, last_u, kb, ts);
         if (done) continue;
-        done = blend_round<K, FB>(S, P, kb, st, ids, max_ids, last_key, last_m);
+        done = blend_round<K, FB>(S, P, kb, st, ids, max_ids, last_key, last_u);
     }
     return ok;
 }

@@ -201,15 +201,15 @@ __device__ __forceinline__ bool march_backward(const SceneView& S, const Ray& ra
     st.init();
     int nh = 0;
     uint64_t last_key = depth_key(P.t_min, 0.f);
-    int32_t last_m = INT32_MAX;
+    int32_t last_u = INT32_MAX;
     KBuffer<K, trace_threads<K>()> kb;
     kb.bind();
     bool ok = true, done = !live;
     while (WARP ? __any_sync(kFullWarp, !done) : !done) {
         if (WARP)
-            ok &= collect_round_warp(S, ray, P, last_key, last_m, kb, !done);
+            ok &= collect_round_warp(S, ray, P, last_key, last_u, kb, !done);
         else
-            ok &= collect_round(S, ray, P, last_key, last_m, kb);
+            ok &= collect_round(S, ray, P, last_key, last_u, kb);
         if (done) continue;
         for (int j = 0; j < kb.cnt && nh < nh_total; ++j, ++nh)
             backward_hit<FB>(S, ray, P, kb.m_at(j), st, Cf, Df, Tfin, gC, gD, gO, acc_rows, rows);
@@ -217,7 +217,7 @@ __device__ __forceinline__ bool march_backward(const SceneView& S, const Ray& ra
             done = true;
         } else {
             last_key = kb.tail_key;
-            last_m = kb.tail_m;
+            last_u = uid_of(S.rec, kb.tail_m);
         }
     }
     return ok;

@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(trace_threads<K>(), K <= 16 ? 6 : 4) k_trace_f
 // same; only which rays share a warp changes.
 enum RoundMode { kRoundFirst = 0, kRoundNext = 1, kRoundLast = 2 };
 
-// Between rounds: C[FB], D, T, hit count, next key (2 words), next Morton index.
+// Between rounds: C[FB], D, T, hit count, next key (2 words), next user index.
 template <int FB>
 struct RoundState {
     static constexpr int kF4 = (FB + 6 + 3) / 4;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(trace_threads<K>(), K <= 16 ? 6 : 4) k_trace_r
                              mk3(rd[3 * r], rd[3 * r + 1], rd[3 * r + 2]));
     MarchState<K, FB> st;
     uint64_t last_key = depth_key(P.t_min, 0.f);
-    int32_t last_m = INT32_MAX;
+    int32_t last_u = INT32_MAX;
     if (MODE == kRoundFirst || !live) {
 #pragma unroll
         for (int c = 0; c < FB; ++c) st.C[c] = 0.f;
@@ -90,15 +90,15 @@ __global__ void __launch_bounds__(trace_threads<K>(), K <= 16 ? 6 : 4) k_trace_r
         st.T = w[FB + 1];
         st.nh = __float_as_int(w[FB + 2]);
         last_key = ((uint64_t)__float_as_uint(w[FB + 4]) << 32) | (uint64_t)__float_as_uint(w[FB + 3]);
-        last_m = __float_as_int(w[FB + 5]);
+        last_u = __float_as_int(w[FB + 5]);
     }
     int32_t* my_ids = (ids != nullptr && live) ? ids + r * (int64_t)max_ids : nullptr;
     KBuffer<K, trace_threads<K>()> kb;
     kb.bind();
     bool ok = true, done = !live;
     do {
-        ok &= collect_round_warp(S, ray, P, last_key, last_m, kb, !done);
-        if (!done) done = blend_round<K, FB>(S, P, kb, st, my_ids, max_ids, last_key, last_m);
+        ok &= collect_round_warp(S, ray, P, last_key, last_u, kb, !done);
+        if (!done) done = blend_round<K, FB>(S, P, kb, st, my_ids, max_ids, last_key, last_u);
     } while (MODE == kRoundLast && __any_sync(kFullWarp, !done));
     if (!live) return;
     if (!ok) atomicOr(S.status, kErrStackOverflow);
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(trace_threads<K>(), K <= 16 ? 6 : 4) k_trace_r
         w[FB + 2] = __int_as_float(st.nh);
         w[FB + 3] = __uint_as_float((uint32_t)last_key);
         w[FB + 4] = __uint_as_float((uint32_t)(last_key >> 32));
-        w[FB + 5] = __int_as_float(last_m);
+        w[FB + 5] = __int_as_float(last_u);
 #pragma unroll
         for (int c = FB + 6; c < 4 * SW; ++c) w[c] = 0.f;
 #pragma unroll

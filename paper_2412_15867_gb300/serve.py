@@ -41,7 +41,7 @@ class Job(C.Structure):
     _fields_ = [("kind", C.c_int32), ("scene", C.c_int32), ("cam", Camera), ("n_diffuse", C.c_int32),
                 ("n_spec", C.c_int32), ("seed", C.c_uint64), ("env", C.c_void_p), ("env_h", C.c_int32),
                 ("env_w", C.c_int32), ("feat", C.c_void_p), ("depth", C.c_void_p), ("opacity", C.c_void_p),
-                ("gbuffer", C.c_void_p), ("rgb", C.c_void_p)]
+                ("gbuffer", C.c_void_p), ("rgb", C.c_void_p), ("ray_o", C.c_void_p), ("ray_d", C.c_void_p)]
 
 
 class Tile(C.Structure):
@@ -99,13 +99,29 @@ def camera_rays(cam: Camera, device="cuda:0", first: int = 0, count: int | None 
     return o, d
 
 
+def _check_rays(rays, P):
+    if rays is None:
+        return
+    o, d = rays
+    for t in (o, d):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+                and t.shape == (P, 3)):
+            raise ValueError("explicit rays must be contiguous float32 CUDA tensors [width x height, 3]")
+
+
 @dataclass
 class RenderRequest:
+    """Render `scene` from a look-at camera at `eye`, or, with `rays` =
+    (ray_o, ray_d) device tensors [width x height, 3], along those rays."""
     scene: int
     eye: tuple
     width: int
     height: int
     fov_deg: float = 60.0
+    rays: tuple | None = None
+
+    def __post_init__(self):
+        _check_rays(self.rays, self.pixels())
 
     def pixels(self) -> int:
         return self.width * self.height
@@ -113,6 +129,10 @@ class RenderRequest:
 
 @dataclass
 class RelightRequest:
+    """G-buffer of `scene` from the camera at `eye` (or along `rays`), then
+    the Monte Carlo rendering equation at its valid pixels with `spp`
+    samples. A caller-made `gbuffer` [width x height, 16] (the layout of
+    irgs_job) skips the G-buffer phase."""
     scene: int
     eye: tuple
     width: int
@@ -121,6 +141,15 @@ class RelightRequest:
     env: torch.Tensor
     seed: int
     fov_deg: float = 60.0
+    rays: tuple | None = None
+    gbuffer: torch.Tensor | None = None
+
+    def __post_init__(self):
+        _check_rays(self.rays, self.pixels())
+        g = self.gbuffer
+        if g is not None and not (isinstance(g, torch.Tensor) and g.is_cuda and g.dtype == torch.float32
+                                  and g.is_contiguous() and g.shape == (self.pixels(), 16)):
+            raise ValueError("gbuffer must be a contiguous float32 CUDA tensor [width x height, 16]")
 
     def pixels(self) -> int:
         return self.width * self.height
@@ -203,6 +232,9 @@ class Server:
                 if isinstance(req, RenderRequest):
                     h.out = {"feat": torch.empty((P, self.render_p.feat_count), device=dev),
                              "depth": torch.empty(P, device=dev), "opacity": torch.empty(P, device=dev)}
+                elif req.gbuffer is not None:
+                    h.out = {"gbuffer": req.gbuffer, "rgb": torch.empty((P, 3), device=dev)}
+                    h.phase = 1
                 else:
                     h.out = {"gbuffer": torch.empty((P, 16), device=dev), "rgb": torch.empty((P, 3), device=dev)}
             h.admitted = time.perf_counter()
@@ -225,6 +257,7 @@ class Server:
         j.scene = req.scene
         j.cam = make_camera(req.eye, req.width, req.height, fov_deg=req.fov_deg)
         ptr = lambda t: t.data_ptr() if t is not None else None
+        j.ray_o, j.ray_d = (ptr(req.rays[0]), ptr(req.rays[1])) if req.rays is not None else (None, None)
         if j.kind == JOB_RENDER:
             j.feat, j.depth, j.opacity = ptr(h.out["feat"]), ptr(h.out["depth"]), ptr(h.out["opacity"])
             j.gbuffer = j.rgb = j.env = None

@@ -19,7 +19,7 @@ def test_exports_every_declared_symbol(L):
     assert len(names) >= 10
     for n in names:
         assert hasattr(L, n), n
-    assert L.irgs_abi_version() == 2
+    assert L.irgs_abi_version() == 3
 
 
 def test_status_strings(L):
@@ -55,3 +55,29 @@ def test_python_binding_fails_loudly_without_cuda_tensors():
     z = torch.zeros((4, 3))
     with pytest.raises(ValueError):
         irgs.Scene(z, torch.zeros((4, 4)), torch.ones((4, 2)), torch.ones(4))
+
+
+@pytest.mark.gpu
+def test_entry_points_keep_the_callers_current_device(L):
+    """Entry points switch to their scene's device and switch back: the
+    caller's current device is the same after every call."""
+    import torch
+    import numpy as np
+    import synth
+    import paper_2412_15867_gb300 as irgs
+    dev0 = torch.cuda.current_device()
+    sc = synth.tiny_scene(seed=5, n=256)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    S = irgs.Scene(*(T(a) for a in sc.arrays()))
+    assert torch.cuda.current_device() == dev0
+    ro, rd = synth.look_at_rays(synth.tiny_camera(5), (0, 0, 0), 8, 8)
+    out = irgs.trace_forward(S, T(ro), T(rd), irgs.TraceParams(k=8, feat_count=3))
+    assert torch.cuda.current_device() == dev0
+    irgs.trace_backward(S, T(ro), T(rd), irgs.TraceParams(k=8, feat_count=3), out, torch.ones_like(out["feat"]))
+    assert torch.cuda.current_device() == dev0
+    S.update()
+    S.refit()
+    assert S.status() == 0
+    assert torch.cuda.current_device() == dev0
+    S.close()
+    assert torch.cuda.current_device() == dev0

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from tests.gpu_util import assert_forward_parity, dev, make_scene
+from tests.gpu_util import assert_forward_parity, dev, make_scene, oracle_reference
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -52,7 +52,7 @@ def test_refit_traces_equal_fresh_build_and_oracle(step):
         assert S.status() == 0 and F.status() == 0
         for k in ("feat", "depth", "opacity", "n_hits", "hit_ids"):
             assert torch.equal(a[k], b[k]), (flags, k)
-    ref = oracle.trace(new, ro, rd, opar(p), max_ids=64)
+    ref = oracle_reference(new, ro, rd, opar(p), max_ids=64)
     # at step 5 some surfels grow ~100x, beyond the sizes the near-tie margin
     # (2e-8 in depth) is set for, so two hits can swap order unflagged; the
     # blended values still meet the bar

@@ -2,13 +2,15 @@
 
 Each request's result must be the same whether it runs alone or in a mix
 (bitwise: the per-ray and per-point computations do not depend on what
-shares the launch), and the serving kernel must agree with the standalone
-entry points on the same rays / G-buffer (which are oracle-checked)."""
+shares the launch), the serving kernel must agree with the standalone entry
+points on the same rays / G-buffer, and served results are compared element
+by element with the FP64 oracle on host-made rays and G-buffers."""
 import math
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 torch = pytest.importorskip("torch")
@@ -16,19 +18,20 @@ pytestmark = pytest.mark.gpu
 
 import paper_2412_15867_gb300 as irgs  # noqa: E402
 from paper_2412_15867_gb300 import serve  # noqa: E402
-from tests.gpu_util import dev, make_scene  # noqa: E402
+from tests.gpu_util import assert_forward_parity, dev, make_scene, oracle_reference  # noqa: E402
+
+SCENE_ARGS = [(20_000, 401), (50_000, 402)]
+ENV_ARGS = dict(seed=403, height=64, width=128)
 
 
 @pytest.fixture(scope="module")
 def scenes():
-    a = make_scene(irgs, synth.object_scene(n=20_000, seed=401))
-    b = make_scene(irgs, synth.object_scene(n=50_000, seed=402))
-    return [a, b]
+    return [make_scene(irgs, synth.object_scene(n=n, seed=s)) for n, s in SCENE_ARGS]
 
 
 @pytest.fixture(scope="module")
 def env():
-    return dev(synth.env_map(seed=403, height=64, width=128))
+    return dev(synth.env_map(**ENV_ARGS))
 
 
 @pytest.mark.parametrize("tile", [(4, 8), (8, 4), (1, 1)])
@@ -148,4 +151,85 @@ def test_poisson_driver_reports_latency(scenes, env):
     hs, wall, rays = serve.run_poisson(srv, make, rate=200.0, duration=0.5, warmup=0.1)
     st = serve.latency_stats(hs)
     assert st["n"] > 20 and st["p99_ms"] >= st["p50_ms"] > 0 and rays > 0
+    srv.close()
+
+
+def opar(p):
+    return oracle.Params(alpha_min=p.alpha_min, alpha_max=p.alpha_max, T_min=p.T_min, t_min=p.t_min,
+                         t_max=p.t_max, feat_offset=p.feat_offset, feat_count=p.feat_count)
+
+
+def test_served_mix_matches_the_oracle(scenes, env):
+    """One served mix, every served result checked element by element
+    against the FP64 oracle on the same host-made inputs:
+      * two render requests on two scenes with their own rays (ragged counts,
+        several tiles each): feat / depth / opacity per ray (Eq. 8) at the
+        forward bars, flagged rays against their admissible outcomes;
+      * a relight request whose G-buffer is traced from its own rays: the
+        served G-buffer against the Eq. 9 normalisation of the oracle's
+        material trace (x = o + (D/O) d, normal, albedo, roughness, w_o,
+        valid = O > 0.5) on unflagged pixels;
+      * a relight request that shades a host-made G-buffer: its radiance
+        against oracle.shade with the request's seed and its pixel indices as
+        the random keys (Eq. 13-15), at the shading bars;
+    with camera-driven requests of both kinds sharing the launches."""
+    sc_np = [synth.object_scene(n=n, seed=s) for n, s in SCENE_ARGS]
+    env_np = synth.env_map(**ENV_ARGS)
+    cams = synth.hemisphere_cameras(4, seed=411)
+    r0 = synth.camera_batch_rays(cams[:1], 37, 29)                 # 1,073 rays
+    r1 = synth.camera_batch_rays(cams[1:2], 41, 23)                # 943 rays
+    rg = synth.camera_batch_rays(cams[2:3], 32, 25)                # 800 rays
+    P_sh = 45
+    x, n, a, r, wo = synth.gbuffer_points(P_sh, seed=412)
+    gb = np.zeros((P_sh, 16), np.float32)
+    gb[:, 0:3], gb[:, 3:6], gb[:, 6:9], gb[:, 9], gb[:, 10:13] = x, n, a, r, wo
+    gb[:, 13] = 1.0
+    gb[:, 14] = 1.0
+    req = [serve.RenderRequest(0, (0, 0, 4), r0[0].shape[0], 1, rays=(dev(r0[0]), dev(r0[1]))),
+           serve.RenderRequest(1, (0, 0, 4), r1[0].shape[0], 1, rays=(dev(r1[0]), dev(r1[1]))),
+           serve.RelightRequest(1, (0, 0, 4), rg[0].shape[0], 1, spp=6, env=env, seed=91,
+                                rays=(dev(rg[0]), dev(rg[1]))),
+           serve.RelightRequest(0, (0, 0, 4), P_sh, 1, spp=10, env=env, seed=92, gbuffer=dev(gb))]
+    mix = _mixed_requests(env)
+    srv = serve.Server(scenes, max_tiles=1024, step_rays=1 << 16, tile_px=512)
+    hs = [srv.submit(q) for q in (mix[0], req[0], mix[1], req[1], req[2], mix[3], req[3], mix[2])]
+    srv.run_until_idle()
+    torch.cuda.synchronize()
+    assert srv.steps > 2 and all(h.done > 0 for h in hs)
+    assert all(S.status() == 0 for S in scenes)
+    h0, h1, hg, hsh = hs[1], hs[3], hs[4], hs[6]
+    # render requests
+    for h, (ro, rd), sc in ((h0, r0, sc_np[0]), (h1, r1, sc_np[1])):
+        ref = oracle_reference(sc, ro, rd, opar(srv.render_p))
+        st = assert_forward_parity(h.out, ref, sc.features, max_flagged=0.02)
+        print("render", st)
+    # relight G-buffer from the request's rays
+    ro, rd = rg
+    mp = srv.render_p.with_(feat_offset=3, feat_count=7)
+    ref = oracle.trace(sc_np[1], ro, rd, opar(mp))
+    g = hg.out["gbuffer"].cpu().numpy().astype(np.float64)
+    O = ref["opacity"]
+    ok = ((ref["flags"] & oracle.FORWARD_FLAGS) == 0) & (np.abs(O - 0.5) > 1e-3)
+    assert ok.mean() > 0.95
+    valid = O > 0.5
+    np.testing.assert_array_equal(g[ok, 13] > 0.5, valid[ok])
+    v = ok & valid
+    assert v.sum() > 100
+    C = ref["feat"]
+    xr = ro + rd * (ref["depth"] / np.where(valid, O, 1))[:, None]
+    nr = C[:, 4:7] / np.linalg.norm(C[:, 4:7], axis=1, keepdims=True).clip(1e-30)
+    np.testing.assert_allclose(g[v, 0:3], xr[v], rtol=0, atol=5e-4)
+    np.testing.assert_allclose(g[v, 6:9], C[v, 0:3] / O[v, None], rtol=0, atol=3e-4)
+    np.testing.assert_allclose(g[v, 9], C[v, 3] / O[v], rtol=0, atol=3e-4)
+    wide = v & (np.linalg.norm(C[:, 4:7], axis=1) > 0.1)
+    np.testing.assert_allclose(g[wide, 3:6], nr[wide], rtol=0, atol=3e-3)
+    np.testing.assert_allclose(g[v, 10:13], -rd[v], rtol=0, atol=0)
+    np.testing.assert_allclose(g[v, 14], O[v], rtol=0, atol=1e-4)
+    # relight shading of the host-made G-buffer
+    sref = oracle.shade(sc_np[0], x, n, a, r, wo, env_np, 5, 5, 92, opar(srv.shade_p))
+    rgb = hsh.out["rgb"].cpu().numpy().astype(np.float64)
+    err = np.abs(rgb - sref["rgb"]).max(1) / np.maximum(1.0, np.abs(sref["rgb"]).max(1))
+    clean = sref["flags"] == 0
+    assert clean.mean() > 0.6 and np.all(err[clean] <= 1e-4), (err, sref["flags"])
+    assert (err <= 1e-4).mean() >= 0.9, err
     srv.close()

@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2412_15867_gb300 as irgs  # noqa: E402
-from tests.gpu_util import assert_forward_parity, dev, make_scene  # noqa: E402
+from tests.gpu_util import assert_forward_parity, dev, forward_errors, make_scene, oracle_reference  # noqa: E402
 
 
 def opar(p):
@@ -36,8 +36,8 @@ def test_tiny_config_all_rays_match_oracle():
     ro, rd = synth.look_at_rays(synth.tiny_camera(1000), (0, 0, 0), 64, 64)
     p = irgs.TraceParams(k=8, feat_count=3)
     _, out = run(sc, ro, rd, p, ids=64)
-    ref = oracle.trace(sc, ro, rd, opar(p), max_ids=64)
-    st = assert_forward_parity(out, ref, sc.features, check_ids=True)
+    ref = oracle_reference(sc, ro, rd, opar(p), max_ids=64)
+    st = assert_forward_parity(out, ref, sc.features, check_ids=True, max_flagged=0.02)
     assert (out["n_hits"].cpu().numpy() > 0).mean() > 0.5
     print(st)
 
@@ -48,7 +48,7 @@ def test_object_scene_ragged_batches(n, cams, w, h):
     ro, rd = synth.camera_batch_rays(synth.hemisphere_cameras(cams, seed=1001), w, h)
     p = irgs.TraceParams(k=16, feat_offset=0, feat_count=10)
     _, out = run(sc, ro, rd, p, ids=32)
-    ref = oracle.trace(sc, ro, rd, opar(p), max_ids=32)
+    ref = oracle_reference(sc, ro, rd, opar(p), max_ids=32)
     assert_forward_parity(out, ref, sc.features, check_ids=True)
 
 
@@ -73,7 +73,7 @@ def test_feature_channel_ranges():
     for off, cnt in ((0, 3), (3, 4), (6, 1), (0, 10), (9, 1), (0, 0)):
         p = irgs.TraceParams(k=16, feat_offset=off, feat_count=cnt)
         out = irgs.trace_forward(S, dev(ro), dev(rd), p)
-        ref = oracle.trace(sc, ro, rd, opar(p))
+        ref = oracle_reference(sc, ro, rd, opar(p))
         assert_forward_parity(out, ref)
 
 
@@ -119,7 +119,7 @@ def test_edge_cases_empty_single_and_duplicates():
     q = frame_to_quat(t_u[None], t_v[None], nrm[None])[0]
     one = scene([0, 0, 0], q, [0.3, 0.2], [0.9], [0.5, 0.25, 1.0])
     _, out = run(one, ro, rd, p)
-    ref = oracle.trace(one, ro, rd, opar(p))
+    ref = oracle_reference(one, ro, rd, opar(p))
     assert_forward_parity(out, ref)
     assert out["n_hits"].sum().item() > 10
     # many exact duplicates (equal Morton codes, equal depths: ties by user index)
@@ -128,11 +128,23 @@ def test_edge_cases_empty_single_and_duplicates():
     dup = base.subset(idx)
     dup.features[:] = np.random.default_rng(0).uniform(0, 1, size=dup.features.shape).astype(np.float32)
     dup.scales[:] *= 4
-    _, out = run(dup, ro, rd, p.with_(T_min=0.0), )
-    ref = oracle.trace(dup, ro, rd, opar(p.with_(T_min=0.0)), max_ids=8)
-    f = out["feat"].cpu().numpy()
-    # exact-tie rays are flagged; where unflagged the results agree
-    assert_forward_parity(out, ref)
+    _, out = run(dup, ro, rd, p.with_(T_min=0.0), ids=64)
+    ref = oracle_reference(dup, ro, rd, opar(p.with_(T_min=0.0)), max_ids=64)
+    # runs of 40 tied hits are too many orders to list (unresolved), but
+    # copies have bitwise-equal records, so their keys tie exactly on the GPU
+    # as in FP64 and the user index decides: on rays whose only near-equal
+    # depths are between copies of one surfel, the result is the definition's
+    assert_forward_parity(out, ref, max_unresolved=1.0)
+    tau, ids = ref["tau"], ref["ids"]
+    near = np.abs(np.diff(tau, axis=1)) < 1e-6
+    same = (ids[:, 1:] // 40) == (ids[:, :-1] // 40)
+    only_copies = ~np.any(near & ~same & (ids[:, 1:] >= 0), axis=1)
+    assert only_copies.mean() > 0.9
+    err = forward_errors(out, ref)
+    assert np.all(err[only_copies] <= 1e-4), err[only_copies].max()
+    gid = out["hit_ids"].cpu().numpy()
+    assert np.array_equal(gid[only_copies], ids[only_copies])
+    assert (out["n_hits"].cpu().numpy()[only_copies] > 40).any()
     # zero rays
     S = make_scene(irgs, base)
     z = torch.zeros((0, 3), device="cuda:0")
@@ -147,7 +159,7 @@ def test_ray_interval_and_parameter_validation():
     for p in (irgs.TraceParams(k=8, t_min=2.5), irgs.TraceParams(k=16, t_min=1.0, t_max=3.0),
               irgs.TraceParams(k=8, alpha_max=1.0, T_min=0.0), irgs.TraceParams(k=8, alpha_min=0.05)):
         out = irgs.trace_forward(S, dev(ro), dev(rd), p)
-        ref = oracle.trace(sc, ro, rd, opar(p))
+        ref = oracle_reference(sc, ro, rd, opar(p))
         assert_forward_parity(out, ref)
     with pytest.raises(irgs.IrgsError):
         irgs.trace_forward(S, dev(ro), dev(rd), irgs.TraceParams(k=7))
@@ -204,26 +216,38 @@ def test_lbvh_structure_invariants():
 
 @pytest.mark.slow
 def test_camera_config_full_size_sampled():
-    """300k-surfel object scene, 100 cameras x 800x800 = 64M rays in 8x4 pixel
-    tiles, k = 16, 10 channels, warp-coherent traversal: the full batch in the
-    benchmark's launch configuration,
-    2,048 sampled rays checked against the oracle, invariants on all rays."""
+    """300k-surfel object scene, 100 cameras x 800x800 = 64M rays in 4x8 pixel
+    tiles, k = 16, 10 channels, warp-coherent traversal with 96 saved hit ids:
+    the full batch in the benchmark's launch configuration. Checked against
+    the oracle element by element on 2,048 random rays, the 256 rays with the
+    most blended hits and 256 rays that need four or more k-buffer rounds
+    (the compacted rounds' run-to-completion launch); invariants on all rays;
+    at most 2% of the sampled rays may carry an ambiguity flag."""
     sc = synth.object_scene(n=300_000, seed=1001)
     cams = synth.hemisphere_cameras(100, seed=1001)
-    ro, rd = synth.camera_batch_rays(cams, 800, 800, tile=(8, 4))
+    ro, rd = synth.camera_batch_rays(cams, 800, 800, tile=(4, 8))
     p = irgs.TraceParams(k=16, feat_count=10)
     S = make_scene(irgs, sc)
-    out = irgs.trace_forward(S, dev(ro), dev(rd), p)
+    out = irgs.trace_forward(S, dev(ro), dev(rd), p, max_hit_ids=96)
     torch.cuda.synchronize()
     assert S.status() == 0
     o = out["opacity"]
     assert torch.isfinite(out["feat"]).all() and (o >= 0).all() and (o <= 1).all()
+    nh_all = out["n_hits"]
     rng = np.random.default_rng(7)
-    idx = np.sort(rng.choice(ro.shape[0], 2048, replace=False))
-    ref = oracle.trace(sc, ro[idx], rd[idx], opar(p))
-    sub = {k: v[torch.from_numpy(idx).cuda()] for k, v in out.items()}
-    st = assert_forward_parity(sub, ref, sc.features)
-    print(st, "mean hits", float(out["n_hits"].float().mean()))
+    rand = rng.choice(ro.shape[0], 2048, replace=False)
+    top = torch.topk(nh_all, 256).indices.cpu().numpy()
+    deep = torch.nonzero(nh_all > 48).flatten().cpu().numpy()
+    assert deep.size > 256
+    deep = rng.choice(deep, 256, replace=False)
+    for name, idx in (("random", rand), ("most hits", top), ("4+ rounds", deep)):
+        idx = np.unique(idx)
+        ref = oracle_reference(sc, ro[idx], rd[idx], opar(p), max_ids=96)
+        ti = torch.from_numpy(idx).cuda()
+        sub = {k: v[ti] for k, v in out.items()}
+        st = assert_forward_parity(sub, ref, sc.features, check_ids=True,
+                                   max_flagged=0.02 if name == "random" else 0.1)
+        print(name, st, "mean hits", float(sub["n_hits"].float().mean()))
 
 
 def test_traversal_modes_give_identical_results():

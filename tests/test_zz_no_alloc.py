@@ -45,9 +45,16 @@ def _noalloc_build(L, sc, alpha_min=1 / 255):
     boxes = torch.empty((max(n, 1), 6), dtype=torch.float32, device="cuda:0")
     s = _lib.Surfels(means.data_ptr(), quats.data_ptr(), scales.data_ptr(), opac.data_ptr(), None, n, 0)
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    dev0 = torch.cuda.current_device()
     st = L.irgs_build_lbvh_noalloc(C.byref(s), alpha_min, C.c_void_p(perm.data_ptr()),
                                    C.c_void_p(keys.data_ptr()), C.c_void_p(nodes.data_ptr()),
                                    C.c_void_p(boxes.data_ptr()), stream)
+    assert torch.cuda.current_device() == dev0
+    if st == 0:
+        bits = C.c_uint32(99)
+        # the build's device-side status word (0: the hierarchy passed its bounds)
+        assert L.irgs_build_lbvh_noalloc_status(0, stream, C.byref(bits)) == 0 and bits.value == 0
+        assert torch.cuda.current_device() == dev0
     torch.cuda.synchronize()
     return st, (perm.cpu().numpy()[:n], keys.cpu().numpy().view(np.uint32)[:n], nodes.cpu().numpy(),
                 boxes.cpu().numpy()[:n])
