@@ -39,10 +39,24 @@ METRIC = "Mrays/s traced+composited (fwd, fwd+bwd) vs roofline; served p50/p99 l
 UNIT = "Mrays/s"
 WORKLOAD = "camera rays at scene scale: 300k-surfel object scene, 100 cameras x 800x800, k=16, 10 channels"
 
-# FP32 pipe of one GB300: 152 SMs x 128 FP32 lanes x 2 flops (FMA) at the
-# 2070 MHz maximum SM clock.
-SMS, LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP32_PEAK_TFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# Nominal FP32 pipe width per SM (for the note beside the measured peak): 128
+# FP32 lanes x 2 flops per FMA. The peak the fractions use is measured on
+# the device by the library's own FMA-chain probe (irgs_probe_fma).
+LANES = 128
+HBM_FALLBACK_GBS = 6800.0
+
+
+def measured_peaks():
+    """HBM copy bandwidth from MEASURED_PEAKS.json (driver-written), else the
+    fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "hbm_source": "of measured (MEASURED_PEAKS.json copy bandwidth)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": HBM_FALLBACK_GBS, "hbm_source": "of fallback (6.8 TB/s)"}
+
 
 # DRAM traffic per launch of the dominant kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) scaled per ray; keyed by
@@ -86,8 +100,11 @@ def parse():
     ap.add_argument("--mc-points", type=int, default=640_000)
     ap.add_argument("--mc-surfels", type=int, default=1_000_000)
     ap.add_argument("--mc-reps", type=int, default=2)
-    ap.add_argument("--serve-seconds", type=float, default=8.0)
-    ap.add_argument("--serve-warmup", type=float, default=2.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="measured window at the headline rate")
+    ap.add_argument("--serve-warmup", type=float, default=10.0)
+    ap.add_argument("--sweep-seconds", type=float, default=10.0, help="window of each sweep point")
+    ap.add_argument("--sweep-warmup", type=float, default=2.0)
+    ap.add_argument("--serve-burst", type=int, default=240, help="requests of the saturation burst")
     ap.add_argument("--cpu-rays", type=int, default=20480, help="oracle sample for cpu_baseline")
     ap.add_argument("--ref-rays", type=int, default=1024, help="oracle rays per reference step")
     return ap.parse_args()
@@ -164,6 +181,71 @@ def algorithmic_flops(nh, k, n_surfels, F, backward=False, saved_hits=0):
         rounds = torch.where(nh > saved_hits, rounds, torch.zeros_like(rounds))
     f = nh * per_hit * (3 if backward else 1) + rounds * depth * 40
     return float(f.sum())
+
+
+def trace_bytes(R, N, fc, backward=False):
+    """Algorithmic bytes of one trace launch: per ray its origin and
+    direction (24 B), fc + 2 outputs and the hit count; the scene once
+    (64-B record + fc channels per surfel, 64-B nodes). The backward adds the
+    upstream gradients and the forward outputs it reads per ray, and one
+    read-modify-write of the 10 + fc gradient floats per surfel."""
+    b = R * (24 + 4 * (fc + 2) + 4) + N * (64 + 4 * fc) + max(N - 1, 0) * 64
+    if backward:
+        b += R * 4 * (fc + 2) * 2 + N * 4 * (10 + fc) * 2
+    return float(b)
+
+
+def per_ray_flops(nh, k, n_surfels, F, backward=False, saved_hits=0):
+    """Mean algorithmic flops per ray of a sample of per-ray hit counts."""
+    return algorithmic_flops(nh, k, n_surfels, F, backward=backward, saved_hits=saved_hits) / max(nh.numel(), 1)
+
+
+def roof_entry(ms, rays, flops, nbytes, peak_tflops, hbm_gbs, **extra):
+    """Throughput against the roofline min(HBM / bytes, FP32 peak / flops)
+    of a launch (or step) of `rays` rays taking `ms` milliseconds."""
+    t = ms * 1e-3
+    mrays = rays / t / 1e6
+    alu = peak_tflops * 1e12 / (flops / rays) / 1e6
+    hbm = hbm_gbs * 1e9 / (nbytes / rays) / 1e6
+    roof = min(alu, hbm)
+    e = {"mrays_s": mrays, "ms": ms, "rays": int(rays), "flops_per_ray": flops / rays,
+         "bytes_per_ray": nbytes / rays, "achieved_tflops": flops / t / 1e12, "achieved_gbs": nbytes / t / 1e9,
+         "alu_bound_mrays_s": alu, "hbm_bound_mrays_s": hbm, "bound": "alu" if alu <= hbm else "hbm",
+         "roofline_mrays_s": roof, "frac": mrays / roof}
+    e.update(extra)
+    return e
+
+
+def fp32_probe(L, dev, index, iters=100_000, launches=10):
+    """FP32 peak measured with the library's FMA-chain probe: CUDA events
+    around `launches` launches, SM clocks sampled meanwhile."""
+    import ctypes as C
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    sp = C.c_void_p(stream.cuda_stream)
+    fl = C.c_double()
+    for _ in range(2):
+        if L.irgs_probe_fma(iters // 10, sp, C.byref(fl)) != 0:
+            raise RuntimeError("irgs_probe_fma failed")
+    torch.cuda.synchronize()
+    clk = ClockSampler(index)
+    clk.start()
+    time.sleep(0.3)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(launches):
+        L.irgs_probe_fma(iters, sp, C.byref(fl))
+    b.record(stream)
+    torch.cuda.synchronize()
+    c = clk.stop()
+    ms = a.elapsed_time(b)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    tflops = launches * fl.value / (ms * 1e-3) / 1e12
+    return {"tflops": tflops, "sm_mhz": c.get("sm_mhz"), "sms": sms, "launch_ms": ms / launches,
+            "flops_per_launch": fl.value,
+            "nominal_at_max_clock_tflops": sms * LANES * 2 * (c.get("sm_max_mhz") or 0) * 1e6 / 1e12,
+            "how": f"{launches} launches of irgs_probe_fma ({sms} SMs x 8 blocks x 256 threads, 8 independent "
+                   "FMA chains per thread), CUDA events; clocks sampled during the launches"}
 
 
 def run_ours(args):
@@ -311,6 +393,18 @@ def run_ours(args):
                   "ms_per_image": r_ms, "mpix_s": args.res * args.res / (r_ms * 1e-3) / 1e6,
                   "traced_ms_per_image": fwd_ms / args.cams}
 
+    # ---- measured peaks: the FP32 pipe by the library's FMA-chain probe (at
+    # the probe's clock, scaled to the timed region's median SM clock), HBM
+    # from the driver's copy measurement
+    peaks = measured_peaks()
+    probe = fp32_probe(L, dev, local)
+    peak = probe["tflops"]
+    if clk.get("sm_mhz") and probe.get("sm_mhz"):
+        peak = probe["tflops"] * clk["sm_mhz"] / probe["sm_mhz"]
+    hbm = peaks["hbm_gbs"]
+    peak_note = (f"of measured: FMA-chain probe {probe['tflops']:.2f} TFLOP/s at {probe['sm_mhz']} MHz median SM "
+                 f"clock, scaled to the timed region's {clk.get('sm_mhz')} MHz ({probe['sms']} SMs)")
+
     # ---- roofline of the dominant kernel (by time)
     nh = out["n_hits"]
     if bwd_ms >= fwd_ms:
@@ -319,7 +413,7 @@ def run_ours(args):
         src = ["trace.cuh", "trace_bwd.cuh", "trace_bwd.cu", "common.cuh", "scene.cu"]
     else:
         # the forward pass: for batches of 2^20 rays or more its compacted
-        # k-buffer rounds (4 launches) and the compaction between them
+        # k-buffer rounds and the compaction between them
         kname, kms = "k_trace_round<16,10,*>", fwd_ms
         flops = algorithmic_flops(nh, 16, sc.n, F)
         src = ["trace.cuh", "trace_fwd.cu", "common.cuh", "scene.cu"]
@@ -327,11 +421,49 @@ def run_ours(args):
     khash = _kernel_hash(src)
     tr = TRAFFIC.get(kname)
     traffic = tr["bytes_per_ray"] * R if (tr and tr.get("bytes_per_ray") and tr.get("src_hash") == khash) else None
-    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "flops_per_launch": flops, "launch_ms": kms,
-                "peak_note": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2070 MHz max SM clock",
-                "hbm_bound_mrays_s": None}
+
+    # ---- work actually done per camera ray (diagnostic counters of the
+    # forward march on one camera's rays): the gap to the roofline splits
+    # into extra work (nodes and candidates beyond the algorithmic count)
+    # and the rate at which that work runs
+    R1 = args.res * args.res
+    ws = irgs.trace_stats(scene, ro[:R1], rd[:R1], p).double().mean(0).tolist()
+    nh1 = float(nh[:R1].double().mean())
+    # per node visit: 4 child slab tests (6 FMA, 6 min/max, 2 three-way) ~ 20
+    # flops each; per surfel test 45; per composited hit the blend
+    work_flops_ray = ws[1] * 4 * 20 + ws[2] * 45 + nh1 * (2 * (F + 2) + 3)
+    alg_flops_ray = flops / R
+    work = {"sample": f"camera 0 ({R1} rays)", "rounds_per_ray": ws[0], "nodes_per_ray": ws[1],
+            "candidates_per_ray": ws[2], "inserts_per_ray": ws[3], "hits_per_ray": nh1,
+            "algorithmic_flops_per_ray": alg_flops_ray, "work_flops_per_ray": work_flops_ray,
+            "work_over_algorithmic": work_flops_ray / alg_flops_ray,
+            "work_frac": work_flops_ray * R / (kms * 1e-3) / 1e12 / peak,
+            "note": "work_frac = the counted work (4 x 20 flops per node visit, 45 per surfel test, the blend per "
+                    "hit) per second over the FP32 peak: how busy the FP32 pipe would be if every counted test "
+                    "were needed; frac / work_frac = algorithmic / counted work"}
+    roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                "flops_per_launch": flops, "launch_ms": kms, "peak_note": peak_note,
+                "hbm_bound_mrays_s": hbm * 1e9 / (trace_bytes(R, sc.n, F) / R) / 1e6,
+                "work_frac": work["work_frac"]}
+
+    # ---- the configurations' table: Mrays/s and roofline fraction each
+    configs = {}
+    if rank == 0:
+        configs["C0"] = tiny_leg(args, dev, peak, hbm)
+    bf = trace_bytes(R, sc.n, F)
+    configs["C1"] = {
+        "workload": WORKLOAD,
+        "fwd": roof_entry(fwd_ms, R, algorithmic_flops(nh, 16, sc.n, F), bf, peak, hbm),
+        "fwd_bwd": roof_entry(fwd_ms + bwd_ms, R,
+                              algorithmic_flops(nh, 16, sc.n, F)
+                              + algorithmic_flops(nh, 16, sc.n, F, backward=True, saved_hits=args.saved_hits),
+                              bf + trace_bytes(R, sc.n, F, backward=True), peak, hbm),
+        "step": roof_entry(ms_per_step, R,
+                           algorithmic_flops(nh, 16, sc.n, F)
+                           + algorithmic_flops(nh, 16, sc.n, F, backward=True, saved_hits=args.saved_hits),
+                           bf + trace_bytes(R, sc.n, F, backward=True), peak, hbm,
+                           note="the timed step: rebuild + forward + backward")}
 
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
@@ -409,7 +541,8 @@ def run_ours(args):
     # ---- Monte Carlo rendering equation configuration
     mc = None
     if not args.no_mc and rank == 0:
-        mc = mc_leg(args, dev)
+        mc = mc_leg(args, dev, peak, hbm, cpu=not args.no_cpu)
+        configs["C2"] = mc.pop("configs")
 
     # ---- serving mix (continuous batching vs one request at a time)
     serving = None
@@ -417,6 +550,7 @@ def run_ours(args):
         del out, grads, ro, rd, gf, gd, go
         torch.cuda.empty_cache()
         serving = serve_leg(args, dev)
+        configs["C4"] = serving_roofline(serving, configs, peak, hbm)
 
     # ---- oracle on the host cores, bounded sample of the same workload
     cpu = None
@@ -441,14 +575,17 @@ def run_ours(args):
             "mean_hits_per_ray": float(nh.float().mean()), "max_hits_per_ray": int(nh.max()),
             "replayed_ray_frac": float((nh > args.saved_hits).float().mean()) if args.saved_hits > 0 else 1.0,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk, "raster": raster, "mc": mc, "serving": serving,
+            "clocks": clk, "fp32_probe": probe, "hbm_gbs": {"value": hbm, "source": peaks["hbm_source"]},
+            "work": work, "configs": configs, "raster": raster, "mc": mc, "serving": serving,
         }
+        if cpu is not None:
+            configs["C1"]["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def mc_leg(args, dev):
+def mc_leg(args, dev, peak, hbm, cpu=True):
     """Monte Carlo rendering equation at G-buffer points (Eq. 13-15): object
     scene of --mc-surfels surfels (1M), --mc-points points (640k) x (32
     cosine + 32 GGX) secondary rays, 512x256 environment, k=16. Times the
@@ -510,11 +647,47 @@ def mc_leg(args, dev):
     ev[1].record(stream)
     torch.cuda.synchronize()
     relight_ms = ev[0].elapsed_time(ev[1]) / reps
+
+    # hits per secondary ray, for the algorithmic flop counts: the rays the
+    # estimators draw for the first 4096 points (the library's own samplers),
+    # traced with the same parameters
+    Ps, N2 = 4096, sc2.n
+    xs = g2[0][:Ps].repeat_interleave(64, 0)
+    dsh, vsh = irgs.shade_sample_rays(g2[1][:Ps], g2[3][:Ps], g2[4][:Ps], 32, 32, 2024)
+    vm = vsh.bool()
+    nh_sh = irgs.trace_forward(S2, xs[vm].contiguous(), dsh[vm].contiguous(), ps)["n_hits"]
+    drl, _, vrl = irgs.relight_sample_rays(E, Ps, 64, 2025)
+    vr = vrl.bool()
+    nh_rl = irgs.trace_forward(S2, xs[vr].contiguous(), drl[vr].contiguous(), pr)["n_hits"]
+    torch.cuda.synchronize()
+    vfrac, vfrac_rl = float(vm.float().mean()), float(vr.float().mean())
+    f_fwd = per_ray_flops(nh_sh, 16, N2, 3)
+    f_bwd = per_ray_flops(nh_sh, 16, N2, 3, backward=True, saved_hits=64)
+    f_rl = per_ray_flops(nh_rl, 16, N2, 7)
+    SAMPLE_FLOPS = 150          # direction, BRDF and estimator terms per sample
+    env_b = 512 * 256 * 3 * 4
+    scene_b = lambda fc: N2 * (64 + 4 * fc) + (N2 - 1) * 64
+    b_sh = Pn * 16 * 4 + env_b + scene_b(3)
+    b_gr = b_sh + Pn * 3 * 4 + Pn * 4 * 4 * 2 + 2 * env_b + N2 * 4 * 13 * 2
+    maps_b = (32 * 64 * 3 + 5 * 64 * 128 * 3 + 32 * 32 * 2) * 4 + 8 * (257 + 256 * 513) + env_b
+    b_rl = Pn * 16 * 4 + maps_b + scene_b(7)
+    note = (f"hits per traced secondary ray from {Ps} points' samples: shading {float(nh_sh.float().mean()):.2f} "
+            f"({vfrac:.3f} of samples traced), relighting {float(nh_rl.float().mean()):.2f}; "
+            f"{SAMPLE_FLOPS} flops per sample for sampling and the BRDF")
+    configs = {
+        "workload": f"{args.mc_surfels} surfels, {Pn} G-buffer points x 64 samples, 512x256 environment, k=16",
+        "shade": roof_entry(fms, rays, rays * (vfrac * f_fwd + SAMPLE_FLOPS), b_sh, peak, hbm, note=note),
+        "grad": roof_entry(bms, rays, rays * (vfrac * (f_fwd + f_bwd) + SAMPLE_FLOPS), b_gr, peak, hbm,
+                           note="forward trace saving hit lists, then the backward from the lists (3x per hit)"),
+        "relight": roof_entry(relight_ms, rays, rays * (vfrac_rl * f_rl + SAMPLE_FLOPS), b_rl, peak, hbm),
+    }
+    if cpu:
+        configs["cpu_baseline"] = cpu_baseline_mc(sc2, gb, synth.env_map(seed=1003))
     E.close()
     if S2.status() != 0:
         raise RuntimeError("device error in the MC leg")
     S2.close()
-    return {"workload": f"{args.mc_surfels} surfels, {Pn} G-buffer points x (32 cosine + 32 GGX) = "
+    return {"configs": configs,"workload": f"{args.mc_surfels} surfels, {Pn} G-buffer points x (32 cosine + 32 GGX) = "
                         f"{rays / 1e6:.1f}M secondary rays, 512x256 env, k=16",
             "ms": fms, "mrays_s": rays / (fms * 1e-3) / 1e6, "points_per_s": Pn / (fms * 1e-3),
             "bwd_ms": bms, "bwd_mrays_s": rays / (bms * 1e-3) / 1e6,
@@ -525,14 +698,137 @@ def mc_leg(args, dev):
                         "envmap_ms": env_ms, "ms": relight_ms, "mrays_s": rays / (relight_ms * 1e-3) / 1e6}}
 
 
+def tiny_leg(args, dev, peak, hbm):
+    """The tiny forward configuration: 1,024 surfels, one 64x64 camera (4,096
+    rays), k = 8, 3 channels. Forward and forward + backward, each call timed
+    with CUDA events over 200 repetitions after a warm-up (calls this small
+    are launch-bound); the oracle on all 4,096 rays beside it."""
+    import numpy as np
+    import torch
+    import synth
+    import paper_2412_15867_gb300 as irgs
+
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    sc = synth.tiny_scene(seed=1000, n=1024)
+    ro_np, rd_np = synth.look_at_rays(synth.tiny_camera(1000), (0, 0, 0), 64, 64)
+    R = ro_np.shape[0]
+    S = irgs.Scene(*(T(a) for a in sc.arrays()))
+    ro, rd = T(ro_np), T(rd_np)
+    gf_np, gd_np, go_np = synth.upstream_grads(R, 3, seed=1004)
+    gf, gd, go = T(gf_np), T(gd_np), T(go_np)
+    p = irgs.TraceParams(k=8, feat_count=3)
+    out = irgs.trace_forward(S, ro, rd, p)
+    grads = irgs.trace_backward(S, ro, rd, p, out, gf, gd, go)
+    stream = torch.cuda.current_stream(dev)
+    reps = 200
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(10):
+        irgs.trace_forward(S, ro, rd, p, out=out)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        irgs.trace_forward(S, ro, rd, p, out=out)
+    ev[1].record(stream)
+    for _ in range(reps):
+        irgs.trace_forward(S, ro, rd, p, out=out)
+        irgs.trace_backward(S, ro, rd, p, out, gf, gd, go, grads=grads)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    if S.status() != 0:
+        raise RuntimeError("device error in the tiny configuration")
+    f_ms = ev[0].elapsed_time(ev[1]) / reps
+    fb_ms = ev[1].elapsed_time(ev[2]) / reps
+    nh = out["n_hits"]
+    ff = algorithmic_flops(nh, 8, sc.n, 3)
+    fbk = algorithmic_flops(nh, 8, sc.n, 3, backward=True)
+    res = {"workload": "1,024 surfels (centres U[-1,1]^3), one 64x64 camera = 4,096 rays, k=8, 3 channels",
+           "fwd": roof_entry(f_ms, R, ff, trace_bytes(R, sc.n, 3), peak, hbm,
+                             note="one launch per call; launch-bound at this size"),
+           "fwd_bwd": roof_entry(fb_ms, R, ff + fbk, trace_bytes(R, sc.n, 3) + trace_bytes(R, sc.n, 3, True),
+                                 peak, hbm)}
+    if not args.no_cpu:
+        res["cpu_baseline"] = cpu_baseline_tiny(sc, ro_np, rd_np, gf_np, gd_np, go_np)
+    S.close()
+    return res
+
+
+def cpu_baseline_tiny(sc, ro, rd, gf, gd, go):
+    """Oracle forward + gradient on all 4,096 rays of the tiny configuration."""
+    import oracle
+    p = oracle.Params(feat_count=3)
+    cores = oracle.num_threads()
+    n, t0 = 0, time.perf_counter()
+    while n == 0 or time.perf_counter() - t0 < 2.0:
+        oracle.trace(sc, ro, rd, p, margins=None)
+        oracle.trace_grad(sc, ro, rd, gf, gd, go, p)
+        n += 1
+    dt = time.perf_counter() - t0
+    return {"value": n * ro.shape[0] / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"all {ro.shape[0]} rays, forward + gradient, {n} passes ({dt:.1f} s)"}
+
+
+def cpu_baseline_mc(sc, gb, env):
+    """Oracle Monte Carlo shading (32 points x 64 samples = 2,048 secondary
+    rays) and its gradient (16 points x 64 samples) over the 1M-surfel scene."""
+    import numpy as np
+    import oracle
+    p = oracle.Params(feat_count=3, t_min=1e-3)
+    cores = oracle.num_threads()
+    sub = [a[:32] for a in gb]
+    t0 = time.perf_counter()
+    oracle.shade(sc, *sub, env, 32, 32, 2024, p, margins=None)
+    dt = time.perf_counter() - t0
+    sub = [a[:16] for a in gb]
+    g = np.random.default_rng(1004).normal(size=(16, 3)).astype(np.float32)
+    t1 = time.perf_counter()
+    oracle.shade_grad(sc, *sub, env, 32, 32, 2024, p, g)
+    dg = time.perf_counter() - t1
+    return {"shade": {"value": 2048 / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+                      "sample": f"32 points x 64 samples = 2,048 secondary rays, FP64 brute force over {sc.n} "
+                                f"surfels ({dt:.1f} s)"},
+            "grad": {"value": 1024 / dg / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+                     "sample": f"16 points x 64 samples = 1,024 secondary rays, gradient ({dg:.1f} s)"},
+            "relight": None,
+            "relight_note": "not timed: the oracle pre-integrates the environment (plain sums over all "
+                            "texels) inside every call, ~50 s on the host before its first ray"}
+
+
+def serving_roofline(serving, configs, peak, hbm):
+    """Aggregate roofline fraction of the served mix at the headline rate:
+    served rays per second against the roofline of the same rays, each kind
+    costed with the per-ray flops measured for its standalone configuration
+    (render rays as the camera rays, G-buffer rays as camera rays with 7
+    channels, shading rays as the Monte Carlo samples)."""
+    h = serving.get("headline", {}).get("batched")
+    kinds = serving.get("rays_by_kind")
+    if not h or not kinds or "C1" not in configs or "C2" not in configs:
+        return None
+    f_cam = configs["C1"]["fwd"]["flops_per_ray"]
+    f_sh = configs["C2"]["shade"]["flops_per_ray"]
+    f_g = f_cam * (45 + 2 * 9 + 3) / (45 + 2 * 12 + 3)
+    tot = kinds["render"] + kinds["gbuffer"] + kinds["shade"]
+    if tot == 0:
+        return None
+    fpr = (kinds["render"] * f_cam + kinds["gbuffer"] * f_g + kinds["shade"] * f_sh) / tot
+    mrays = h["mrays_s"]
+    alu = peak * 1e12 / fpr / 1e6
+    return {"workload": serving["mix"], "mrays_s": mrays, "flops_per_ray": fpr, "alu_bound_mrays_s": alu,
+            "bound": "alu", "roofline_mrays_s": alu, "frac": mrays / alu,
+            "ray_mix": {k: v / tot for k, v in kinds.items()},
+            "note": "served rays per second at the headline Poisson rate over the FP32 roofline of the same "
+                    "ray mix (bytes are far from binding for these traces)"}
+
+
 def serve_leg(args, dev):
     """Serving mix: 4 resident scenes (100k, 300k, 1M, 2M surfels, object scene
     with median scale 0.01 sqrt(300k/N)); 50% render (camera rays, 10
     channels) / 50% relight (G-buffer + Monte Carlo shading, spp log-uniform
     in [1, 128]) requests at resolutions {128, 256, 512, 1024}^2 from random
-    hemisphere cameras. Saturated throughput first (all requests queued at
-    once), then a Poisson stream at 0.7x that rate served with continuous
-    batching and, separately, one request at a time."""
+    hemisphere cameras. Saturated throughput first: a burst of requests of
+    the Poisson stream's distribution, all queued at once. Then Poisson
+    streams at fractions of that rate, served with continuous batching and,
+    separately, one request at a time: the headline at 0.7x (warm-up, then
+    the measured window) and a sweep at 0.3x, 0.5x and 0.9x."""
     import numpy as np
     import torch
     import synth
@@ -561,36 +857,59 @@ def serve_leg(args, dev):
         return make
 
     budget = 24 << 30
-    # saturated: a burst of requests served with continuous batching
-    srv = serve.Server(scenes, hbm_budget=budget, max_jobs=64, max_tiles=8192)
-    mk = maker(11)
-    n_burst = 48
-    for i in range(4):                                   # warm-up (graph capture, caches)
-        srv.submit(mk(i))
+    kw = dict(hbm_budget=budget, max_jobs=64, max_tiles=8192)
+    # saturated: a burst of requests of the stream's distribution, continuous batching
+    srv = serve.Server(scenes, **kw)
+    warm = maker(99)
+    for i in range(6):                                   # warm-up (graph capture, caches)
+        srv.submit(warm(i))
     srv.run_until_idle()
+    mk = maker(23)
+    n_sat = args.serve_burst
     rays0 = srv.rays_total
     t0 = time.perf_counter()
-    burst = [srv.submit(mk(100 + i), arrival=t0) for i in range(n_burst)]
+    for i in range(n_sat):
+        srv.submit(mk(i), arrival=t0)
     srv.run_until_idle()
     sat_wall = time.perf_counter() - t0
-    sat_rate = n_burst / sat_wall
+    sat_rate = n_sat / sat_wall
     sat_mrays = (srv.rays_total - rays0) / sat_wall / 1e6
-    rate = 0.7 * sat_rate
+    srv.close()
     out = {"scenes_surfels": sizes, "mix": "50% render (10 ch) / 50% relight (spp log-uniform 1-128), "
            "res {128,256,512,1024}^2, random hemisphere cameras, Poisson arrivals",
-           "saturated": {"requests_per_s": sat_rate, "mrays_s": sat_mrays, "requests": n_burst},
-           "rate_requests_per_s": rate}
-    for name, batching in (("batched", True), ("one_at_a_time", False)):
-        srv2 = serve.Server(scenes, hbm_budget=budget, max_jobs=64, max_tiles=8192, batching=batching)
-        hs, wall, rays = serve.run_poisson(srv2, maker(23), rate, args.serve_seconds, args.serve_warmup, seed=5)
+           "saturated": {"requests_per_s": sat_rate, "mrays_s": sat_mrays, "requests": n_sat,
+                         "how": "burst of requests of the stream's distribution queued at once"}}
+
+    def run(frac, batching, seconds, warmup, seed):
+        srv2 = serve.Server(scenes, batching=batching, **kw)
+        rate = frac * sat_rate
+        k0 = dict(srv2.rays_by_kind)
+        hs, wall, rays = serve.run_poisson(srv2, maker(seed), rate, seconds, warmup, seed=seed)
         st = serve.latency_stats(hs)
-        st.update({"mrays_s": rays / wall / 1e6, "requests_per_s": len(hs) / wall, "steps": srv2.steps})
-        out[name] = st
+        served = len(hs) / wall
+        st.update({"offered_requests_per_s": rate, "served_requests_per_s": served,
+                   "served_over_offered": served / rate, "mrays_s": rays / wall / 1e6, "steps": srv2.steps,
+                   "window_s": seconds, "warmup_s": warmup})
+        kinds = {k: srv2.rays_by_kind[k] - k0[k] for k in k0}
         srv2.close()
+        return st, kinds
+
+    # headline: 0.7x saturation, warm-up then the measured window
+    b, kinds = run(0.7, True, args.serve_seconds, args.serve_warmup, 24)
+    o, _ = run(0.7, False, args.sweep_seconds, args.sweep_warmup, 24)
+    out["headline"] = {"lambda_over_saturated": 0.7, "batched": b, "one_at_a_time": o,
+                       "stable": bool(b["served_over_offered"] >= 0.95)}
+    out["rays_by_kind"] = {"render": kinds[serve.TILE_RENDER], "gbuffer": kinds[serve.TILE_GBUFFER],
+                           "shade": kinds[serve.TILE_SHADE]}
+    sweep = []
+    for frac in (0.3, 0.5, 0.9):
+        b, _ = run(frac, True, args.sweep_seconds, args.sweep_warmup, 25 + int(frac * 10))
+        o, _ = run(frac, False, args.sweep_seconds, args.sweep_warmup, 25 + int(frac * 10))
+        sweep.append({"lambda_over_saturated": frac, "batched": b, "one_at_a_time": o})
+    out["sweep"] = sweep
     status = sum(S.status() for S in scenes)
     if status:
         raise RuntimeError("device error in the serving leg")
-    srv.close()
     for S in scenes:
         S.close()
     return out

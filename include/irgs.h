@@ -95,6 +95,15 @@ typedef struct {
 /* Human-readable name of a status code (static storage). */
 const char* irgs_status_string(irgs_status status);
 
+/* Measurement probe (the paper has no counterpart): one launch of a kernel
+ * that keeps the FP32 FMA pipes of every SM of the current device busy
+ * (8 blocks of 256 threads per SM, eight independent FMA chains per thread,
+ * `iters` passes of 16 dependent steps each). *flops receives the launch's
+ * FP32 flop count (2 per FMA); the caller times the launch on `stream` and
+ * divides, which gives the measured FP32 peak that bounds the intersection
+ * arithmetic of Eq. 6-7. Enqueued on `stream`; allocates nothing. */
+irgs_status irgs_probe_fma(int64_t iters, void* stream, double* flops);
+
 /* IRGS_ABI_VERSION of the loaded library. */
 int32_t irgs_abi_version(void);
 
@@ -328,6 +337,21 @@ irgs_status irgs_shade_mc_backward(irgs_scene scene, const float* x, const float
                                    float* g_quats, float* g_scales, float* g_opacity, float* g_features,
                                    void* stream);
 
+/*
+ * The incident directions irgs_shade_mc draws (Eq. 15's samples; cosine /
+ * GGX half-vector sampling of the supplementary "Composited scene details",
+ * or the stratified uniform directions with IRGS_FLAG_UNIFORM in `flags`),
+ * without tracing them: sample s of point p is ray i = p (n_diffuse +
+ * n_spec) + s, starting at x[p] (not written). n, wo : [n_points, 3], rough
+ * : [n_points] device arrays as for irgs_shade_mc. out_dir [n_points S, 3]
+ * receives the unit direction w_i, out_valid [n_points S] (may be NULL) 1
+ * where the sample is traced and 0 where it lies below the horizon (adds 0
+ * but counts). Same random numbers, frame and arithmetic as the estimator.
+ */
+irgs_status irgs_shade_sample_rays(const float* n, const float* rough, const float* wo, int64_t n_points,
+                                  int32_t n_diffuse, int32_t n_spec, uint64_t seed, uint32_t flags,
+                                  float* out_dir, int32_t* out_valid, void* stream);
+
 /* ---------------------------------------------------------------------- */
 /* Relighting (supplementary "Relighting details", Eq. 18).               */
 /* ---------------------------------------------------------------------- */
@@ -403,6 +427,17 @@ irgs_status irgs_relight(irgs_scene scene, irgs_envmap envmap, const float* x, c
                          const float* albedo, const float* rough, const float* wo, int64_t n_points,
                          int32_t n_samples, uint64_t seed, const irgs_trace_params* params,
                          float* out_rgb, float* out_vis, float* out_ind, void* stream);
+
+/*
+ * The environment-importance directions irgs_relight draws (Eq. 18's
+ * samples), without tracing them: sample s of point p is ray i = p
+ * n_samples + s. out_dir [n_points n_samples, 3] unit directions, out_pdf
+ * (may be NULL) their solid-angle density, out_valid (may be NULL) 1 where
+ * the sample is used. Device arrays; the directions depend only on the
+ * environment, the seed and the keys (p, s).
+ */
+irgs_status irgs_relight_sample_rays(irgs_envmap envmap, int64_t n_points, int32_t n_samples, uint64_t seed,
+                                    float* out_dir, float* out_pdf, int32_t* out_valid, void* stream);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: several resident scenes, many requests per persistent launch. */

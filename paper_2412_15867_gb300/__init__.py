@@ -389,6 +389,25 @@ def shade_mc_backward(scene: Scene, x, n, albedo, rough, wo, env, n_diffuse: int
     return grads
 
 
+def shade_sample_rays(n, rough, wo, n_diffuse: int, n_spec: int, seed: int, mode: str = "split"):
+    """Directions [P * S, 3] and validity [P * S] (int32) of the secondary
+    rays shade_mc draws for points with normals n, roughness rough and
+    outgoing directions wo (ray i = p * S + s, origin x[p])."""
+    nn = _dev_f32(n, "n", 3)
+    P = nn.shape[0]
+    r = _dev_f32(rough, "rough").reshape(P)
+    w = _dev_f32(wo, "wo", 3)
+    S = n_diffuse + n_spec
+    d = torch.empty((P * S, 3), device=nn.device, dtype=torch.float32)
+    v = torch.empty(P * S, device=nn.device, dtype=torch.int32)
+    flags = FLAG_UNIFORM if mode == "uniform" else 0
+    with torch.cuda.device(nn.device):
+        _lib.check(_lib.lib().irgs_shade_sample_rays(_ptr(nn), _ptr(r), _ptr(w), P, n_diffuse, n_spec,
+                                                     C.c_uint64(seed & (2 ** 64 - 1)), flags, _ptr(d), _ptr(v),
+                                                     _stream(nn.device)), "irgs_shade_sample_rays")
+    return d, v
+
+
 class _ShadeFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, means, quats, scales, opacity, features, albedo, rough, env, x, n, wo, scene, cfg):
@@ -472,6 +491,21 @@ class EnvMap:
             self.close()
         except Exception:
             pass
+
+
+def relight_sample_rays(envmap: "EnvMap", n_points: int, n_samples: int, seed: int):
+    """Directions [P * S, 3], densities [P * S] and validity [P * S] of the
+    environment samples relight draws (ray i = p * S + s)."""
+    dev = envmap.device
+    R = n_points * n_samples
+    d = torch.empty((R, 3), device=dev, dtype=torch.float32)
+    pdf = torch.empty(R, device=dev, dtype=torch.float32)
+    v = torch.empty(R, device=dev, dtype=torch.int32)
+    with torch.cuda.device(dev):
+        _lib.check(_lib.lib().irgs_relight_sample_rays(envmap.handle, n_points, n_samples,
+                                                       C.c_uint64(seed & (2 ** 64 - 1)), _ptr(d), _ptr(pdf),
+                                                       _ptr(v), _stream(dev)), "irgs_relight_sample_rays")
+    return d, pdf, v
 
 
 def relight(scene: Scene, envmap: EnvMap, x, n, albedo, rough, wo, n_samples: int, seed: int,

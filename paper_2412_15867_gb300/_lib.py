@@ -49,6 +49,10 @@ _SIGS = {
     "irgs_relight": (C.c_int, [P, P, P, P, P, P, P, C.c_int64, C.c_int32, C.c_uint64, C.POINTER(TraceParamsC),
                                P, P, P, P]),
     "irgs_kernel_launches": (C.c_uint64, []),
+    "irgs_shade_sample_rays": (C.c_int, [P, P, P, C.c_int64, C.c_int32, C.c_int32, C.c_uint64, C.c_uint32, P, P,
+                                         P]),
+    "irgs_relight_sample_rays": (C.c_int, [P, C.c_int64, C.c_int32, C.c_uint64, P, P, P, P]),
+    "irgs_probe_fma": (C.c_int, [C.c_int64, P, C.POINTER(C.c_double)]),
     "irgs_build_scene": (C.c_int, [C.POINTER(Surfels), C.c_float, P, C.POINTER(P)]),
     "irgs_build_scene_ex": (C.c_int, [C.POINTER(Surfels), C.c_float, C.c_uint32, P, C.POINTER(P)]),
     "irgs_update_scene": (C.c_int, [P, C.POINTER(Surfels), P]),

@@ -66,9 +66,46 @@ irgs_status check_shade(const irgs_scene sc, const irgs_trace_params* params, in
     return IRGS_OK;
 }
 
+// FP32 pipe probe: eight independent FMA chains per thread, 16 steps per
+// loop pass (256 flops per thread per pass). The final sum is stored only if
+// it equals a value it never reaches, which keeps the chains live.
+__device__ float g_fma_sink;
+
+__global__ void __launch_bounds__(256) k_fma_probe(float b, float c, int64_t iters) {
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = 1.0f + 1e-3f * k + 1e-7f * threadIdx.x;
+    for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k] = fmaf(a[k], b, c);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == -12345.0f) g_fma_sink = s;
+}
+
 }  // namespace
 
 extern "C" {
+
+irgs_status irgs_probe_fma(int64_t iters, void* stream, double* flops) {
+    if (iters <= 0 || iters > ((int64_t)1 << 40)) return IRGS_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return IRGS_ERR_CUDA;
+    }
+    const int blocks = sms * 8, threads = 256;
+    k_fma_probe<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(0.9999999f, 1e-7f, iters);
+    irgs::count_launches(1);
+    if (cudaGetLastError() != cudaSuccess) return IRGS_ERR_CUDA;
+    if (flops) *flops = (double)blocks * threads * (double)iters * 256.0;
+    return IRGS_OK;
+}
 
 const char* irgs_status_string(irgs_status s) {
     switch (s) {
@@ -300,6 +337,19 @@ irgs_status irgs_shade_mc_backward(irgs_scene sc, const float* x, const float* n
                                             g_features, static_cast<cudaStream_t>(stream));
 }
 
+irgs_status irgs_shade_sample_rays(const float* n, const float* rough, const float* wo, int64_t n_points,
+                                  int32_t n_diffuse, int32_t n_spec, uint64_t seed, uint32_t flags, float* out_dir,
+                                  int32_t* out_valid, void* stream) {
+    if (n_points < 0 || n_diffuse < 0 || n_spec < 0 || n_diffuse + n_spec <= 0 || n_diffuse + n_spec > (1 << 24))
+        return IRGS_ERR_INVALID_ARG;
+    if ((flags & ~IRGS_FLAG_UNIFORM) != 0u || ((flags & IRGS_FLAG_UNIFORM) && n_spec != 0))
+        return IRGS_ERR_INVALID_ARG;
+    if (n_points > 0 && (!n || !rough || !wo || !out_dir)) return IRGS_ERR_INVALID_ARG;
+    if (n_points >= (int64_t)UINT32_MAX * 4) return IRGS_ERR_INVALID_ARG;
+    return irgs::launch_sample_rays(n, rough, wo, n_points, n_diffuse, n_spec, seed, (flags & IRGS_FLAG_UNIFORM) ? 1 : 0,
+                                    out_dir, out_valid, static_cast<cudaStream_t>(stream));
+}
+
 irgs_status irgs_rasterize(irgs_scene sc, const irgs_camera* cam, const irgs_trace_params* params, float* out_feat,
                            float* out_depth, float* out_opacity, int32_t* out_nhits, void* stream) {
     if (sc == nullptr || cam == nullptr) return IRGS_ERR_INVALID_ARG;
@@ -355,6 +405,17 @@ irgs_status irgs_relight(irgs_scene sc, irgs_envmap m, const float* x, const flo
     if ((s = use_device(dg, sc)) != IRGS_OK) return s;
     return irgs::launch_relight(sc->view(), sc->bounds, m, x, n, albedo, rough, wo, n_points, n_samples, seed,
                                 *params, out_rgb, out_vis, out_ind, static_cast<cudaStream_t>(stream));
+}
+
+irgs_status irgs_relight_sample_rays(irgs_envmap m, int64_t n_points, int32_t n_samples, uint64_t seed,
+                                    float* out_dir, float* out_pdf, int32_t* out_valid, void* stream) {
+    if (m == nullptr || n_points < 0 || n_samples <= 0 || n_samples > (1 << 24)) return IRGS_ERR_INVALID_ARG;
+    if (n_points > 0 && !out_dir) return IRGS_ERR_INVALID_ARG;
+    if (n_points >= (int64_t)UINT32_MAX * 4) return IRGS_ERR_INVALID_ARG;
+    irgs::DeviceGuard dg;
+    if (!dg.set(m->device)) return IRGS_ERR_CUDA;
+    return irgs::launch_relight_rays(m, n_points, n_samples, seed, out_dir, out_pdf, out_valid,
+                                     static_cast<cudaStream_t>(stream));
 }
 
 irgs_status irgs_build_lbvh_noalloc(const irgs_surfels* s, float alpha_min, int32_t* perm, uint32_t* keys,

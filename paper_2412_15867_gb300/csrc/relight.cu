@@ -645,6 +645,33 @@ irgs_status export_envmap_impl(irgs_envmap m, float* irr, float* pref, float* lu
     return e == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
 }
 
+// Directions of the environment-importance samples the relighting traces:
+// ray i = p * n_samples + s (they depend on the keys only, not on the point).
+__global__ void k_relight_rays(EnvMaps M, int64_t rays, int Sn, uint64_t seed, float* __restrict__ dir,
+                               float* __restrict__ pdf_out, int32_t* __restrict__ valid) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= rays) return;
+    f3 w = mk3(0.f, 0.f, 1.f);
+    float pdf = 0.f;
+    const bool ok = relight_dir(M, i / Sn, (int)(i % Sn), Sn, seed, w, pdf);
+    dir[3 * i] = w.x;
+    dir[3 * i + 1] = w.y;
+    dir[3 * i + 2] = w.z;
+    if (pdf_out != nullptr) pdf_out[i] = ok ? pdf : 0.f;
+    if (valid != nullptr) valid[i] = ok ? 1 : 0;
+}
+
+irgs_status launch_relight_rays(irgs_envmap m, int64_t P, int32_t n_samples, uint64_t seed, float* dir, float* pdf,
+                                int32_t* valid, cudaStream_t st) {
+    const int64_t rays = P * (int64_t)n_samples;
+    if (rays == 0) return IRGS_OK;
+    const EnvMaps M{m->env, m->irr, m->pref, m->lut, m->row_cdf, m->col_cdf, m->H, m->W};
+    const int T = 256;
+    k_relight_rays<<<(unsigned)((rays + T - 1) / T), T, 0, st>>>(M, rays, n_samples, seed, dir, pdf, valid);
+    count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+}
+
 irgs_status launch_relight(const SceneView& S, const uint32_t* bounds, irgs_envmap m, const float* x,
                            const float* n, const float* albedo, const float* rough, const float* wo, int64_t P,
                            int32_t n_samples, uint64_t seed, const irgs_trace_params& p, float* rgb, float* vis,

@@ -952,9 +952,15 @@ static void enqueue_wide(irgs_scene sc, cudaStream_t st) {
     const int64_t n = sc->n;
     int2* a = sc->wide_frontier;
     int2* b = sc->wide_frontier + n;
+    // a grid-stride loop over the frontier: four 256-thread blocks per SM
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, sc->device) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        sms = 1;
+    }
     k_wide_root<<<1, 1, 0, st>>>(n, a, sc->wide_counters);
     for (int level = 0; level < kWideLevels; ++level) {
-        k_wide_level<<<152 * 4, 256, 0, st>>>(level, sc->nodes, a, b, sc->wide_counters, sc->max_wide, sc->wide,
+        k_wide_level<<<sms * 4, 256, 0, st>>>(level, sc->nodes, a, b, sc->wide_counters, sc->max_wide, sc->wide,
                                              sc->status);
         int2* t = a; a = b; b = t;
     }

@@ -112,6 +112,10 @@ irgs_status build_envmap_impl(const float* env, int32_t H, int32_t W, cudaStream
 void free_envmap(irgs_envmap m);
 irgs_status export_envmap_impl(irgs_envmap m, float* irr, float* pref, float* lut, double* row_cdf,
                                double* col_cdf, cudaStream_t st);
+irgs_status launch_sample_rays(const float* n, const float* rough, const float* wo, int64_t P, int32_t nd,
+                               int32_t ns, uint64_t seed, int mode, float* dir, int32_t* valid, cudaStream_t st);
+irgs_status launch_relight_rays(irgs_envmap m, int64_t P, int32_t n_samples, uint64_t seed, float* dir, float* pdf,
+                                int32_t* valid, cudaStream_t st);
 irgs_status launch_relight(const SceneView& sv, const uint32_t* bounds, irgs_envmap m, const float* x,
                            const float* n, const float* albedo, const float* rough, const float* wo, int64_t P,
                            int32_t n_samples, uint64_t seed, const irgs_trace_params& p, float* rgb, float* vis,

@@ -107,6 +107,35 @@ int shade_mode(const irgs_trace_params& p) { return (p.flags & IRGS_FLAG_UNIFORM
 
 }  // namespace
 
+// Directions of the secondary rays the estimator traces (the sampler of
+// shade_point_warp without the traces): ray i = p * (nd + ns) + s.
+__global__ void k_sample_rays(const float* __restrict__ ng, const float* __restrict__ rg,
+                              const float* __restrict__ wog, int64_t Pn, int nd, int ns, int mode, uint64_t seed,
+                              float* __restrict__ dir, int32_t* __restrict__ valid) {
+    const int St = nd + ns;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= Pn * St) return;
+    const int64_t p = i / St;
+    const int s = (int)(i - p * St);
+    const ShadeFrame F = shade_frame(mk3(ng[3 * p], ng[3 * p + 1], ng[3 * p + 2]),
+                                     mk3(wog[3 * p], wog[3 * p + 1], wog[3 * p + 2]), rg[p]);
+    const ShadeSample d = draw_sample(F, mode, (uint64_t)p, s, St, nd, seed);
+    dir[3 * i] = d.wi.x;
+    dir[3 * i + 1] = d.wi.y;
+    dir[3 * i + 2] = d.wi.z;
+    if (valid != nullptr) valid[i] = d.valid ? 1 : 0;
+}
+
+irgs_status launch_sample_rays(const float* n, const float* rough, const float* wo, int64_t P, int32_t nd,
+                               int32_t ns, uint64_t seed, int mode, float* dir, int32_t* valid, cudaStream_t st) {
+    const int64_t rays = P * (int64_t)(nd + ns);
+    if (rays == 0) return IRGS_OK;
+    const int T = 256;
+    k_sample_rays<<<(unsigned)((rays + T - 1) / T), T, 0, st>>>(n, rough, wo, P, nd, ns, mode, seed, dir, valid);
+    count_launches(1);
+    return cudaGetLastError() == cudaSuccess ? IRGS_OK : IRGS_ERR_CUDA;
+}
+
 irgs_status launch_shade_mc(const SceneView& S, const float* x, const float* n, const float* albedo,
                             const float* rough, const float* wo, int64_t P, const float* env, int32_t H, int32_t W,
                             int32_t n_diffuse, int32_t n_spec, uint64_t seed, const irgs_trace_params& p,

@@ -207,6 +207,7 @@ class Server:
         self.used = 0
         self.steps = 0
         self.rays_total = 0
+        self.rays_by_kind = {TILE_RENDER: 0, TILE_GBUFFER: 0, TILE_SHADE: 0}
         self.stream = torch.cuda.Stream(self.device)
 
     # ---- requests
@@ -312,6 +313,7 @@ class Server:
                 h.rays += rays
                 budget -= rays
                 self.rays_total += rays
+                self.rays_by_kind[kind] += rays
             plan.append(h)
             if n_tiles >= self.max_tiles or budget <= 0 or n_jobs >= self.max_jobs:
                 break

@@ -90,7 +90,7 @@ def test_exact_tie_gradients_follow_user_order(saved):
     gd = rng.normal(size=R).astype(np.float32)
     go = rng.normal(size=R).astype(np.float32)
     S = make_scene(irgs, sc)
-    p = irgs.TraceParams(k=1, feat_count=3)
+    p = irgs.TraceParams(k=8, feat_count=3)
     fwd = irgs.trace_forward(S, dev(ro), dev(rd), p, max_hit_ids=saved)
     g = irgs.trace_backward(S, dev(ro), dev(rd), p, fwd, dev(gf), dev(gd), dev(go))
     torch.cuda.synchronize()
