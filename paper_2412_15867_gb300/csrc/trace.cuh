@@ -24,6 +24,7 @@ struct Ray {
     f3 oinv;           // o * inv
     float inv_dd;      // 1 / |d|^2
     float graze;       // 1e-8 |d|
+    int nrx, nry, nrz; // row of a wide node holding each axis' entry plane (lo if inv >= 0, else hi)
 };
 
 __device__ __forceinline__ Ray make_ray(f3 o, f3 d) {
@@ -36,6 +37,9 @@ __device__ __forceinline__ Ray make_ray(f3 o, f3 d) {
     float dd = fmaf(d.x, d.x, fmaf(d.y, d.y, d.z * d.z));
     r.inv_dd = 1.0f / dd;
     r.graze = 1e-8f * sqrtf(dd);
+    r.nrx = r.inv.x >= 0.f ? 0 : 3;
+    r.nry = r.inv.y >= 0.f ? 1 : 4;
+    r.nrz = r.inv.z >= 0.f ? 2 : 5;
     return r;
 }
 
@@ -151,6 +155,44 @@ __device__ __forceinline__ void slab4(const WideNode& w, const Ray& r, float tn[
         const float z0 = fmaf(lz[k], r.inv.z, -r.oinv.z), z1 = fmaf(hz[k], r.inv.z, -r.oinv.z);
         tn[k] = max3f(fminf(x0, x1), fminf(y0, y1), fminf(z0, z1));
         tf[k] = min3f(fmaxf(x0, x1), fmaxf(y0, y1), fmaxf(z0, z1));
+    }
+}
+
+// A wide node's child boxes as the ray meets them: for each axis the plane
+// it enters through (lo where 1/d >= 0, else hi) and the one it leaves
+// through, selected by which rows are loaded.
+struct WideNodeRay {
+    float4 nx, ny, nz, fx, fy, fz;
+    int4 child;
+};
+
+__device__ __forceinline__ WideNodeRay load_wide_ray(const WideNode* w, int i, const Ray& r) {
+    const float4* p = reinterpret_cast<const float4*>(w + i);
+    WideNodeRay n;
+    n.nx = ldg4(p + r.nrx);
+    n.ny = ldg4(p + r.nry);
+    n.nz = ldg4(p + r.nrz);
+    n.fx = ldg4(p + (r.nrx ^ 3));   // rows 0 <-> 3, 1 <-> 4, 2 <-> 5
+    n.fy = ldg4(p + (r.nry ^ 5));
+    n.fz = ldg4(p + (r.nrz ^ 7));
+    n.child = ldg4i(reinterpret_cast<const int4*>(p + 6));
+    return n;
+}
+
+// Slab intervals of the four children from the entry / exit planes: the same
+// values slab4 gives (fma(v, inv, -oinv) is monotone in v for a fixed sign
+// of inv, so the entry plane's distance is the minimum of the pair), with
+// no per-axis min/max.
+__device__ __forceinline__ void slab4_ray(const WideNodeRay& w, const Ray& r, float tn[4], float tf[4]) {
+    const float nx[4] = {w.nx.x, w.nx.y, w.nx.z, w.nx.w}, fx[4] = {w.fx.x, w.fx.y, w.fx.z, w.fx.w};
+    const float ny[4] = {w.ny.x, w.ny.y, w.ny.z, w.ny.w}, fy[4] = {w.fy.x, w.fy.y, w.fy.z, w.fy.w};
+    const float nz[4] = {w.nz.x, w.nz.y, w.nz.z, w.nz.w}, fz[4] = {w.fz.x, w.fz.y, w.fz.z, w.fz.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        tn[k] = max3f(fmaf(nx[k], r.inv.x, -r.oinv.x), fmaf(ny[k], r.inv.y, -r.oinv.y),
+                      fmaf(nz[k], r.inv.z, -r.oinv.z));
+        tf[k] = min3f(fmaf(fx[k], r.inv.x, -r.oinv.x), fmaf(fy[k], r.inv.y, -r.oinv.y),
+                      fmaf(fz[k], r.inv.z, -r.oinv.z));
     }
 }
 
@@ -289,10 +331,10 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
             ok = false;
             break;
         }
-        const WideNode nd = load_wide(S.wide, ni);
+        const WideNodeRay nd = load_wide_ray(S.wide, ni, ray);
         if (STATS) ts->nodes++;
         float tn[4], tf[4];
-        slab4(nd, ray, tn, tf);
+        slab4_ray(nd, ray, tn, tf);
         const int c[4] = {nd.child.x, nd.child.y, nd.child.z, nd.child.w};
         float hi_c = t_hi + tslack(t_hi);
         bool h[4];
@@ -395,10 +437,10 @@ __device__ __forceinline__ bool collect_round_warp(const SceneView& S, const Ray
             ok = false;
             break;
         }
-        const WideNode nd = load_wide(S.wide, ni);
+        const WideNodeRay nd = load_wide_ray(S.wide, ni, ray);
         if (STATS && active) ts->nodes++;
         float tn[4], tf[4];
-        slab4(nd, ray, tn, tf);
+        slab4_ray(nd, ray, tn, tf);
         const int c[4] = {nd.child.x, nd.child.y, nd.child.z, nd.child.w};
         float hi_c = t_hi + tslack(t_hi);
         bool h[4];
