@@ -87,14 +87,6 @@ typedef struct {
  * the fused kernel with a warp-shared stack). Setting both is invalid. */
 #define IRGS_FLAG_PER_THREAD 1u
 #define IRGS_FLAG_WARP 2u
-/* Trace entry points (used by irgs_trace_forward and irgs_trace_stats,
- * accepted and ignored by irgs_trace_backward, whose replay always walks in
- * rounds; invalid with IRGS_FLAG_PER_THREAD): the warp-coherent walk in k-buffer rounds, each
- * restarted from the root after the last blended hit (regrouping the rays
- * still marching between rounds for batches of 2^20 rays or more), instead
- * of the default single ordered pass that blends each pending hit as soon as
- * no unvisited subtree can hold a nearer one. Same results. */
-#define IRGS_FLAG_ROUNDS 8u
 /* Shading only (irgs_shade_mc / irgs_shade_mc_backward): the stratified
  * uniform hemisphere estimator of Eq. 15 instead of split-lobe importance
  * sampling; n_spec must be 0. Rejected by the trace entry points. */

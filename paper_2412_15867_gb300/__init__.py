@@ -27,7 +27,6 @@ __all__ = ["TraceParams", "Scene", "trace", "trace_forward", "trace_backward", "
 FLAG_PER_THREAD = 1   # one traversal stack per ray
 FLAG_WARP = 2         # one traversal stack per warp of 32 rays
 FLAG_UNIFORM = 4      # shading: stratified uniform hemisphere estimator (Eq. 15)
-FLAG_ROUNDS = 8       # trace: warp-coherent k-buffer rounds restarted from the root (default: one ordered pass)
 
 
 def library_path() -> str:

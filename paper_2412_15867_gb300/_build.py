@@ -12,7 +12,7 @@ OBJ = os.path.join(HERE, "_obj")
 LIB = os.path.join(OBJ, "libirgs.so")
 SOURCES = ["scene.cu", "trace_fwd.cu", "trace_bwd.cu", "shade.cu", "shade_wave.cu", "relight.cu", "raster.cu",
            "serve.cu", "capi.cu"]
-HEADERS = ["common.cuh", "trace.cuh", "trace_flush.cuh", "trace_bwd.cuh", "shade.cuh", "camera.cuh", "wave.cuh", "scene.h"]
+HEADERS = ["common.cuh", "trace.cuh", "trace_bwd.cuh", "shade.cuh", "camera.cuh", "wave.cuh", "scene.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

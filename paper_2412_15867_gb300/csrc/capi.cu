@@ -33,10 +33,9 @@ irgs_status check_params(const irgs_scene sc, const irgs_trace_params* p, bool s
     if (p->feat_count < 0 || p->feat_count > IRGS_MAX_FEATURES) return IRGS_ERR_INVALID_ARG;
     if (p->feat_count > 0 && (p->feat_offset < 0 || p->feat_offset + p->feat_count > sc->F))
         return IRGS_ERR_INVALID_ARG;
-    const uint32_t allowed = IRGS_FLAG_PER_THREAD | IRGS_FLAG_WARP | (shading ? IRGS_FLAG_UNIFORM : IRGS_FLAG_ROUNDS);
+    const uint32_t allowed = IRGS_FLAG_PER_THREAD | IRGS_FLAG_WARP | (shading ? IRGS_FLAG_UNIFORM : 0u);
     if ((p->flags & ~allowed) != 0u) return IRGS_ERR_INVALID_ARG;
-    if ((p->flags & IRGS_FLAG_PER_THREAD) && (p->flags & (IRGS_FLAG_WARP | IRGS_FLAG_ROUNDS)))
-        return IRGS_ERR_INVALID_ARG;
+    if ((p->flags & IRGS_FLAG_PER_THREAD) && (p->flags & IRGS_FLAG_WARP)) return IRGS_ERR_INVALID_ARG;
     return IRGS_OK;
 }
 

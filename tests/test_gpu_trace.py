@@ -254,9 +254,8 @@ def test_camera_config_full_size_sampled():
 
 
 def test_traversal_modes_give_identical_results():
-    """The single ordered pass (default), warp-coherent k-buffer rounds and
-    per-ray traversal return bit-identical outputs (the hits are blended in
-    the same order with the same arithmetic whatever the visiting order)."""
+    """Warp-coherent and per-ray traversal return bit-identical outputs
+    (the k-buffer holds the K nearest hits whatever the visiting order)."""
     sc = synth.object_scene(n=20_000, seed=15)
     ro, rd = synth.camera_batch_rays(synth.hemisphere_cameras(2, seed=15), 61, 33)
     ri, di = synth.random_rays_through_scene(3000, seed=16, box=2.0, radius=4.0)
@@ -265,7 +264,7 @@ def test_traversal_modes_give_identical_results():
         for k in (4, 8, 16, 32):
             pw = irgs.TraceParams(k=k, feat_count=10)
             a = irgs.trace_forward(S, dev(o), dev(d), pw, max_hit_ids=16)
-            for fl in (irgs.FLAG_PER_THREAD, irgs.FLAG_ROUNDS, irgs.FLAG_WARP):
+            for fl in (irgs.FLAG_PER_THREAD, irgs.FLAG_WARP):
                 b = irgs.trace_forward(S, dev(o), dev(d), pw.with_(flags=fl), max_hit_ids=16)
                 for key in a:
                     assert torch.equal(a[key], b[key]), (k, fl, key)
@@ -273,8 +272,6 @@ def test_traversal_modes_give_identical_results():
         irgs.trace_forward(S, dev(ro), dev(rd), irgs.TraceParams(flags=3))
     with pytest.raises(irgs.IrgsError):
         irgs.trace_forward(S, dev(ro), dev(rd), irgs.TraceParams(flags=4))
-    with pytest.raises(irgs.IrgsError):
-        irgs.trace_forward(S, dev(ro), dev(rd), irgs.TraceParams(flags=irgs.FLAG_ROUNDS | irgs.FLAG_PER_THREAD))
 
 
 def test_compacted_rounds_equal_per_ray_march():
@@ -287,16 +284,14 @@ def test_compacted_rounds_equal_per_ray_march():
     assert ro.shape[0] >= 1 << 20
     S = make_scene(irgs, sc)
     pw = irgs.TraceParams(k=16, feat_count=10)
-    a = irgs.trace_forward(S, dev(ro), dev(rd), pw.with_(flags=irgs.FLAG_ROUNDS), max_hit_ids=96)
+    a = irgs.trace_forward(S, dev(ro), dev(rd), pw, max_hit_ids=96)
     b = irgs.trace_forward(S, dev(ro), dev(rd), pw.with_(flags=irgs.FLAG_PER_THREAD), max_hit_ids=96)
-    c = irgs.trace_forward(S, dev(ro), dev(rd), pw, max_hit_ids=96)      # the single ordered pass
     torch.cuda.synchronize()
     assert S.status() == 0
     nh = a["n_hits"].cpu().numpy()
     assert (nh > 48).any() and (nh > 16).mean() > 0.3     # rounds 4+ (run to completion) and the compacted rounds both occur
     for key in a:
         assert torch.equal(a[key], b[key]), key
-        assert torch.equal(c[key], b[key]), key
 
 
 def test_trace_stats_counters_are_consistent():
@@ -306,18 +301,14 @@ def test_trace_stats_counters_are_consistent():
     p = irgs.TraceParams(k=16, feat_count=10)
     out = irgs.trace_forward(S, dev(ro), dev(rd), p)
     nh = out["n_hits"].cpu().numpy()
-    sw = irgs.trace_stats(S, dev(ro), dev(rd), p.with_(flags=irgs.FLAG_ROUNDS)).cpu().numpy()
+    sw = irgs.trace_stats(S, dev(ro), dev(rd), p).cpu().numpy()
     st = irgs.trace_stats(S, dev(ro), dev(rd), p.with_(flags=irgs.FLAG_PER_THREAD)).cpu().numpy()
-    sf = irgs.trace_stats(S, dev(ro), dev(rd), p).cpu().numpy()        # the single ordered pass
     for s in (sw, st):
         assert np.array_equal(s[:, 0], sw[:, 0])          # rounds depend only on the hits
         assert np.all(s[:, 0] >= 1)
         assert np.all(s[:, 0] >= np.ceil(nh / 16))
-    for s in (sw, st, sf):
         assert np.all(s[:, 3] >= nh) and np.all(s[:, 2] >= s[:, 3])
         assert np.all(s[nh > 0, 1] > 0)
-    # a pass restarts only after the ring of pending hits overflowed: never more passes than rounds
-    assert np.all(sf[:, 0] >= 1) and np.all(sf[:, 0] <= sw[:, 0])
 
 
 def test_wide_hierarchy_invariants():
