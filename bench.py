@@ -886,9 +886,13 @@ def serve_leg(args, dev):
         k0 = dict(srv2.rays_by_kind)
         hs, wall, rays = serve.run_poisson(srv2, maker(seed), rate, seconds, warmup, seed=seed)
         st = serve.latency_stats(hs)
-        served = len(hs) / wall
-        st.update({"offered_requests_per_s": rate, "served_requests_per_s": served,
-                   "served_over_offered": served / rate, "mrays_s": rays / wall / 1e6, "steps": srv2.steps,
+        # throughput: requests completed inside the measured window (of any
+        # arrival time) per second of it; a stable server keeps up with the
+        # offered rate, an overloaded one falls behind and its backlog grows
+        served = srv2.window_stats["completed_in_window"] / seconds
+        st.update({"offered_requests_per_s": rate, "arrived_in_window": len(hs),
+                   "served_requests_per_s": served, "served_over_offered": served / rate,
+                   "drain_s": wall - seconds, "mrays_s": rays / wall / 1e6, "steps": srv2.steps,
                    "window_s": seconds, "warmup_s": warmup})
         kinds = {k: srv2.rays_by_kind[k] - k0[k] for k in k0}
         srv2.close()
@@ -986,7 +990,11 @@ def main():
         return
     if args.mc_only:
         import torch
-        print(json.dumps({"mc": mc_leg(args, torch.device("cuda", 0))}), flush=True)
+        from paper_2412_15867_gb300 import _lib
+        dev = torch.device("cuda", 0)
+        probe = fp32_probe(_lib.lib(), dev, 0)
+        print(json.dumps({"mc": mc_leg(args, dev, probe["tflops"], measured_peaks()["hbm_gbs"],
+                                       cpu=not args.no_cpu)}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

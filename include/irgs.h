@@ -464,11 +464,14 @@ typedef enum { IRGS_JOB_RENDER = 0, IRGS_JOB_RELIGHT = 1 } irgs_job_kind;
 
 /* One request of a serving step. Device pointers; the caller owns them.
  *   render : feat [P, render.feat_count], depth [P], opacity [P] (Eq. 8).
- *   relight: gbuffer [P, 16] (written by G-buffer tiles, read by shade
- *            tiles: x(3) n(3) albedo(3) roughness w_o(3) valid opacity -),
+ *   relight: gbuffer, 16 P floats written by G-buffer tiles and read by
+ *            shade tiles, planar: x [P, 3], then n [P, 3], albedo [P, 3],
+ *            roughness [P], w_o [P, 3], valid [P] (1 where the opacity
+ *            exceeds 0.5), opacity [P] and [P] unused, one after the other;
  *            rgb [P, 3] (Eq. 15 with n_diffuse cosine + n_spec GGX samples
  *            per pixel against env [env_h, env_w, 3], random stream `seed`,
- *            stream point = pixel index p; background pixels get 0).
+ *            stream point = pixel index p, exactly as irgs_shade_mc keys
+ *            point p; pixels whose valid entry is 0 get 0).
  * P = width x height of the camera. Render and G-buffer tiles trace the
  * camera's ray of pixel p, or, when ray_o and ray_d are both non-NULL, the
  * caller's ray p of ray_o / ray_d [P, 3] (the camera then only sets P). */
@@ -524,10 +527,13 @@ irgs_status irgs_server_staging(irgs_server server, irgs_job** jobs, irgs_tile**
 /*
  * Run one step: validate the first n_jobs / n_tiles table entries, copy the
  * tables to the device and launch one persistent kernel whose blocks pull
- * tiles until none is left. With use_graph != 0 the copy, counter reset and
- * launch are captured into a CUDA graph on the first such call and replayed
- * afterwards. Ordered after prior work on `stream`; later work on `stream`
- * waits for the step. Returns once the work is enqueued.
+ * the render and G-buffer tiles until none is left. With use_graph != 0 the
+ * copy, counter reset and launch are captured into a CUDA graph on the first
+ * such call and replayed afterwards. The shade tiles follow: each run of
+ * consecutive tiles of one job over consecutive points is shaded by the
+ * wavefront path of irgs_shade_mc (scratch from the stream-ordered
+ * allocator, as there). Ordered after prior work on `stream`; later work on
+ * `stream` waits for the step. Returns once the work is enqueued.
  */
 irgs_status irgs_server_step(irgs_server server, int32_t n_jobs, int32_t n_tiles, int32_t use_graph,
                              void* stream);

@@ -382,6 +382,184 @@ static double factorial_d(int k)
     return f;
 }
 
+/* Work arrays of ray_alternatives (capacity n each, plus one row of C). */
+typedef struct { alt64* L; int64_t* base; int64_t* ord; unsigned char* use; double* C; } alt_work;
+
+static int alt_work_init(alt_work* w, int64_t n, int fc)
+{
+    size_t cap = (size_t)(n > 0 ? n : 1);
+    w->L = (alt64*)malloc(sizeof(alt64) * cap);
+    w->base = (int64_t*)malloc(sizeof(int64_t) * cap);
+    w->ord = (int64_t*)malloc(sizeof(int64_t) * cap);
+    w->use = (unsigned char*)malloc(cap);
+    w->C = (double*)malloc(sizeof(double) * (size_t)(fc > 0 ? fc : 1));
+    return w->L && w->base && w->ord && w->use && w->C;
+}
+
+static void alt_work_free(alt_work* w)
+{
+    free(w->L); free(w->base); free(w->ord); free(w->use); free(w->C);
+}
+
+/* The admissible outcomes of one ray (o, d): feat of[max_alts, fc], depth
+ * od, opacity oo, hit count on. Returns their number, or -1 (more than
+ * max_alts outcomes, a run of more than 5 ties or more than 12 optional
+ * candidates) with only the definition's answer in slot 0. */
+static int32_t ray_alternatives(const surfel64* s, int64_t n, const float* feats, int32_t F_total,
+                                const double o[3], const double d[3], const oracle_params* P,
+                                const oracle_margins* M, int32_t max_alts, alt_work* wk,
+                                double* of, double* od, double* oo, int32_t* on)
+{
+    const int fc = P->feat_count;
+    alt64* L = wk->L;
+    int64_t* base = wk->base;
+    int64_t* ord = wk->ord;
+    unsigned char* use = wk->use;
+    double* C = wk->C;
+    double dn = sqrt(dot3(d, d));
+    int64_t nl = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        const surfel64* S = &s[i];
+        cand64 c;
+        if (S->rc2 < 0.0) continue;
+        int meets = intersect(S, o, d, &c);
+        if (c.den == 0.0) continue;
+        int near_graze = fabs(c.den) < 2e-8 * dn;
+        if (!meets && fabs(c.den) < 0.5e-8 * dn) continue;
+        double rc2 = S->rc2 > 1e-12 ? S->rc2 : 1e-12;
+        /* rejected whichever way a rounding goes */
+        if (c.rho2 > S->rc2 + M->rho_rel * rc2) continue;
+        if (c.alpha_raw < P->alpha_min - M->alpha_abs) continue;
+        if (!(c.tau > P->t_min - M->t_abs) || !(c.tau < P->t_max + M->t_abs)) continue;
+        double alpha = c.alpha_raw < P->alpha_max ? c.alpha_raw : P->alpha_max;
+        int accepted = meets && c.rho2 <= S->rc2 && alpha >= P->alpha_min
+                       && c.tau > P->t_min && c.tau < P->t_max;
+        int ambiguous = !meets || near_graze || fabs(c.rho2 - S->rc2) < M->rho_rel * rc2
+                        || fabs(c.alpha_raw - P->alpha_min) < M->alpha_abs
+                        || fabs(c.tau - P->t_min) < M->t_abs
+                        || (isfinite(P->t_max) && fabs(c.tau - P->t_max) < M->t_abs);
+        if (!accepted && !ambiguous) continue;
+        L[nl].tau = c.tau;
+        L[nl].alpha = alpha;
+        L[nl].id = i;
+        L[nl].optional = ambiguous;
+        L[nl].def_in = accepted;
+        nl++;
+    }
+    qsort(L, (size_t)nl, sizeof(alt64), alt_cmp);
+    for (int64_t i = 0; i < nl; ++i) base[i] = i;
+    /* farthest stop: every optional candidate out, the lower threshold */
+    double D, Tf;
+    double Tlo = P->T_min * (1.0 - 2.0 * M->T_rel);
+    int64_t far = 0;
+    {
+        double T = 1.0;
+        int64_t i = 0;
+        for (; i < nl; ++i) {
+            if (L[i].optional) continue;
+            T *= (1.0 - L[i].alpha);
+            if (T < Tlo) break;
+        }
+        far = i < nl ? i : nl - 1;   /* index of the farthest possible stop hit */
+    }
+    int64_t kept = nl;
+    if (nl > 0) {
+        kept = far + 1;
+        while (kept < nl) {
+            double t = fabs(L[kept - 1].tau) > 1.0 ? fabs(L[kept - 1].tau) : 1.0;
+            if (fabs(L[kept].tau - L[kept - 1].tau) < M->tie_abs * t) kept++;
+            else break;
+        }
+    }
+    /* optional candidates and runs of near-equal depths among the kept entries */
+    int n_opt = 0;
+    int opt_idx[12];
+    int64_t run_start[64];
+    int run_len[64];
+    int n_runs = 0;
+    int unresolved = 0;
+    for (int64_t i = 0; i < kept; ++i) {
+        if (L[i].optional) {
+            if (n_opt < 12) opt_idx[n_opt] = (int)i;
+            n_opt++;
+        }
+    }
+    for (int64_t i = 0; i + 1 < kept;) {
+        int64_t j = i;
+        while (j + 1 < kept) {
+            double t = fabs(L[j].tau) > 1.0 ? fabs(L[j].tau) : 1.0;
+            if (fabs(L[j + 1].tau - L[j].tau) < M->tie_abs * t) j++;
+            else break;
+        }
+        if (j > i) {
+            if (n_runs < 64 && j - i + 1 <= 5) {
+                run_start[n_runs] = i;
+                run_len[n_runs] = (int)(j - i + 1);
+            }
+            n_runs++;
+            if (j - i + 1 > 5) unresolved = 1;
+        }
+        i = j + 1;
+    }
+    double n_var = ldexp(1.0, n_opt > 12 ? 12 : n_opt);
+    for (int q = 0; q < n_runs && q < 64; ++q) n_var *= factorial_d(run_len[q]);
+    if (n_opt > 12 || n_runs > 64 || n_var > (double)max_alts) unresolved = 1;
+    int32_t cnt = 0;
+    for (int64_t v = 0; v < (unresolved ? 1 : (int64_t)n_var); ++v) {
+        /* selection: bit b of v flips the definition's decision on
+         * optional candidate b (v = 0 is the definition's answer) */
+        for (int64_t i = 0; i < kept; ++i) use[i] = (unsigned char)L[i].def_in;
+        int64_t rest = v;
+        if (!unresolved) {
+            for (int b = 0; b < n_opt; ++b) {
+                if (rest & 1) use[opt_idx[b]] = (unsigned char)!L[opt_idx[b]].def_in;
+                rest >>= 1;
+            }
+        }
+        /* order: each run of near-equal depths permuted by its
+         * Lehmer code (code 0 = the definition's (tau, id) order) */
+        for (int64_t i = 0; i < kept; ++i) ord[i] = base[i];
+        if (!unresolved) {
+            for (int q = 0; q < n_runs; ++q) {
+                int len = run_len[q];
+                double f = factorial_d(len);
+                int64_t code = rest % (int64_t)f;
+                rest /= (int64_t)f;
+                int avail[5];
+                for (int a = 0; a < len; ++a) avail[a] = a;
+                int left = len;
+                for (int a = 0; a < len; ++a) {
+                    int64_t fa = (int64_t)factorial_d(len - 1 - a);
+                    int pick = (int)(code / fa);
+                    code %= fa;
+                    ord[run_start[q] + a] = run_start[q] + avail[pick];
+                    for (int z = pick; z + 1 < left; ++z) avail[z] = avail[z + 1];
+                    left--;
+                }
+            }
+        }
+        int nearT = 0;
+        int64_t nc = alt_composite(L, ord, use, kept, feats, F_total, P, P->T_min, M->T_rel, C, &D, &Tf, &nearT);
+        double thr[3] = {P->T_min, P->T_min * (1.0 + 2.0 * M->T_rel), P->T_min * (1.0 - 2.0 * M->T_rel)};
+        int nthr = nearT ? 3 : 1;
+        for (int t = 0; t < nthr; ++t) {
+            if (t > 0)
+                nc = alt_composite(L, ord, use, kept, feats, F_total, P, thr[t], M->T_rel, C, &D, &Tf, NULL);
+            if (cnt >= max_alts) {
+                unresolved = 1;
+                break;
+            }
+            for (int c = 0; c < fc; ++c) of[(size_t)cnt * fc + c] = C[c];
+            od[cnt] = D;
+            oo[cnt] = 1.0 - Tf;
+            on[cnt] = (int32_t)nc;
+            cnt++;
+        }
+        if (unresolved && v > 0) break;
+    }
+    return unresolved ? -1 : cnt;
+}
+
 /* For R rays: the admissible outcomes (feat [R, max_alts, feat_count],
  * depth / opacity [R, max_alts], n_hits [R, max_alts]) and their number
  * count[R] (-1: more than max_alts outcomes, or a run of more than 5 ties or
@@ -404,13 +582,8 @@ int oracle_trace_alternatives(const float* means, const float* quats, const floa
     int err = 0;
 #pragma omp parallel
     {
-        size_t cap = (size_t)(n > 0 ? n : 1);
-        alt64* L = (alt64*)malloc(sizeof(alt64) * cap);
-        int64_t* base = (int64_t*)malloc(sizeof(int64_t) * cap);
-        int64_t* ord = (int64_t*)malloc(sizeof(int64_t) * cap);
-        unsigned char* use = (unsigned char*)malloc(cap);
-        double* C = (double*)malloc(sizeof(double) * (size_t)(fc > 0 ? fc : 1));
-        if (!L || !base || !ord || !use || !C) {
+        alt_work wk;
+        if (!alt_work_init(&wk, n, fc)) {
 #pragma omp atomic write
             err = 1;
         } else {
@@ -418,158 +591,13 @@ int oracle_trace_alternatives(const float* means, const float* quats, const floa
             for (int64_t r = 0; r < R; ++r) {
                 double o[3] = {ray_o[3 * r], ray_o[3 * r + 1], ray_o[3 * r + 2]};
                 double d[3] = {ray_d[3 * r], ray_d[3 * r + 1], ray_d[3 * r + 2]};
-                double dn = sqrt(dot3(d, d));
-                int64_t nl = 0;
-                for (int64_t i = 0; i < n; ++i) {
-                    const surfel64* S = &s[i];
-                    cand64 c;
-                    if (S->rc2 < 0.0) continue;
-                    int meets = intersect(S, o, d, &c);
-                    if (c.den == 0.0) continue;
-                    int near_graze = fabs(c.den) < 2e-8 * dn;
-                    if (!meets && fabs(c.den) < 0.5e-8 * dn) continue;
-                    double rc2 = S->rc2 > 1e-12 ? S->rc2 : 1e-12;
-                    /* rejected whichever way a rounding goes */
-                    if (c.rho2 > S->rc2 + M->rho_rel * rc2) continue;
-                    if (c.alpha_raw < P->alpha_min - M->alpha_abs) continue;
-                    if (!(c.tau > P->t_min - M->t_abs) || !(c.tau < P->t_max + M->t_abs)) continue;
-                    double alpha = c.alpha_raw < P->alpha_max ? c.alpha_raw : P->alpha_max;
-                    int accepted = meets && c.rho2 <= S->rc2 && alpha >= P->alpha_min
-                                   && c.tau > P->t_min && c.tau < P->t_max;
-                    int ambiguous = !meets || near_graze || fabs(c.rho2 - S->rc2) < M->rho_rel * rc2
-                                    || fabs(c.alpha_raw - P->alpha_min) < M->alpha_abs
-                                    || fabs(c.tau - P->t_min) < M->t_abs
-                                    || (isfinite(P->t_max) && fabs(c.tau - P->t_max) < M->t_abs);
-                    if (!accepted && !ambiguous) continue;
-                    L[nl].tau = c.tau;
-                    L[nl].alpha = alpha;
-                    L[nl].id = i;
-                    L[nl].optional = ambiguous;
-                    L[nl].def_in = accepted;
-                    nl++;
-                }
-                qsort(L, (size_t)nl, sizeof(alt64), alt_cmp);
-                for (int64_t i = 0; i < nl; ++i) base[i] = i;
-                /* farthest stop: every optional candidate out, the lower threshold */
-                for (int64_t i = 0; i < nl; ++i) use[i] = (unsigned char)!L[i].optional;
-                double D, Tf;
-                double Tlo = P->T_min * (1.0 - 2.0 * M->T_rel);
-                int64_t far = 0;
-                {
-                    double T = 1.0;
-                    int64_t i = 0;
-                    for (; i < nl; ++i) {
-                        if (!use[i]) continue;
-                        T *= (1.0 - L[i].alpha);
-                        if (T < Tlo) break;
-                    }
-                    far = i < nl ? i : nl - 1;   /* index of the farthest possible stop hit */
-                }
-                int64_t kept = nl;
-                if (nl > 0) {
-                    kept = far + 1;
-                    while (kept < nl) {
-                        double t = fabs(L[kept - 1].tau) > 1.0 ? fabs(L[kept - 1].tau) : 1.0;
-                        if (fabs(L[kept].tau - L[kept - 1].tau) < M->tie_abs * t) kept++;
-                        else break;
-                    }
-                }
-                /* optional candidates and runs of near-equal depths among the kept entries */
-                int n_opt = 0;
-                int opt_idx[12];
-                int64_t run_start[64];
-                int run_len[64];
-                int n_runs = 0;
-                int unresolved = 0;
-                for (int64_t i = 0; i < kept; ++i) {
-                    if (L[i].optional) {
-                        if (n_opt < 12) opt_idx[n_opt] = (int)i;
-                        n_opt++;
-                    }
-                }
-                for (int64_t i = 0; i + 1 < kept;) {
-                    int64_t j = i;
-                    while (j + 1 < kept) {
-                        double t = fabs(L[j].tau) > 1.0 ? fabs(L[j].tau) : 1.0;
-                        if (fabs(L[j + 1].tau - L[j].tau) < M->tie_abs * t) j++;
-                        else break;
-                    }
-                    if (j > i) {
-                        if (n_runs < 64 && j - i + 1 <= 5) {
-                            run_start[n_runs] = i;
-                            run_len[n_runs] = (int)(j - i + 1);
-                        }
-                        n_runs++;
-                        if (j - i + 1 > 5) unresolved = 1;
-                    }
-                    i = j + 1;
-                }
-                double n_var = ldexp(1.0, n_opt > 12 ? 12 : n_opt);
-                for (int q = 0; q < n_runs && q < 64; ++q) n_var *= factorial_d(run_len[q]);
-                if (n_opt > 12 || n_runs > 64 || n_var > (double)max_alts) unresolved = 1;
-                int32_t cnt = 0;
-                double* of = out_feat + (size_t)r * max_alts * (fc > 0 ? fc : 0);
-                double* od = out_depth + (size_t)r * max_alts;
-                double* oo = out_opacity + (size_t)r * max_alts;
-                int32_t* on = out_nhits + (size_t)r * max_alts;
-                for (int64_t v = 0; v < (unresolved ? 1 : (int64_t)n_var); ++v) {
-                    /* selection: bit b of v flips the definition's decision on
-                     * optional candidate b (v = 0 is the definition's answer) */
-                    for (int64_t i = 0; i < kept; ++i) use[i] = (unsigned char)L[i].def_in;
-                    int64_t rest = v;
-                    if (!unresolved) {
-                        for (int b = 0; b < n_opt; ++b) {
-                            if (rest & 1) use[opt_idx[b]] = (unsigned char)!L[opt_idx[b]].def_in;
-                            rest >>= 1;
-                        }
-                    }
-                    /* order: each run of near-equal depths permuted by its
-                     * Lehmer code (code 0 = the definition's (tau, id) order) */
-                    for (int64_t i = 0; i < kept; ++i) ord[i] = base[i];
-                    if (!unresolved) {
-                        for (int q = 0; q < n_runs; ++q) {
-                            int len = run_len[q];
-                            double f = factorial_d(len);
-                            int64_t code = rest % (int64_t)f;
-                            rest /= (int64_t)f;
-                            int avail[5];
-                            for (int a = 0; a < len; ++a) avail[a] = a;
-                            int left = len;
-                            for (int a = 0; a < len; ++a) {
-                                int64_t fa = (int64_t)factorial_d(len - 1 - a);
-                                int pick = (int)(code / fa);
-                                code %= fa;
-                                ord[run_start[q] + a] = run_start[q] + avail[pick];
-                                for (int z = pick; z + 1 < left; ++z) avail[z] = avail[z + 1];
-                                left--;
-                            }
-                        }
-                    }
-                    int nearT = 0;
-                    int64_t nc = alt_composite(L, ord, use, kept, feats, F_total, P, P->T_min, M->T_rel, C, &D,
-                                               &Tf, &nearT);
-                    double thr[3] = {P->T_min, P->T_min * (1.0 + 2.0 * M->T_rel), P->T_min * (1.0 - 2.0 * M->T_rel)};
-                    int nthr = nearT ? 3 : 1;
-                    for (int t = 0; t < nthr; ++t) {
-                        if (t > 0)
-                            nc = alt_composite(L, ord, use, kept, feats, F_total, P, thr[t], M->T_rel, C, &D, &Tf,
-                                               NULL);
-                        if (cnt >= max_alts) {
-                            unresolved = 1;
-                            break;
-                        }
-                        for (int c = 0; c < fc; ++c) of[(size_t)cnt * fc + c] = C[c];
-                        od[cnt] = D;
-                        oo[cnt] = 1.0 - Tf;
-                        on[cnt] = (int32_t)nc;
-                        cnt++;
-                    }
-                    if (unresolved && v > 0) break;
-                }
-                out_count[r] = unresolved ? -1 : cnt;
+                out_count[r] = ray_alternatives(s, n, feats, F_total, o, d, P, M, max_alts, &wk,
+                                                out_feat + (size_t)r * max_alts * (fc > 0 ? fc : 0),
+                                                out_depth + (size_t)r * max_alts, out_opacity + (size_t)r * max_alts,
+                                                out_nhits + (size_t)r * max_alts);
             }
         }
-        free(L); free(base); free(ord); free(use); free(C);
+        alt_work_free(&wk);
     }
     free(s);
     return err ? -1 : 0;
@@ -920,6 +948,37 @@ typedef struct {
  * The gradient keeps the sample directions fixed: d/dr goes through f_s
  * only (d ln(D G)/dr), and each traced ray receives dL/dL_ind = g and
  * dL/dO = -g.L_dir. */
+/* The per-channel factor w_c multiplying L_i of sample sI in the estimate
+ * (Eq. 15 with the split or uniform estimator), and its derivatives by the
+ * albedo and the roughness. Returns 1 for the samples whose traces are
+ * averaged into vis / ind (the cosine samples, or all in uniform mode). */
+static int sample_weight64(int mode, int64_t sI, int32_t n_diffuse, int32_t n_spec, int64_t S, const double nn[3],
+                           const double wo[3], double no, const double a[3], double r, const double wi[3],
+                           const double h[3], double wc[3], double dwc_da[3], double dwc_dr[3])
+{
+    for (int k = 0; k < 3; ++k) { dwc_da[k] = 0.0; dwc_dr[k] = 0.0; }
+    if (mode == MODE_UNIFORM) {
+        double ni = dot3(nn, wi), nh_ = dot3(nn, h), oh = dot3(wo, h);
+        spec_terms t = spec_eval(r, ni, no, nh_, oh);
+        double fs_cos = t.D * t.F * t.G1i * t.G1o / (4.0 * no);     /* f_s (w_i.n) */
+        for (int k = 0; k < 3; ++k) {
+            wc[k] = (2.0 * a[k] * ni + 2.0 * OR_PI * fs_cos) / (double)S;
+            dwc_da[k] = 2.0 * ni / (double)S;
+            dwc_dr[k] = 2.0 * OR_PI * fs_cos * t.dlnf_dr / (double)S;
+        }
+        return 1;
+    }
+    if (sI < n_diffuse) {
+        for (int k = 0; k < 3; ++k) { wc[k] = a[k] / n_diffuse; dwc_da[k] = 1.0 / n_diffuse; }
+        return 1;
+    }
+    double oh = dot3(wo, h), nh_ = dot3(nn, h), ni = dot3(nn, wi);
+    spec_terms t = spec_eval(r, ni, no, nh_, oh);
+    double w = t.F * t.G1i * t.G1o * oh / (no * nh_);
+    for (int k = 0; k < 3; ++k) { wc[k] = w / n_spec; dwc_dr[k] = w / n_spec * t.dlnf_dr; }
+    return 0;
+}
+
 static void shade_point(const surfel64* s, int64_t n, const float* feats, int32_t F_total,
                         const oracle_params* P, const oracle_margins* M, hit64* hits, near64* nears, double* Tl,
                         const double x[3], const double n_raw[3], const double wo_raw[3], const double a[3],
@@ -950,28 +1009,8 @@ static void shade_point(const surfel64* s, int64_t n, const float* feats, int32_
         double Ld[3];
         oracle_env_lookup(env, H, W, wi, Ld);
         double Li[3] = {V * Ld[0] + C[0], V * Ld[1] + C[1], V * Ld[2] + C[2]};
-        /* per-channel factor w_c multiplying L_i in the estimate, and d w_c / d r */
-        double wc[3], dwc_dr[3] = {0, 0, 0}, dwc_da[3] = {0, 0, 0};
-        int aux = 0;
-        if (mode == MODE_UNIFORM) {
-            double ni = dot3(nn, wi), nh_ = dot3(nn, h), oh = dot3(wo, h);
-            spec_terms t = spec_eval(r, ni, no, nh_, oh);
-            double fs_cos = t.D * t.F * t.G1i * t.G1o / (4.0 * no);     /* f_s (w_i.n) */
-            for (int k = 0; k < 3; ++k) {
-                wc[k] = (2.0 * a[k] * ni + 2.0 * OR_PI * fs_cos) / (double)S;
-                dwc_da[k] = 2.0 * ni / (double)S;
-                dwc_dr[k] = 2.0 * OR_PI * fs_cos * t.dlnf_dr / (double)S;
-            }
-            aux = 1;
-        } else if (sI < n_diffuse) {
-            for (int k = 0; k < 3; ++k) { wc[k] = a[k] / n_diffuse; dwc_da[k] = 1.0 / n_diffuse; }
-            aux = 1;
-        } else {
-            double oh = dot3(wo, h), nh_ = dot3(nn, h), ni = dot3(nn, wi);
-            spec_terms t = spec_eval(r, ni, no, nh_, oh);
-            double w = t.F * t.G1i * t.G1o * oh / (no * nh_);
-            for (int k = 0; k < 3; ++k) { wc[k] = w / n_spec; dwc_dr[k] = w / n_spec * t.dlnf_dr; }
-        }
+        double wc[3], dwc_dr[3], dwc_da[3];
+        int aux = sample_weight64(mode, sI, n_diffuse, n_spec, S, nn, wo, no, a, r, wi, h, wc, dwc_da, dwc_dr);
         for (int k = 0; k < 3; ++k) acc[k] += wc[k] * Li[k];
         if (aux) {
             for (int k = 0; k < 3; ++k) sum_i[k] += C[k];
@@ -1071,6 +1110,91 @@ int oracle_shade(const float* means, const float* quats, const float* scales, co
             }
         }
         free(hits); free(nears); free(Tl);
+    }
+    free(s);
+    return err ? -1 : 0;
+}
+
+/* Admissible range of each point's estimate: every traced sample is one of
+ * its ray's admissible outcomes (ray_alternatives), and the estimate is the
+ * sum of the samples' terms w_c L_i (sample_weight64), so each channel lies
+ * between the sums of the per-sample minima and maxima over the outcomes.
+ * Outputs rgb_lo, rgb_hi [P, 3] (equal for a point with no ambiguous ray)
+ * and unresolved [P] (samples whose outcomes could not all be listed; only
+ * the definition's term enters for them). Returns 0, or -1 on bad
+ * arguments. */
+int oracle_shade_bounds(const float* means, const float* quats, const float* scales, const float* opacity,
+                        const float* feats, int64_t n, int32_t F_total,
+                        const float* x_in, const float* n_in, const float* albedo, const float* rough,
+                        const float* wo_in, int64_t Pn, const float* env, int32_t env_h, int32_t env_w,
+                        int32_t n_diffuse, int32_t n_spec, int32_t mode, uint64_t seed, const int64_t* point_ids,
+                        const oracle_params* P, const oracle_margins* M, int32_t max_alts, double* rgb_lo,
+                        double* rgb_hi, int32_t* unresolved, int n_threads)
+{
+    if (!shade_args_ok(n, Pn, P, F_total, n_diffuse, n_spec, mode) || !M || max_alts < 1) return -1;
+    surfel64* s = (surfel64*)malloc(sizeof(surfel64) * (size_t)(n > 0 ? n : 1));
+    if (!s) return -1;
+    load_surfels(means, quats, scales, opacity, n, P->alpha_min, s);
+    nthreads_set(n_threads);
+    int err = 0;
+#pragma omp parallel
+    {
+        alt_work wk;
+        double* of = (double*)malloc(sizeof(double) * 3 * (size_t)max_alts);
+        double* od = (double*)malloc(sizeof(double) * (size_t)max_alts);
+        double* oo = (double*)malloc(sizeof(double) * (size_t)max_alts);
+        int32_t* on = (int32_t*)malloc(sizeof(int32_t) * (size_t)max_alts);
+        if (!alt_work_init(&wk, n, 3) || !of || !od || !oo || !on) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t p = 0; p < Pn; ++p) {
+                double x[3] = {x_in[3 * p], x_in[3 * p + 1], x_in[3 * p + 2]};
+                double nn[3] = {n_in[3 * p], n_in[3 * p + 1], n_in[3 * p + 2]};
+                double wo[3] = {wo_in[3 * p], wo_in[3 * p + 1], wo_in[3 * p + 2]};
+                double a[3] = {albedo[3 * p], albedo[3 * p + 1], albedo[3 * p + 2]};
+                double r = rough[p];
+                int64_t key = point_ids ? point_ids[p] : p;
+                normalize3(nn);
+                normalize3(wo);
+                if (dot3(nn, wo) <= 0.0) { nn[0] = -nn[0]; nn[1] = -nn[1]; nn[2] = -nn[2]; }
+                const int64_t S = (int64_t)n_diffuse + n_spec;
+                double no = dot3(nn, wo);
+                double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+                int32_t unres = 0;
+                for (int64_t sI = 0; sI < S; ++sI) {
+                    double wi[3], h[3];
+                    if (!sample_direction(seed, key, sI, S, n_diffuse, mode, nn, wo, r, wi, h)) continue;
+                    int32_t cnt = ray_alternatives(s, n, feats, F_total, x, wi, P, M, max_alts, &wk, of, od, oo, on);
+                    if (cnt < 0) {
+                        unres++;
+                        cnt = 1;
+                    }
+                    double Ld[3], wc[3], dwa[3], dwr[3];
+                    oracle_env_lookup(env, env_h, env_w, wi, Ld);
+                    sample_weight64(mode, sI, n_diffuse, n_spec, S, nn, wo, no, a, r, wi, h, wc, dwa, dwr);
+                    for (int k = 0; k < 3; ++k) {
+                        double mn = INFINITY, mx = -INFINITY;
+                        for (int32_t j = 0; j < cnt; ++j) {
+                            double V = 1.0 - oo[j];
+                            double term = wc[k] * (V * Ld[k] + of[3 * j + k]);
+                            mn = term < mn ? term : mn;
+                            mx = term > mx ? term : mx;
+                        }
+                        lo[k] += mn;
+                        hi[k] += mx;
+                    }
+                }
+                for (int k = 0; k < 3; ++k) {
+                    rgb_lo[3 * p + k] = lo[k];
+                    rgb_hi[3 * p + k] = hi[k];
+                }
+                if (unresolved) unresolved[p] = unres;
+            }
+        }
+        alt_work_free(&wk);
+        free(of); free(od); free(oo); free(on);
     }
     free(s);
     return err ? -1 : 0;

@@ -174,7 +174,8 @@ irgs_status launch_shade_mc(const SceneView& sv, const float* x, const float* n,
 irgs_status launch_shade_wave(const SceneView& sv, const uint32_t* bounds, const float* x, const float* n,
                               const float* albedo, const float* rough, const float* wo, int64_t P, const float* env,
                               int32_t H, int32_t W, int32_t n_diffuse, int32_t n_spec, uint64_t seed, int mode,
-                              const irgs_trace_params& p, float* rgb, float* vis, float* ind, cudaStream_t st);
+                              const irgs_trace_params& p, float* rgb, float* vis, float* ind, cudaStream_t st,
+                              uint64_t key_base = 0, const float* valid = nullptr);
 irgs_status launch_shade_wave_backward(const SceneView& sv, const int32_t* perm, const uint32_t* bounds,
                                        const float* x, const float* n, const float* albedo, const float* rough,
                                        const float* wo, int64_t P, const float* env, int32_t H, int32_t W,

@@ -1,9 +1,13 @@
-// Serving: one persistent launch per scheduling step processes tiles of many
-// requests over several resident scenes. Blocks pull tiles from the step's
-// tile table with an atomic counter until it is exhausted; a tile is up to a
-// few thousand camera rays (render / G-buffer) or G-buffer points to shade.
-// The step (staging copy, counter reset, kernel) can be captured once into a
-// CUDA graph and replayed with new table contents.
+// Serving: one persistent launch per scheduling step processes the trace
+// tiles of many requests over several resident scenes. Blocks pull tiles
+// from the step's tile table with an atomic counter until it is exhausted; a
+// tile is up to a few thousand camera rays. The step (staging copy, counter
+// reset, kernel) can be captured once into a CUDA graph and replayed with new
+// table contents. The shading tiles of the step then run, one request's range
+// of G-buffer points at a time, through the wavefront shading path (secondary
+// rays regrouped by direction and origin, traced in that order, estimated
+// per point), keyed by pixel index, so a pixel's estimate is the one
+// irgs_shade_mc gives for it.
 //
 // Work per tile kind (IRGS Eq. 8 for the traces, Eq. 13-15 for shading):
 //   render  : camera rays (or the request's own rays) -> Trace -> feat /
@@ -13,7 +17,7 @@
 //             opacity (Eq. 9): x = o + (D/O) d, n, a, r, w_o = -d;
 //   shade   : G-buffer points -> Monte Carlo rendering equation.
 // Each result depends only on its own request (camera, seed, pixel index),
-// never on what else shares the launch.
+// never on what else shares the step.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -37,6 +41,9 @@ struct irgs_server_s {
     int* dev_next = nullptr;
     int grid = 0;
     irgs::TraceParams render{}, gbuf{}, shade{};
+    irgs_trace_params shade_params{};
+    irgs::SceneView* host_views = nullptr;     // [n_scenes] the scenes' views and bounds, for the shading calls
+    const uint32_t** host_bounds = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -84,7 +91,6 @@ __global__ void __launch_bounds__(kServeThreads) k_serve(ServeArgs A) {
     static_assert(kServeThreads == trace_threads<kServeK>(), "k-buffer slots are laid out per block thread");
     __shared__ int s_tile;
     const int n_tiles = A.header[1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(A.next_tile, 1);
         __syncthreads();
@@ -120,42 +126,33 @@ __global__ void __launch_bounds__(kServeThreads) k_serve(ServeArgs A) {
                     job.depth[p] = st.D;
                     job.opacity[p] = 1.f - st.T;
                 } else {
-                    // Eq. 9 normalisation by the accumulated opacity
+                    // Eq. 9 normalisation by the accumulated opacity, into the
+                    // planar G-buffer of P = width x height pixels
+                    const int64_t Pj = (int64_t)job.cam.width * job.cam.height;
                     const float O = 1.f - st.T;
-                    float* g = job.gbuffer + p * 16;
+                    float* g = job.gbuffer;
                     const bool valid = O > 0.5f;
                     const float inv = valid ? 1.f / O : 0.f;
                     const f3 x = add3(o, mul3(d, st.D * inv));
                     f3 nn = mk3(st.C[4], st.C[5], st.C[6]);
                     const float nl = sqrtf(dot3(nn, nn));
                     nn = nl > 0.f ? mul3(nn, 1.f / nl) : mk3(0.f, 0.f, 1.f);
-                    g[0] = x.x; g[1] = x.y; g[2] = x.z;
-                    g[3] = nn.x; g[4] = nn.y; g[5] = nn.z;
-                    g[6] = st.C[0] * inv; g[7] = st.C[1] * inv; g[8] = st.C[2] * inv;
-                    g[9] = st.C[3] * inv;
-                    g[10] = -d.x; g[11] = -d.y; g[12] = -d.z;
-                    g[13] = valid ? 1.f : 0.f;
-                    g[14] = O; g[15] = 0.f;
+                    float* gx = g + 3 * p;
+                    float* gn = g + 3 * Pj + 3 * p;
+                    float* ga = g + 6 * Pj + 3 * p;
+                    float* gw = g + 10 * Pj + 3 * p;
+                    gx[0] = x.x; gx[1] = x.y; gx[2] = x.z;
+                    gn[0] = nn.x; gn[1] = nn.y; gn[2] = nn.z;
+                    ga[0] = st.C[0] * inv; ga[1] = st.C[1] * inv; ga[2] = st.C[2] * inv;
+                    g[9 * Pj + p] = st.C[3] * inv;
+                    gw[0] = -d.x; gw[1] = -d.y; gw[2] = -d.z;
+                    g[13 * Pj + p] = valid ? 1.f : 0.f;
+                    g[14 * Pj + p] = O;
+                    g[15 * Pj + p] = 0.f;
                 }
-            }
-        } else {
-            // one warp per G-buffer point
-            for (int j = warp; j < tile.count; j += kServeThreads / 32) {
-                const int64_t p = (int64_t)tile.first + j;
-                const float* g = job.gbuffer + p * 16;
-                float out[3] = {0.f, 0.f, 0.f};
-                if (g[13] > 0.5f) {
-                    ShadeSums sums;
-                    shade_point_warp<kServeK, false>(S, mk3(g[0], g[1], g[2]), mk3(g[3], g[4], g[5]),
-                                                     mk3(g[10], g[11], g[12]), mk3(g[6], g[7], g[8]), g[9],
-                                                     (uint64_t)p, job.n_diffuse, job.n_spec, kModeSplit, job.seed, job.env,
-                                                     job.env_h, job.env_w, A.shade, sums);
-                    out[0] = sums.rgb[0]; out[1] = sums.rgb[1]; out[2] = sums.rgb[2];
-                }
-                if (lane == 0)
-                    for (int c = 0; c < 3; ++c) job.rgb[3 * p + c] = out[c];
             }
         }
+        // shading tiles run after this kernel through the wavefront path
     }
 }
 
@@ -169,6 +166,8 @@ void server_free(irgs_server s) {
     if (s->dev_stage) cudaFree(s->dev_stage);
     if (s->dev_scenes) cudaFree(s->dev_scenes);
     if (s->dev_next) cudaFree(s->dev_next);
+    delete[] s->host_views;
+    delete[] s->host_bounds;
     delete s;
 }
 
@@ -233,6 +232,17 @@ irgs_status irgs_server_create(const irgs_scene* scenes, int32_t n_scenes, int32
     s->stage_bytes = kHeaderBytes + sizeof(irgs_job) * (size_t)max_jobs + sizeof(irgs_tile) * (size_t)max_tiles;
     s->render = to_params(*render);
     s->shade = to_params(*shade);
+    s->shade_params = *shade;
+    s->host_views = new (std::nothrow) SceneView[n_scenes];
+    s->host_bounds = new (std::nothrow) const uint32_t*[n_scenes];
+    if (!s->host_views || !s->host_bounds) {
+        server_free(s);
+        return IRGS_ERR_OOM;
+    }
+    for (int i = 0; i < n_scenes; ++i) {
+        s->host_views[i] = scenes[i]->view();
+        s->host_bounds[i] = scenes[i]->bounds;
+    }
     s->gbuf = s->render;
     s->gbuf.off = material_offset;
     s->gbuf.fc = 7;
@@ -295,7 +305,7 @@ irgs_status irgs_server_step(irgs_server s, int32_t n_jobs, int32_t n_tiles, int
         if (tl.kind == IRGS_TILE_GBUFFER && !jb.gbuffer) return IRGS_ERR_INVALID_ARG;
         if (tl.kind == IRGS_TILE_SHADE &&
             (!jb.gbuffer || !jb.rgb || !jb.env || jb.env_h <= 0 || jb.env_w <= 0 || jb.n_diffuse < 0 || jb.n_spec < 0 ||
-             jb.n_diffuse + jb.n_spec <= 0))
+             jb.n_diffuse + jb.n_spec <= 0 || jb.n_diffuse + jb.n_spec > (1 << 24)))
             return IRGS_ERR_INVALID_ARG;
     }
     int32_t* hdr = reinterpret_cast<int32_t*>(s->host_stage);
@@ -325,13 +335,38 @@ irgs_status irgs_server_step(irgs_server s, int32_t n_jobs, int32_t n_tiles, int
         }
     }
     count_launches(1);
+    // shading tiles: each maximal run of consecutive tiles of one job over
+    // consecutive points is one wavefront call on its G-buffer range
+    irgs_status ss = IRGS_OK;
+    for (int t = 0; t < n_tiles && e == cudaSuccess && ss == IRGS_OK;) {
+        const irgs_tile& tl = tiles[t];
+        if (tl.kind != IRGS_TILE_SHADE) {
+            ++t;
+            continue;
+        }
+        int64_t first = tl.first, count = tl.count;
+        int u = t + 1;
+        while (u < n_tiles && tiles[u].kind == IRGS_TILE_SHADE && tiles[u].job == tl.job &&
+               tiles[u].first == first + count) {
+            count += tiles[u].count;
+            ++u;
+        }
+        const irgs_job& jb = jobs[tl.job];
+        const int64_t Pj = (int64_t)jb.cam.width * jb.cam.height;
+        const float* g = jb.gbuffer;
+        ss = launch_shade_wave(s->host_views[jb.scene], s->host_bounds[jb.scene], g + 3 * first, g + 3 * Pj + 3 * first,
+                               g + 6 * Pj + 3 * first, g + 9 * Pj + first, g + 10 * Pj + 3 * first, count, jb.env,
+                               jb.env_h, jb.env_w, jb.n_diffuse, jb.n_spec, jb.seed, kModeSplit, s->shade_params,
+                               jb.rgb + 3 * first, nullptr, nullptr, s->stream, (uint64_t)first, g + 13 * Pj + first);
+        t = u;
+    }
     if (e == cudaSuccess) e = cudaEventRecord(s->ev_out, s->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(caller, s->ev_out, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return IRGS_ERR_CUDA;
     }
-    return IRGS_OK;
+    return ss;
 }
 
 irgs_status irgs_server_destroy(irgs_server s) {

@@ -41,16 +41,25 @@ __device__ __forceinline__ f3 ld3w(const float* p, int64_t i) { return mk3(p[3 *
 
 // One thread per sample of points [p0, p0 + rays / St): direction (w = 1 if
 // the sample is valid) and its regrouping key (invalid samples sort last).
+// Point p draws the random numbers of point number key_base + p; a point
+// whose `valid` entry (if given) is not above 0.5 traces nothing.
 __global__ void k_wave_gen(const float* __restrict__ xg, const float* __restrict__ ng, const float* __restrict__ rg,
                            const float* __restrict__ wog, int64_t p0, int64_t rays, int St, int nd, int mode,
                            uint64_t seed, const uint32_t* __restrict__ bounds, float4* __restrict__ dir,
-                           uint32_t* __restrict__ key, int32_t* __restrict__ val) {
+                           uint32_t* __restrict__ key, int32_t* __restrict__ val, uint64_t key_base,
+                           const float* __restrict__ valid) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= rays) return;
     const int64_t p = p0 + i / St;
     const int s = (int)(i % St);
+    if (valid != nullptr && !(valid[p] > 0.5f)) {
+        dir[i] = make_float4(0.f, 0.f, 1.f, 0.f);
+        key[i] = kInvalidWaveKey;
+        val[i] = (int32_t)i;
+        return;
+    }
     const ShadeFrame F = shade_frame(ld3w(ng, p), ld3w(wog, p), rg[p]);
-    const ShadeSample d = draw_sample(F, mode, (uint64_t)p, s, St, nd, seed);
+    const ShadeSample d = draw_sample(F, mode, key_base + (uint64_t)p, s, St, nd, seed);
     dir[i] = make_float4(d.wi.x, d.wi.y, d.wi.z, d.valid ? 1.f : 0.f);
     key[i] = d.valid ? wave_key(ld3w(xg, p), d.wi, bounds) : kInvalidWaveKey;
     val[i] = (int32_t)i;
@@ -168,15 +177,22 @@ __global__ void __launch_bounds__(kWaveThreads) k_wave_shade(SceneView S, const 
                                                              const float* __restrict__ env, int H, int W, int nd,
                                                              int ns, int mode, uint64_t seed, TraceParams TP,
                                                              const float4* __restrict__ res, float* __restrict__ rgb,
-                                                             float* __restrict__ vis, float* __restrict__ ind) {
+                                                             float* __restrict__ vis, float* __restrict__ ind,
+                                                             uint64_t key_base, const float* __restrict__ valid) {
     const int lane = threadIdx.x & 31;
     const int64_t k = blockIdx.x * (int64_t)(kWaveThreads / 32) + (threadIdx.x >> 5);
     if (k >= np) return;
     const int64_t p = p0 + k;
     const int St = nd + ns;
     ShadeSums o;
-    shade_point_warp<K, false, true>(S, ld3w(xg, p), ld3w(ng, p), ld3w(wog, p), ld3w(ag, p), rg[p], (uint64_t)p, nd,
-                                     ns, mode, seed, env, H, W, TP, o, res + k * St);
+    if (valid != nullptr && !(valid[p] > 0.5f)) {   // background: no estimate (warp-uniform)
+        o.rgb[0] = o.rgb[1] = o.rgb[2] = 0.f;
+        o.ind[0] = o.ind[1] = o.ind[2] = 0.f;
+        o.vis = 0.f;
+    } else {
+        shade_point_warp<K, false, true>(S, ld3w(xg, p), ld3w(ng, p), ld3w(wog, p), ld3w(ag, p), rg[p],
+                                         key_base + (uint64_t)p, nd, ns, mode, seed, env, H, W, TP, o, res + k * St);
+    }
     if (lane == 0) {
         for (int c = 0; c < 3; ++c) rgb[3 * p + c] = o.rgb[c];
         if (vis != nullptr) vis[p] = o.vis;
@@ -374,7 +390,7 @@ template <int K>
 cudaError_t wave_forward(const SceneView& S, const uint32_t* bounds, const float* x, const float* n, const float* a,
                          const float* r, const float* wo, int64_t P, const float* env, int H, int W, int nd, int ns,
                          int mode, uint64_t seed, const TraceParams& TP, float* rgb, float* vis, float* ind,
-                         cudaStream_t st) {
+                         cudaStream_t st, uint64_t key_base, const float* valid) {
     const int St = nd + ns;
     const int64_t pc = chunk_points(St);
     WaveScratch w;
@@ -384,13 +400,13 @@ cudaError_t wave_forward(const SceneView& S, const uint32_t* bounds, const float
         const int64_t np = P - p0 < pc ? P - p0 : pc;
         const int64_t rays = np * St;
         k_wave_gen<<<grid_for(rays, 256), 256, 0, st>>>(x, n, r, wo, p0, rays, St, nd, mode, seed, bounds, w.dir,
-                                                        w.key, w.val);
+                                                        w.key, w.val, key_base, valid);
         e = sort_pairs(w.key, w.val, w.key_tmp, w.val_tmp, w.hist, rays, st);
         if (e != cudaSuccess) break;
         e = wave_trace<K, false>(S, TP, x, p0, St, rays, w, st);
         if (e != cudaSuccess) break;
         k_wave_shade<K><<<grid_for(np, kWaveThreads / 32), kWaveThreads, 0, st>>>(
-            S, x, n, a, r, wo, p0, np, env, H, W, nd, ns, mode, seed, TP, w.res, rgb, vis, ind);
+            S, x, n, a, r, wo, p0, np, env, H, W, nd, ns, mode, seed, TP, w.res, rgb, vis, ind, key_base, valid);
         count_launches(2);
         e = cudaGetLastError();
     }
@@ -419,7 +435,7 @@ cudaError_t wave_backward(const SceneView& S, const int32_t* perm, const uint32_
         const int64_t np = P - p0 < pc ? P - p0 : pc;
         const int64_t rays = np * St;
         k_wave_gen<<<grid_for(rays, 256), 256, 0, st>>>(x, n, r, wo, p0, rays, St, nd, mode, seed, bounds, w.dir,
-                                                        w.key, w.val);
+                                                        w.key, w.val, 0ull, nullptr);
         e = sort_pairs(w.key, w.val, w.key_tmp, w.val_tmp, w.hist, rays, st);
         if (e != cudaSuccess) break;
         const unsigned g = grid_for(rays, kWaveThreads);
@@ -456,16 +472,17 @@ irgs_status to_status(cudaError_t e) {
 irgs_status launch_shade_wave(const SceneView& S, const uint32_t* bounds, const float* x, const float* n,
                               const float* albedo, const float* rough, const float* wo, int64_t P, const float* env,
                               int32_t H, int32_t W, int32_t n_diffuse, int32_t n_spec, uint64_t seed, int mode,
-                              const irgs_trace_params& p, float* rgb, float* vis, float* ind, cudaStream_t st) {
+                              const irgs_trace_params& p, float* rgb, float* vis, float* ind, cudaStream_t st,
+                              uint64_t key_base, const float* valid) {
     if (P == 0) return IRGS_OK;
     const TraceParams TP = to_params(p);
     switch (p.k) {
         case 8:
             return to_status(wave_forward<8>(S, bounds, x, n, albedo, rough, wo, P, env, H, W, n_diffuse, n_spec,
-                                             mode, seed, TP, rgb, vis, ind, st));
+                                             mode, seed, TP, rgb, vis, ind, st, key_base, valid));
         case 16:
             return to_status(wave_forward<16>(S, bounds, x, n, albedo, rough, wo, P, env, H, W, n_diffuse, n_spec,
-                                              mode, seed, TP, rgb, vis, ind, st));
+                                              mode, seed, TP, rgb, vis, ind, st, key_base, valid));
         default: return IRGS_ERR_UNSUPPORTED;
     }
 }

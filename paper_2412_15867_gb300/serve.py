@@ -44,6 +44,36 @@ class Job(C.Structure):
                 ("gbuffer", C.c_void_p), ("rgb", C.c_void_p), ("ray_o", C.c_void_p), ("ray_d", C.c_void_p)]
 
 
+# Planar G-buffer of a relight request (16 P floats): name -> (first plane, width)
+GBUFFER_LAYOUT = {"x": (0, 3), "n": (3, 3), "albedo": (6, 3), "rough": (9, 1), "wo": (10, 3), "valid": (13, 1),
+                  "opacity": (14, 1)}
+
+
+def gbuffer_views(g: torch.Tensor, P: int) -> dict:
+    """Views of a request's planar G-buffer: x, n, albedo, wo [P, 3]; rough,
+    valid, opacity [P]."""
+    out = {}
+    for k, (o, w) in GBUFFER_LAYOUT.items():
+        v = g[o * P:(o + w) * P]
+        out[k] = v.view(P, 3) if w == 3 else v
+    return out
+
+
+def pack_gbuffer(x, n, albedo, rough, wo, valid=None) -> torch.Tensor:
+    """A planar G-buffer (16 P floats, see gbuffer_views) from device arrays."""
+    P = x.shape[0]
+    g = torch.zeros(16 * P, device=x.device, dtype=torch.float32)
+    v = gbuffer_views(g, P)
+    v["x"].copy_(x)
+    v["n"].copy_(n)
+    v["albedo"].copy_(albedo)
+    v["rough"].copy_(rough.reshape(P))
+    v["wo"].copy_(wo)
+    v["valid"].copy_(torch.ones(P, device=x.device) if valid is None else valid.reshape(P))
+    v["opacity"].fill_(1.0)
+    return g
+
+
 class Tile(C.Structure):
     _fields_ = [("kind", C.c_int32), ("job", C.c_int32), ("first", C.c_int32), ("count", C.c_int32)]
 
@@ -131,8 +161,8 @@ class RenderRequest:
 class RelightRequest:
     """G-buffer of `scene` from the camera at `eye` (or along `rays`), then
     the Monte Carlo rendering equation at its valid pixels with `spp`
-    samples. A caller-made `gbuffer` [width x height, 16] (the layout of
-    irgs_job) skips the G-buffer phase."""
+    samples. A caller-made planar `gbuffer` of 16 x width x height floats
+    (pack_gbuffer, the layout of irgs_job) skips the G-buffer phase."""
     scene: int
     eye: tuple
     width: int
@@ -148,8 +178,8 @@ class RelightRequest:
         _check_rays(self.rays, self.pixels())
         g = self.gbuffer
         if g is not None and not (isinstance(g, torch.Tensor) and g.is_cuda and g.dtype == torch.float32
-                                  and g.is_contiguous() and g.shape == (self.pixels(), 16)):
-            raise ValueError("gbuffer must be a contiguous float32 CUDA tensor [width x height, 16]")
+                                  and g.is_contiguous() and g.numel() == 16 * self.pixels()):
+            raise ValueError("gbuffer must be a contiguous float32 CUDA tensor of 16 x width x height floats")
 
     def pixels(self) -> int:
         return self.width * self.height
@@ -237,7 +267,7 @@ class Server:
                     h.out = {"gbuffer": req.gbuffer, "rgb": torch.empty((P, 3), device=dev)}
                     h.phase = 1
                 else:
-                    h.out = {"gbuffer": torch.empty((P, 16), device=dev), "rgb": torch.empty((P, 3), device=dev)}
+                    h.out = {"gbuffer": torch.empty(16 * P, device=dev), "rgb": torch.empty((P, 3), device=dev)}
             h.admitted = time.perf_counter()
             self.used += h.bytes
             self.active.append(h)
@@ -370,7 +400,9 @@ def run_poisson(server: Server, make_request, rate: float, duration: float, warm
     """Drive `server` with a Poisson stream of `rate` requests/s for
     warmup + duration seconds (arrival times in real time). Requests that
     arrive during the warm-up are served but not reported. Returns
-    (reported handles, wall seconds of the measured window, rays traced in it)."""
+    (reported handles, wall seconds of the measured window, rays traced in it).
+    server.window_stats then holds the window's bounds and how many requests
+    (of any arrival time) completed inside it."""
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
     t_next = t0 + rng.exponential(1.0 / rate)
@@ -394,4 +426,7 @@ def run_poisson(server: Server, make_request, rate: float, duration: float, warm
             time.sleep(min(0.0005, max(0.0, t_next - time.perf_counter())))
     wall = time.perf_counter() - (t0 + warmup)
     rays = sum(h.rays for h in measured)
+    w0, w1 = t0 + warmup, t0 + warmup + duration
+    done_in = sum(1 for h in server.finished if w0 <= h.done < w1)
+    server.window_stats = {"start": w0, "end": w1, "completed_in_window": done_in}
     return measured, wall, rays

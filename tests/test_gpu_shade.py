@@ -5,7 +5,9 @@ traces and the estimator are FP32 on the GPU and FP64 in the oracle. Shaded
 radiance reaches ~50 (bright lobes), so the bar is relative above 1:
 |rgb - ref| <= 1e-4 max(1, |ref|) on points whose traced rays carry no
 ambiguity flag, and on >= 99.9% of all points; 2e-3 max(1,|ref|) on every
-unflagged point."""
+unflagged point. A flagged point must lie, within 1e-4 max(1,|ref|), inside
+the range the oracle admits for it: each of its traced samples is one of its
+ray's admissible outcomes (oracle.shade_bounds)."""
 import numpy as np
 import pytest
 
@@ -25,6 +27,16 @@ def opar(p):
                          t_max=p.t_max, feat_offset=p.feat_offset, feat_count=p.feat_count)
 
 
+def add_bounds(ref, sc, gb, env, nd, ns, seed, p, point_ids=None, mode=oracle.MODE_SPLIT):
+    """The oracle's admissible range of the flagged points' estimates."""
+    idx = np.nonzero(ref["flags"] != 0)[0]
+    keys = idx if point_ids is None else np.asarray(point_ids)[idx]
+    ref["bound_points"] = idx
+    ref["bounds"] = oracle.shade_bounds(sc, *(arr[idx] for arr in gb), env, nd, ns, seed, opar(p),
+                                        point_ids=keys, mode=mode) if idx.size else None
+    return ref
+
+
 def shade_both(sc, gb, env, nd, ns, seed, p, S=None):
     x, n, a, r, wo = gb
     S = S or make_scene(irgs, sc)
@@ -32,7 +44,7 @@ def shade_both(sc, gb, env, nd, ns, seed, p, S=None):
     torch.cuda.synchronize()
     assert S.status() == 0
     ref = oracle.shade(sc, x, n, a, r, wo, env, nd, ns, seed, opar(p))
-    return out, ref
+    return out, add_bounds(ref, sc, gb, env, nd, ns, seed, p)
 
 
 def check(out, ref, frac=0.999):
@@ -44,6 +56,16 @@ def check(out, ref, frac=0.999):
           "max_err_all": float(err.max()), "within": float((err <= 1e-4).mean())}
     assert (err <= 1e-4).mean() >= frac, st
     assert np.all(err[ok] <= 2e-3), st
+    # flagged points: inside the admissible range
+    idx = ref["bound_points"]
+    if idx.size:
+        b = ref["bounds"]
+        tol = 1e-4 * np.maximum(1.0, np.abs(ref["rgb"][idx]).max(1))[:, None]
+        inside = (g[idx] >= b["lo"] - tol) & (g[idx] <= b["hi"] + tol)
+        st.update({"flagged": int(idx.size), "unresolved_samples": int(b["unresolved"].sum()),
+                   "max_range": float((b["hi"] - b["lo"]).max())})
+        assert np.all(inside), ("flagged points outside their admissible range", idx[~inside.all(1)], st)
+        assert b["unresolved"].sum() <= 1e-3 * idx.size * 64, st
     v = out["vis"].cpu().numpy()
     assert np.all(np.abs(v - ref["vis"])[ok] <= 1e-4), st
     ind = out["ind"].cpu().numpy()
@@ -121,7 +143,9 @@ def test_mc_config_full_size_sampled():
     pc = (1 << 24) // 64
     edges = [0, pc - 1, pc, 2 * pc - 1, 2 * pc, 640_000 - 1]
     idx = np.unique(np.concatenate([np.random.default_rng(5).choice(640_000, 32, replace=False), edges]))
-    ref = oracle.shade(sc, *(arr[idx] for arr in gb), env, 32, 32, 2024, opar(p), point_ids=idx)
+    sub_gb = [arr[idx] for arr in gb]
+    ref = oracle.shade(sc, *sub_gb, env, 32, 32, 2024, opar(p), point_ids=idx)
+    add_bounds(ref, sc, sub_gb, env, 32, 32, 2024, p, point_ids=idx)
     it = torch.from_numpy(idx).cuda()
     sub = {k: v[it] for k, v in out.items()}
     print(check(sub, ref, frac=0.95))

@@ -127,3 +127,54 @@ def test_too_many_outcomes_left_unresolved():
     assert c == -1
     ref = oracle.trace(sc, *rays([0, 0, 3], [0, 0, -1]), Params(feat_count=3, T_min=0.0))
     np.testing.assert_array_equal(outs[0][0], ref["feat"][0])
+
+
+def test_shade_bounds_equal_the_estimate_where_nothing_is_ambiguous():
+    sc = synth.object_scene(n=3000, seed=33)
+    gb = synth.gbuffer_points(24, seed=34)
+    env = synth.env_map(seed=35, height=16, width=32)
+    p = Params(feat_count=3, t_min=1e-3)
+    ref = oracle.shade(sc, *gb, env, 8, 8, 7, p)
+    b = oracle.shade_bounds(sc, *gb, env, 8, 8, 7, p)
+    assert np.all(b["lo"] <= ref["rgb"] + 1e-12) and np.all(ref["rgb"] <= b["hi"] + 1e-12)
+    clean = ref["flags"] == 0
+    assert clean.any()
+    np.testing.assert_allclose(b["lo"][clean], ref["rgb"][clean], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(b["hi"][clean], ref["rgb"][clean], rtol=0, atol=1e-12)
+
+
+def test_shade_bounds_span_both_orders_of_a_near_tie():
+    # a point under two large parallel canopy disks 1e-9 apart in height:
+    # every upward sample meets both at near-equal depths, so either order
+    # is admissible; with f1 = red and f2 = green the two orders' indirect
+    # light is (a1, (1 - a1) a2) or ((1 - a2) a1, a2) for the ray's alphas
+    f1, f2 = [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]
+    sc = scene([[0, 0, 1.0], [0, 0, 1.0 + 1e-9]], [Q, Q], [[10.0, 10.0]] * 2, [0.5, 0.7], [f1, f2])
+    x = np.zeros((1, 3), np.float32)
+    n = np.array([[0, 0, 1.0]], np.float32)
+    alb = np.array([[0.5, 0.6, 0.7]], np.float32)
+    rough = np.array([0.5], np.float32)
+    L = np.array([1.5, 0.5, 0.25], np.float32)
+    env = np.tile(L, (8, 16, 1)).astype(np.float32)
+    p = Params(feat_count=3, t_min=1e-3)
+    nd = 16
+    b = oracle.shade_bounds(sc, x, n, alb, rough, n, env, nd, 0, 11, p)
+    ref = oracle.shade(sc, x, n, alb, rough, n, env, nd, 0, 11, p)
+    # the per-sample definitions from the oracle's own trace of the same directions
+    dirs, valid = oracle.sample_dirs(n, n, rough, nd, 0, 11)
+    d = dirs[0][valid[0]]
+    tr = oracle.trace(sc, np.zeros_like(d, dtype=np.float32), d.astype(np.float32), p)
+    a1 = tr["feat"][:, 0]
+    a2 = tr["feat"][:, 1] / (1 - a1)
+    V = 1 - tr["opacity"]
+    assert np.all(a1 > 0.4) and np.all(a2 > 0.5)
+    defn = np.stack([a1, (1 - a1) * a2, 0 * a1], 1)
+    swap = np.stack([(1 - a2) * a1, a2, 0 * a1], 1)
+    t_def = alb[0] * (V[:, None] * L + defn) / nd
+    t_swp = alb[0] * (V[:, None] * L + swap) / nd
+    # (the check trace takes the directions rounded to float32, the
+    # estimate its FP64 directions: agreement to ~1e-9)
+    np.testing.assert_allclose(ref["rgb"][0], t_def.sum(0), rtol=1e-7)
+    np.testing.assert_allclose(b["lo"][0], np.minimum(t_def, t_swp).sum(0), rtol=1e-7)
+    np.testing.assert_allclose(b["hi"][0], np.maximum(t_def, t_swp).sum(0), rtol=1e-7)
+    assert b["hi"][0, 1] - b["lo"][0, 1] > 1e-3
