@@ -303,10 +303,10 @@ class Server:
 
     # ---- one scheduling step
     def step(self) -> bool:
-        """Admit what fits, run one persistent launch over the tiles of the
-        active requests (shortest remaining work first, up to step_rays
-        rays), retire finished requests. Returns False if there was nothing
-        to do."""
+        """Admit what fits, run one step over the tiles of the active
+        requests (the oldest first with up to a quarter of step_rays, then
+        shortest remaining work first, up to step_rays rays in all), retire
+        finished requests. Returns False if there was nothing to do."""
         self._admit()
         if not self.active:
             return False
@@ -315,8 +315,15 @@ class Server:
         budget = self.step_rays
         plan = []
         # shortest remaining work first: small requests finish in the step
-        # they join, large ones take what is left of the ray budget
-        for h in sorted(self.active, key=self._remaining_rays):
+        # they join, large ones take what is left of the ray budget; the
+        # oldest request always gets a share, so a stream of small requests
+        # cannot starve a large one
+        order = sorted(self.active, key=self._remaining_rays)
+        oldest = min(self.active, key=lambda h: h.arrival)
+        order.remove(oldest)
+        order.insert(0, oldest)
+        for h in order:
+            cap = self.step_rays // 4 if h is oldest and len(order) > 1 else budget
             req = h.request
             P = req.pixels()
             if h.phase < 0:
@@ -333,7 +340,8 @@ class Server:
             h.jid = n_jobs
             self._job_struct(h, self.jobs_tab[n_jobs])
             n_jobs += 1
-            while h.next_px < P and n_tiles < self.max_tiles and budget > 0:
+            took = 0
+            while h.next_px < P and n_tiles < self.max_tiles and budget > 0 and took < cap:
                 cnt = min(per_tile, P - h.next_px)
                 t = self.tiles_tab[n_tiles]
                 t.kind, t.job, t.first, t.count = kind, h.jid, h.next_px, cnt
@@ -341,6 +349,7 @@ class Server:
                 h.next_px += cnt
                 rays = cnt * rays_per_unit
                 h.rays += rays
+                took += rays
                 budget -= rays
                 self.rays_total += rays
                 self.rays_by_kind[kind] += rays
