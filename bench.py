@@ -62,12 +62,14 @@ def measured_peaks():
 # (dram__bytes_read.sum + dram__bytes_write.sum) scaled per ray; keyed by
 # the hash of the sources it was measured on, the hierarchy's builder
 # included (null once they change).
-# Captured on the 10-camera case (6.4M rays; the ~90 MB scene read is ~5% of
+# Captured on the 10-camera case (6.4M rays; the ~90 MB scene read is ~3% of
 # it, so the per-ray figure slightly overstates a 64M-ray launch).
 TRAFFIC = {
-    # the four round launches of one forward (6.4M-ray capture): read 428.9 + 919.9 + 358.2 + 87.1 MB,
-    # written 756.3 + 561.3 + 125.0 + 11.7 MB
-    "k_trace_round<16,10,*>": {"bytes_per_ray": (1794.1e6 + 1454.3e6) / 6.4e6, "src_hash": "99bbb098cc97"},
+    # the four round launches of one forward (6.4M-ray capture): read 426.7 + 919.6 + 358.8 + 87.4 MB,
+    # written 756.2 + 560.0 + 124.4 + 11.8 MB
+    "k_trace_round<16,10,*>": {"bytes_per_ray": (1792.5e6 + 1452.4e6) / 6.4e6, "src_hash": "6a245dfa735e"},
+    # the listed backward (same capture): read 1949.7 MB, written 187.0 MB
+    "k_trace_backward<16,10>": {"bytes_per_ray": (1949.7e6 + 187.0e6) / 6.4e6, "src_hash": "412251f765ad"},
 }
 
 
