@@ -9,8 +9,14 @@ A step is the training-style pass over that batch: rebuild the scene's LBVH
 from the surfel values (K1-K5), trace all rays forward (Eq. 8) and run the
 backward pass for a random N(0,1) upstream gradient. `value` is rays traced
 forward and backward per second (Mrays/s), inputs resident on the device.
-The Monte Carlo rendering-equation configuration (1M surfels, 640k points x
-64 samples = 41M secondary rays) is timed in the same run under "mc".
+The same run measures every configuration against the roofline (`configs`:
+the tiny cloud, the camera step, the Monte Carlo rendering equation with
+1M surfels and 640k points x 64 samples = 41M secondary rays, its
+gradient, relighting, and the served mix), with the FP32 peak measured by
+the library's FMA probe and the FP64 oracle timed beside each on bounded
+samples; the serving leg measures saturated throughput, then p50/p99 at a
+Poisson rate of 0.7x saturation (10 s warm-up, 60 s window) with a sweep,
+batched and one request at a time.
 
 `--impl reference` times the FP64 CPU oracle (there is no reference implementation to run)
 on bounded samples of the same workload, on the host cores.

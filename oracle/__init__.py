@@ -105,6 +105,10 @@ def _load():
     lib.oracle_shade_bounds.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P, P, P, P, P, C.c_int64,
                                         P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P,
                                         P, P, C.c_int32, P, P, P, C.c_int]
+    lib.oracle_relight_bounds.restype = C.c_int
+    lib.oracle_relight_bounds.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P, P, P, P, P, C.c_int64,
+                                          P, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P, P, C.c_int32,
+                                          P, P, P, C.c_int]
     lib.oracle_trace_grad.restype = C.c_int
     lib.oracle_trace_grad.argtypes = [P, P, P, P, P, C.c_int64, C.c_int32, P, P, C.c_int64,
                                       P, P, P, P, P, P, P, P, P, C.c_int]
@@ -466,4 +470,26 @@ def rasterize(scene, cam: Camera, params: Params = Params(), margins: Margins | 
                               int(n_threads))
     if rc != 0:
         raise ValueError("oracle_rasterize rejected its arguments")
+    return out
+
+
+def relight_bounds(scene, x, nrm, albedo, rough, wo, env, n_samples: int, seed: int, params: Params,
+                   margins: Margins = Margins(), max_alts: int = 256, n_threads: int = 0, point_ids=None):
+    """Admissible range of each point's relighting estimate
+    (oracle_relight_bounds in irgs_oracle.c). Returns lo [P,3], hi [P,3] and
+    unresolved [P]."""
+    lib = _load()
+    (means, quats, scales, opacity, feats), x, nrm, albedo, rough, wo, env = _shade_inputs(
+        scene, x, nrm, albedo, rough, wo, env)
+    Pn, n, F = x.shape[0], means.shape[0], feats.shape[1]
+    out = {"lo": np.zeros((Pn, 3)), "hi": np.zeros((Pn, 3)), "unresolved": np.zeros(Pn, np.int32)}
+    p, m = params.c(), margins.c()
+    pid = None if point_ids is None else np.ascontiguousarray(point_ids, np.int64).reshape(Pn)
+    rc = lib.oracle_relight_bounds(_ptr(means), _ptr(quats), _ptr(scales), _ptr(opacity), _ptr(feats), n, F,
+                                   _ptr(x), _ptr(nrm), _ptr(albedo), _ptr(rough), _ptr(wo), Pn, _ptr(env),
+                                   env.shape[0], env.shape[1], int(n_samples), C.c_uint64(seed & (2**64 - 1)),
+                                   _ptr(pid), C.byref(p), C.byref(m), int(max_alts), _ptr(out["lo"]),
+                                   _ptr(out["hi"]), _ptr(out["unresolved"]), int(n_threads))
+    if rc != 0:
+        raise ValueError("oracle_relight_bounds rejected its arguments")
     return out

@@ -1581,6 +1581,48 @@ int oracle_env_samples(const float* env, int32_t H, int32_t W, int64_t P, int32_
  * channels (params feat_offset, feat_count = 7) are [a (3), r, n (3)].
  * Outputs rgb [P,3]; vis [P] and ind [P,3] are means over all samples;
  * flags [P] ORs the traced rays' ambiguity flags. */
+/* One relighting sample w (density pdf) whose trace gave the blended
+ * material channels C[7] = [albedo (3), roughness, normal (3)] sums and the
+ * transmittance V: the indirect light of the traced surface, Lind, and the
+ * sample's term of the estimate, term = (a/pi + f_s) (V E + Lind) (n.w) / pdf
+ * (0 below the horizon). */
+static void relight_sample_term(const relight_maps* maps, const float* env, int32_t H, int32_t W,
+                                const double w[3], double pdf, const double C[7], double V, const double nn[3],
+                                const double wo[3], double no, const double a[3], double r, double term[3],
+                                double Lind[3])
+{
+    double O = 1.0 - V;
+    for (int k = 0; k < 3; ++k) { Lind[k] = 0.0; term[k] = 0.0; }
+    if (O > 0.0) {
+        double Ar[3] = {C[0] / O, C[1] / O, C[2] / O}, Rr = C[3] / O;
+        double Nr[3] = {C[4], C[5], C[6]}, v[3] = {-w[0], -w[1], -w[2]};
+        double len = sqrt(dot3(Nr, Nr));
+        if (len > 1e-12) {
+            for (int k = 0; k < 3; ++k) Nr[k] /= len;
+        } else {
+            for (int k = 0; k < 3; ++k) Nr[k] = v[k];
+        }
+        if (dot3(Nr, v) < 0.0) for (int k = 0; k < 3; ++k) Nr[k] = -Nr[k];
+        double mu = dot3(Nr, v);
+        if (mu > 1.0) mu = 1.0;
+        double refl[3], irr[3], pref[3], LA, LB;
+        for (int k = 0; k < 3; ++k) refl[k] = 2.0 * mu * Nr[k] - v[k];
+        map_lookup(maps->irr, RL_IRR_H, RL_IRR_W, Nr, irr);
+        pref_lookup(maps, env, H, W, refl, Rr, pref);
+        lut_lookup(maps->lut, mu, Rr, &LA, &LB);
+        for (int k = 0; k < 3; ++k) Lind[k] = O * (Ar[k] * irr[k] + pref[k] * (0.04 * LA + LB));
+    }
+    double E[3];
+    oracle_env_lookup(env, H, W, w, E);
+    double ni = dot3(nn, w);
+    if (ni <= 0.0) return;
+    double h[3] = {w[0] + wo[0], w[1] + wo[1], w[2] + wo[2]};
+    normalize3(h);
+    spec_terms t = spec_eval(r, ni, no, dot3(nn, h), dot3(wo, h));
+    double fs = t.D * t.F * t.G1i * t.G1o / (4.0 * ni * no);
+    for (int k = 0; k < 3; ++k) term[k] = (a[k] / OR_PI + fs) * (V * E[k] + Lind[k]) * ni / pdf;
+}
+
 int oracle_relight(const float* means, const float* quats, const float* scales, const float* opacity,
                    const float* feats, int64_t n, int32_t F_total,
                    const float* x_in, const float* n_in, const float* albedo, const float* rough,
@@ -1635,37 +1677,13 @@ int oracle_relight(const float* means, const float* quats, const float* scales, 
                     double C[7], D, Tfin;
                     int64_t nc = composite(hits, nh, feats, F_total, P, C, &D, &Tfin, Tl);
                     if (M) fl |= resolve_flags(hits, nh, nc, nears, nnr, P, M, Tl, Tfin);
-                    double V = Tfin, O = 1.0 - Tfin, Lind[3] = {0, 0, 0};
-                    if (O > 0.0) {
-                        double Ar[3] = {C[0] / O, C[1] / O, C[2] / O}, Rr = C[3] / O;
-                        double Nr[3] = {C[4], C[5], C[6]}, v[3] = {-w[0], -w[1], -w[2]};
-                        double len = sqrt(dot3(Nr, Nr));
-                        if (len > 1e-12) {
-                            for (int k = 0; k < 3; ++k) Nr[k] /= len;
-                        } else {
-                            for (int k = 0; k < 3; ++k) Nr[k] = v[k];
-                        }
-                        if (dot3(Nr, v) < 0.0) for (int k = 0; k < 3; ++k) Nr[k] = -Nr[k];
-                        double mu = dot3(Nr, v);
-                        if (mu > 1.0) mu = 1.0;
-                        double refl[3], irr[3], pref[3], LA, LB;
-                        for (int k = 0; k < 3; ++k) refl[k] = 2.0 * mu * Nr[k] - v[k];
-                        map_lookup(maps->irr, RL_IRR_H, RL_IRR_W, Nr, irr);
-                        pref_lookup(maps, env, H, W, refl, Rr, pref);
-                        lut_lookup(maps->lut, mu, Rr, &LA, &LB);
-                        for (int k = 0; k < 3; ++k) Lind[k] = O * (Ar[k] * irr[k] + pref[k] * (0.04 * LA + LB));
+                    double term[3], Lind[3];
+                    relight_sample_term(maps, env, H, W, w, pdf, C, Tfin, nn, wo, no, a, r, term, Lind);
+                    sv += Tfin;
+                    for (int k = 0; k < 3; ++k) {
+                        si[k] += Lind[k];
+                        acc[k] += term[k];
                     }
-                    double E[3];
-                    oracle_env_lookup(env, H, W, w, E);
-                    sv += V;
-                    for (int k = 0; k < 3; ++k) si[k] += Lind[k];
-                    double ni = dot3(nn, w);
-                    if (ni <= 0.0) continue;
-                    double h[3] = {w[0] + wo[0], w[1] + wo[1], w[2] + wo[2]};
-                    normalize3(h);
-                    spec_terms t = spec_eval(r, ni, no, dot3(nn, h), dot3(wo, h));
-                    double fs = t.D * t.F * t.G1i * t.G1o / (4.0 * ni * no);
-                    for (int k = 0; k < 3; ++k) acc[k] += (a[k] / OR_PI + fs) * (V * E[k] + Lind[k]) * ni / pdf;
                 }
                 for (int k = 0; k < 3; ++k) {
                     out_rgb[3 * p + k] = acc[k] / (double)S;
@@ -1676,6 +1694,98 @@ int oracle_relight(const float* means, const float* quats, const float* scales, 
             }
         }
         free(hits); free(nears); free(Tl);
+    }
+    free(maps); free(row_cdf); free(col_cdf); free(s);
+    return err ? -1 : 0;
+}
+
+/* Admissible range of each point's relighting estimate (as
+ * oracle_shade_bounds for oracle_shade): every traced sample is one of its
+ * ray's admissible outcomes of the 7 material channels and the opacity, and
+ * the estimate is (1/S) times the sum of the samples' terms, so each channel
+ * lies between the sums of the per-sample minima and maxima. Outputs
+ * rgb_lo, rgb_hi [P, 3] and unresolved [P] (samples whose outcomes could not
+ * all be listed; only the definition's term enters for them). */
+int oracle_relight_bounds(const float* means, const float* quats, const float* scales, const float* opacity,
+                          const float* feats, int64_t n, int32_t F_total,
+                          const float* x_in, const float* n_in, const float* albedo, const float* rough,
+                          const float* wo_in, int64_t Pn, const float* env, int32_t H, int32_t W, int32_t S,
+                          uint64_t seed, const int64_t* point_ids, const oracle_params* P, const oracle_margins* M,
+                          int32_t max_alts, double* rgb_lo, double* rgb_hi, int32_t* unresolved, int n_threads)
+{
+    if (n < 0 || Pn < 0 || !P || !M || P->feat_count != 7 || S <= 0 || H <= 0 || W <= 0 || max_alts < 1) return -1;
+    if (P->feat_offset < 0 || P->feat_offset + 7 > F_total) return -1;
+    relight_maps* maps = (relight_maps*)malloc(sizeof(relight_maps));
+    double* row_cdf = (double*)malloc(sizeof(double) * (size_t)(H + 1));
+    double* col_cdf = (double*)malloc(sizeof(double) * (size_t)H * (size_t)(W + 1));
+    surfel64* s = (surfel64*)malloc(sizeof(surfel64) * (size_t)(n > 0 ? n : 1));
+    if (!maps || !row_cdf || !col_cdf || !s) {
+        free(maps); free(row_cdf); free(col_cdf); free(s);
+        return -1;
+    }
+    oracle_relight_maps(env, H, W, n_threads, maps->irr, maps->pref, maps->lut, row_cdf, col_cdf);
+    load_surfels(means, quats, scales, opacity, n, P->alpha_min, s);
+    nthreads_set(n_threads);
+    int err = 0;
+#pragma omp parallel
+    {
+        alt_work wk;
+        double* of = (double*)malloc(sizeof(double) * 7 * (size_t)max_alts);
+        double* od = (double*)malloc(sizeof(double) * (size_t)max_alts);
+        double* oo = (double*)malloc(sizeof(double) * (size_t)max_alts);
+        int32_t* on = (int32_t*)malloc(sizeof(int32_t) * (size_t)max_alts);
+        if (!alt_work_init(&wk, n, 7) || !of || !od || !oo || !on) {
+#pragma omp atomic write
+            err = 1;
+        } else {
+#pragma omp for schedule(dynamic, 1)
+            for (int64_t p = 0; p < Pn; ++p) {
+                double x[3] = {x_in[3 * p], x_in[3 * p + 1], x_in[3 * p + 2]};
+                double nn[3] = {n_in[3 * p], n_in[3 * p + 1], n_in[3 * p + 2]};
+                double wo[3] = {wo_in[3 * p], wo_in[3 * p + 1], wo_in[3 * p + 2]};
+                double a[3] = {albedo[3 * p], albedo[3 * p + 1], albedo[3 * p + 2]};
+                double r = rough[p];
+                int64_t key = point_ids ? point_ids[p] : p;
+                normalize3(nn);
+                normalize3(wo);
+                if (dot3(nn, wo) <= 0.0) { nn[0] = -nn[0]; nn[1] = -nn[1]; nn[2] = -nn[2]; }
+                double no = dot3(nn, wo);
+                double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+                int32_t unres = 0;
+                for (int64_t sI = 0; sI < S; ++sI) {
+                    double w[3], pdf;
+                    if (!env_sample(row_cdf, col_cdf, H, W, uniform01(seed, key, sI, S, 0),
+                                    uniform01(seed, key, sI, S, 1), w, &pdf))
+                        continue;
+                    int32_t cnt = ray_alternatives(s, n, feats, F_total, x, w, P, M, max_alts, &wk, of, od, oo, on);
+                    if (cnt < 0) {
+                        unres++;
+                        cnt = 1;
+                    }
+                    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+                    for (int32_t j = 0; j < cnt; ++j) {
+                        double term[3], Lind[3];
+                        relight_sample_term(maps, env, H, W, w, pdf, of + 7 * (size_t)j, 1.0 - oo[j], nn, wo, no, a,
+                                            r, term, Lind);
+                        for (int k = 0; k < 3; ++k) {
+                            mn[k] = term[k] < mn[k] ? term[k] : mn[k];
+                            mx[k] = term[k] > mx[k] ? term[k] : mx[k];
+                        }
+                    }
+                    for (int k = 0; k < 3; ++k) {
+                        lo[k] += mn[k];
+                        hi[k] += mx[k];
+                    }
+                }
+                for (int k = 0; k < 3; ++k) {
+                    rgb_lo[3 * p + k] = lo[k] / (double)S;
+                    rgb_hi[3 * p + k] = hi[k] / (double)S;
+                }
+                if (unresolved) unresolved[p] = unres;
+            }
+        }
+        alt_work_free(&wk);
+        free(of); free(od); free(oo); free(on);
     }
     free(maps); free(row_cdf); free(col_cdf); free(s);
     return err ? -1 : 0;

@@ -41,7 +41,10 @@ def test_maps_match_oracle(h, w):
     E.close()
 
 
-def check(out, ref, frac=0.99):
+def check(out, ref, frac=0.99, bounds=None):
+    """Unflagged points at the shading bars; flagged points (if `bounds`, the
+    oracle's relight_bounds of the flagged points) inside their admissible
+    range within 1e-4 max(1, |ref|)."""
     g = out["rgb"].cpu().numpy().astype(np.float64)
     err = np.abs(g - ref["rgb"]).max(1) / np.maximum(1.0, np.abs(ref["rgb"]).max(1))
     ok = ref["flags"] == 0
@@ -49,6 +52,12 @@ def check(out, ref, frac=0.99):
           "max_err_unflagged": float(err[ok].max()) if ok.any() else None, "within": float((err <= 1e-4).mean())}
     assert (err <= 1e-4).mean() >= frac, st
     assert np.all(err[ok] <= 2e-3), st
+    if bounds is not None:
+        fl = np.nonzero(~ok)[0]
+        tol = 1e-4 * np.maximum(1.0, np.abs(ref["rgb"][fl]).max(1))[:, None]
+        inside = (g[fl] >= bounds["lo"] - tol) & (g[fl] <= bounds["hi"] + tol)
+        st["flagged"] = int(fl.size)
+        assert np.all(inside), ("flagged points outside their admissible range", fl[~inside.all(1)], st)
     v = out["vis"].cpu().numpy()
     assert np.all(np.abs(v - ref["vis"])[ok] <= 1e-4), st
     ind = out["ind"].cpu().numpy()
@@ -68,7 +77,10 @@ def test_relight_matches_oracle_object_scene(k, S, flags):
     torch.cuda.synchronize()
     assert S_.status() == 0
     ref = oracle.relight(sc, x, n, a, r, wo, env, S, 77, opar(p))
-    print(check(out, ref))
+    fl = np.nonzero(ref["flags"] != 0)[0]
+    b = (oracle.relight_bounds(sc, x[fl], n[fl], a[fl], r[fl], wo[fl], env, S, 77, opar(p), point_ids=fl)
+         if fl.size else None)
+    print(check(out, ref, bounds=b))
 
 
 def test_relight_furnace_and_visibility_in_an_empty_scene():

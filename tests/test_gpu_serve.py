@@ -241,3 +241,25 @@ def test_served_mix_matches_the_oracle(scenes, env):
         tol = 1e-4 * np.maximum(1.0, np.abs(sref["rgb"][fl]).max(1))[:, None]
         assert np.all((rgb[fl] >= b["lo"] - tol) & (rgb[fl] <= b["hi"] + tol)), (rgb[fl], b)
     srv.close()
+
+
+def test_oldest_request_is_not_starved(scenes):
+    """A large request keeps a share of every step while more small work
+    arrives each step than the step budget holds (shortest remaining work
+    first alone would give the large request nothing): it finishes within a
+    bounded number of steps."""
+    srv = serve.Server(scenes, max_tiles=1024, step_rays=1 << 16, tile_px=1024)
+    big = srv.submit(serve.RenderRequest(0, (3.0, 0.5, 2.0), 512, 512))      # 262,144 rays: 4 steps' budget
+    small = []
+    for i in range(40):
+        for _ in range(5):                                                   # 5 x 16,384 rays per step
+            small.append(srv.submit(serve.RenderRequest(1, (0.5, -3.5, 1.5), 128, 128)))
+        srv.step()
+        if big.done > 0:
+            break
+    # a quarter of each step's budget goes to the oldest request: 16 steps at most
+    assert big.done > 0 and srv.steps <= 16, srv.steps
+    srv.run_until_idle()
+    assert all(h.done > 0 for h in small)
+    assert all(S.status() == 0 for S in scenes)
+    srv.close()

@@ -178,3 +178,37 @@ def test_shade_bounds_span_both_orders_of_a_near_tie():
     np.testing.assert_allclose(b["lo"][0], np.minimum(t_def, t_swp).sum(0), rtol=1e-7)
     np.testing.assert_allclose(b["hi"][0], np.maximum(t_def, t_swp).sum(0), rtol=1e-7)
     assert b["hi"][0, 1] - b["lo"][0, 1] > 1e-3
+
+
+def test_relight_bounds_equal_the_estimate_where_nothing_is_ambiguous():
+    sc = synth.object_scene(n=3000, seed=36)
+    x, n, a, r, wo = synth.gbuffer_points(16, seed=37)
+    env = synth.env_map(seed=38, height=16, width=32)
+    p = Params(feat_offset=3, feat_count=7, t_min=1e-3)
+    ref = oracle.relight(sc, x, n, a, r, wo, env, 16, 5, p)
+    b = oracle.relight_bounds(sc, x, n, a, r, wo, env, 16, 5, p)
+    assert np.all(b["lo"] <= ref["rgb"] + 1e-12) and np.all(ref["rgb"] <= b["hi"] + 1e-12)
+    clean = ref["flags"] == 0
+    assert clean.any()
+    np.testing.assert_allclose(b["lo"][clean], ref["rgb"][clean], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(b["hi"][clean], ref["rgb"][clean], rtol=0, atol=1e-12)
+
+
+def test_relight_bounds_widen_under_a_near_tie():
+    # two large canopy disks 1e-9 apart with different albedo and roughness
+    # channels: the two blend orders give different traced materials, so the
+    # range has width, and the definition's estimate lies inside it
+    f1 = [0, 0, 0, 0.9, 0.1, 0.1, 0.2, 0, 0, 1]
+    f2 = [0, 0, 0, 0.1, 0.8, 0.3, 0.9, 0, 0, 1]
+    sc = scene([[0, 0, 1.0], [0, 0, 1.0 + 1e-9]], [Q, Q], [[10.0, 10.0]] * 2, [0.5, 0.7], [f1, f2])
+    x = np.zeros((1, 3), np.float32)
+    n = np.array([[0, 0, 1.0]], np.float32)
+    alb = np.array([[0.5, 0.6, 0.7]], np.float32)
+    rough = np.array([0.5], np.float32)
+    env = synth.env_map(seed=39, height=16, width=32)
+    p = Params(feat_offset=3, feat_count=7, t_min=1e-3)
+    ref = oracle.relight(sc, x, n, alb, rough, n, env, 32, 3, p)
+    b = oracle.relight_bounds(sc, x, n, alb, rough, n, env, 32, 3, p)
+    assert ref["flags"][0] & oracle.F_TIE
+    assert np.all(b["lo"][0] <= ref["rgb"][0] + 1e-12) and np.all(ref["rgb"][0] <= b["hi"][0] + 1e-12)
+    assert (b["hi"][0] - b["lo"][0]).max() > 1e-4
