@@ -512,7 +512,8 @@ typedef struct irgs_server_s* irgs_server;
  * feat_count <= 10); G-buffer tiles trace the 7 material channels starting
  * at `material_offset` (albedo 3, roughness 1, normal 3) with the render
  * parameters otherwise; `shade` traces the secondary rays (k = 16,
- * feat_count = 3 radiance channels, t_min > 0). Allocates pinned staging
+ * feat_count = 3 radiance channels, t_min > 0, flags 0: served shading is
+ * the split-lobe estimator through the wavefront path). Allocates pinned staging
  * for max_jobs jobs and max_tiles tiles and its device copy.
  */
 irgs_status irgs_server_create(const irgs_scene* scenes, int32_t n_scenes, int32_t max_jobs, int32_t max_tiles,

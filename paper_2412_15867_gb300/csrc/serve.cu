@@ -40,8 +40,8 @@ struct irgs_server_s {
     irgs::SceneView* dev_scenes = nullptr;
     int* dev_next = nullptr;
     int grid = 0;
-    irgs::TraceParams render{}, gbuf{}, shade{};
-    irgs_trace_params shade_params{};
+    irgs::TraceParams render{}, gbuf{};
+    irgs_trace_params shade_params{};          // the shading calls' trace parameters
     irgs::SceneView* host_views = nullptr;     // [n_scenes] the scenes' views and bounds, for the shading calls
     const uint32_t** host_bounds = nullptr;
     cudaStream_t stream = nullptr;
@@ -62,7 +62,7 @@ struct ServeArgs {
     const irgs_job* jobs;
     const irgs_tile* tiles;
     int* next_tile;
-    TraceParams render, gbuf, shade;
+    TraceParams render, gbuf;
 };
 
 // Pixel p of a camera (tile by tile when tile_w x tile_h > 1) -> ray.
@@ -180,7 +180,6 @@ ServeArgs args_of(irgs_server s) {
     A.next_tile = s->dev_next;
     A.render = s->render;
     A.gbuf = s->gbuf;
-    A.shade = s->shade;
     return A;
 }
 
@@ -208,7 +207,8 @@ irgs_status irgs_server_create(const irgs_scene* scenes, int32_t n_scenes, int32
     if (!scenes || n_scenes <= 0 || max_jobs <= 0 || max_tiles <= 0 || !render || !shade || !out)
         return IRGS_ERR_INVALID_ARG;
     if (render->k != kServeK || shade->k != kServeK) return IRGS_ERR_UNSUPPORTED;
-    if (render->feat_count < 0 || render->feat_count > 10 || shade->feat_count != 3 || !(shade->t_min > 0.f))
+    if (render->feat_count < 0 || render->feat_count > 10 || shade->feat_count != 3 || !(shade->t_min > 0.f) ||
+        shade->flags != 0u)
         return IRGS_ERR_INVALID_ARG;
     for (int i = 0; i < n_scenes; ++i) {
         if (!scenes[i]) return IRGS_ERR_INVALID_ARG;
@@ -231,7 +231,6 @@ irgs_status irgs_server_create(const irgs_scene* scenes, int32_t n_scenes, int32
     s->max_tiles = max_tiles;
     s->stage_bytes = kHeaderBytes + sizeof(irgs_job) * (size_t)max_jobs + sizeof(irgs_tile) * (size_t)max_tiles;
     s->render = to_params(*render);
-    s->shade = to_params(*shade);
     s->shade_params = *shade;
     s->host_views = new (std::nothrow) SceneView[n_scenes];
     s->host_bounds = new (std::nothrow) const uint32_t*[n_scenes];
