@@ -220,3 +220,4 @@ def test_autograd_with_saved_hits_equals_replay():
         ((feat * gf).sum() + (depth * gd).sum() + (opac * go).sum()).backward()
         grads.append({k: l.grad for k, l in zip(NAMES, leaves)})
     _grads_close(grads[1], grads[0])
+
