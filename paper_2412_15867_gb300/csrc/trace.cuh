@@ -510,6 +510,25 @@ struct MarchState {
     int nh;
 };
 
+// The traced channels f[0..fc) of one surfel, zero beyond fc; as 8-byte
+// pairs when f is 8-byte aligned for every surfel (even row length and
+// offset).
+template <int FB>
+__device__ __forceinline__ void load_channels(const float* __restrict__ f, int fc, bool pairs, float (&fv)[FB]) {
+    if (pairs) {
+#pragma unroll
+        for (int c = 0; c < FB; c += 2) {
+            const float2 t = c + 1 < fc ? __ldg(reinterpret_cast<const float2*>(f + c))
+                                        : make_float2(c < fc ? __ldg(f + c) : 0.f, 0.f);
+            fv[c] = t.x;
+            if (c + 1 < FB) fv[c + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < FB; ++c) fv[c] = c < fc ? __ldg(f + c) : 0.f;
+    }
+}
+
 // Blend the round's buffered hits in order (Eq. 2, Eq. 8) until the
 // transmittance drops below T_min (the crossing hit included). Returns true
 // when the ray is done: terminated, or fewer than K hits were left; else
@@ -524,10 +543,11 @@ __device__ __forceinline__ bool blend_round(const SceneView& S, const TraceParam
         const float a = kb.a_at(j);
         const int32_t m = kb.m_at(j);
         const float w = __fmul_rn(st.T, a);
-        const float* f = S.feat + (int64_t)m * S.F + P.off;
+        float fv[FB];
+        load_channels<FB>(S.feat + (int64_t)m * S.F + P.off, P.fc, ((S.F | P.off) & 1) == 0, fv);
 #pragma unroll
         for (int c = 0; c < FB; ++c)
-            if (c < P.fc) st.C[c] = __fmaf_rn(w, __ldg(f + c), st.C[c]);
+            if (c < P.fc) st.C[c] = __fmaf_rn(w, fv[c], st.C[c]);
         st.D = __fmaf_rn(w, key_depth(kb.key_at(j)), st.D);
         st.T = __fmul_rn(st.T, __fsub_rn(1.0f, a));
         if (ids != nullptr && st.nh < max_ids) ids[st.nh] = __float_as_int(__ldg(&S.rec[(int64_t)m * kRecF4 + 2].w));

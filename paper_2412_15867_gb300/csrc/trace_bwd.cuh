@@ -25,13 +25,13 @@
 namespace irgs {
 
 // Per-surfel gradient row in the Morton-ordered scratch accumulator (16-byte
-// aligned, added with vector atomics):
-//   [g_mu.x g_mu.y g_mu.z g_o] [g_q.w g_q.x g_q.y g_q.z] [g_su g_sv 0 0]
-//   [g_f 0..3] [g_f 4..7] ...   (the traced channels, padded to 4)
+// aligned, added with vector atomics), packed without gaps:
+//   g_mu.x g_mu.y g_mu.z g_o | g_q.w g_q.x g_q.y g_q.z | g_su g_sv g_f0 g_f1 | g_f2 ...
+// (the traced channels follow the scales; the row is padded to a multiple of
+// 4 floats: 20 floats = 5 vector atomics at 10 channels)
 template <int FB>
 struct GradRow {
-    static constexpr int FB4 = (FB + 3) / 4 * 4;
-    static constexpr int N = 12 + FB4;   // floats per row
+    static constexpr int N = (10 + FB + 3) / 4 * 4;   // floats per row
     float v[N];
 };
 
@@ -84,7 +84,8 @@ __global__ void k_grad_scatter(const int32_t* __restrict__ perm, int64_t n, cons
     if (m >= n) return;
     const int64_t u = perm[m];
     const float4* r = reinterpret_cast<const float4*>(acc_rows + m * N);
-    const float4 a = r[0], q = r[1], sc = r[2];
+    const float4 a = r[0], q = r[1];
+    const float2 sc = *reinterpret_cast<const float2*>(r + 2);
     g_means[3 * u] += a.x;
     g_means[3 * u + 1] += a.y;
     g_means[3 * u + 2] += a.z;
@@ -95,7 +96,7 @@ __global__ void k_grad_scatter(const int32_t* __restrict__ perm, int64_t n, cons
     g_quats[4 * u + 3] += q.w;
     g_scales[2 * u] += sc.x;
     g_scales[2 * u + 1] += sc.y;
-    const float* f = acc_rows + m * N + 12;
+    const float* f = acc_rows + m * N + 10;
     for (int c = 0; c < fc; ++c) g_feat[u * F + off + c] += f[c];
 }
 
@@ -129,13 +130,13 @@ __device__ __forceinline__ void backward_hit(const SceneView& S, const Ray& ray,
     surfel_hit<true>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a, &hg);
     const float tau = kh + 0.0f;
     const float w = __fmul_rn(st.T, a);
-    const float* f = S.feat + (int64_t)m * S.F + P.off;
+    float fv[FB];
+    load_channels<FB>(S.feat + (int64_t)m * S.F + P.off, P.fc, ((S.F | P.off) & 1) == 0, fv);
     float v = __fmul_rn(gD, tau), Sj = 0.f;
 #pragma unroll
     for (int c = 0; c < FB; ++c) {
-        const float fv = c < P.fc ? __ldg(f + c) : 0.f;
-        st.C[c] = c < P.fc ? __fmaf_rn(w, fv, st.C[c]) : 0.f;
-        v = fmaf(gC[c], fv, v);
+        st.C[c] = c < P.fc ? __fmaf_rn(w, fv[c], st.C[c]) : 0.f;
+        v = fmaf(gC[c], fv[c], v);
         Sj = fmaf(gC[c], Cf[c] - st.C[c], Sj);
     }
     st.D = __fmaf_rn(w, tau, st.D);
@@ -179,10 +180,8 @@ __device__ __forceinline__ void backward_hit(const SceneView& S, const Ray& ray,
     gv.v[7] = (hz - qz * proj) * iqn;
     gv.v[8] = -gu * hg.u * isx;
     gv.v[9] = -gvv * hg.v * isy;
-    gv.v[10] = 0.f;
-    gv.v[11] = 0.f;
 #pragma unroll
-    for (int c = 0; c < GradRow<FB>::FB4; ++c) gv.v[12 + c] = c < FB ? w * gC[c] : 0.f;
+    for (int c = 0; c < GradRow<FB>::N - 10; ++c) gv.v[10 + c] = c < FB ? w * gC[c] : 0.f;
     accumulate_row<FB>(gv, m, acc_rows, rows);
     st.T = __fmul_rn(st.T, __fsub_rn(1.0f, a));
 }
