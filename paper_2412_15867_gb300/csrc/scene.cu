@@ -838,6 +838,13 @@ __global__ void k_wide_level(int level, const Node* __restrict__ nodes, const in
             ++m;
         }
         int32_t out[4] = {kNoChild, kNoChild, kNoChild, kNoChild};
+        // empty slots get an empty box (lo = +inf, hi = -inf): no ray's slab
+        // interval meets it, so the walks need no test of the child id
+        for (int k = m; k < 4; ++k)
+            for (int j = 0; j < 3; ++j) {
+                box[k][j] = INFINITY;
+                box[k][3 + j] = -INFINITY;
+            }
         for (int k = 0; k < m; ++k) {
             if (cid[k] < 0) {
                 out[k] = cid[k];
@@ -872,16 +879,16 @@ __global__ void k_wide_check(const uint32_t* __restrict__ counters, uint32_t* st
 // Wide root of a one-surfel (or empty) scene.
 __global__ void k_wide_tiny(int64_t n, const float* __restrict__ leaf_box, WideNode* wide) {
     WideNode o;
-    const float z = 0.f;
-    float b[6] = {z, z, z, z, z, z};
+    const float e = INFINITY;   // empty slots: lo = +inf, hi = -inf
+    float b[6] = {e, e, e, -e, -e, -e};
     if (n == 1)
         for (int k = 0; k < 6; ++k) b[k] = leaf_box[k];
-    o.lox = make_float4(b[0], z, z, z);
-    o.loy = make_float4(b[1], z, z, z);
-    o.loz = make_float4(b[2], z, z, z);
-    o.hix = make_float4(b[3], z, z, z);
-    o.hiy = make_float4(b[4], z, z, z);
-    o.hiz = make_float4(b[5], z, z, z);
+    o.lox = make_float4(b[0], e, e, e);
+    o.loy = make_float4(b[1], e, e, e);
+    o.loz = make_float4(b[2], e, e, e);
+    o.hix = make_float4(b[3], -e, -e, -e);
+    o.hiy = make_float4(b[4], -e, -e, -e);
+    o.hiz = make_float4(b[5], -e, -e, -e);
     o.child = make_int4(n == 1 ? ~0 : kNoChild, kNoChild, kNoChild, kNoChild);
     o.pad = make_int4(n == 1 ? 1 : 0, 0, 0, 0);
     wide[0] = o;

@@ -293,14 +293,16 @@ __device__ __forceinline__ void leaf_insert(const SceneView& S, const Ray& ray, 
     const float4 r0 = ldg4(R), r1 = ldg4(R + 1), r2 = ldg4(R + 2), r3 = ldg4(R + 3);
     float kh, kl, a;
     // a rounded depth below the last blended key's, or above the full
-    // buffer's last entry (or t_max), cannot pass the key tests below
-    const float lo = key_depth(last_key);
-    const float hi = kb.full() ? key_depth(kb.tail_key) : P.t_max;
-    if (!surfel_hit<false>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a, nullptr, lo, hi)) return;
+    // buffer's last entry (t_hi, else t_max), cannot pass the key tests
+    // below; kh >= key_depth(last_key) >= t_min >= 0 also makes the key
+    // order that of the depths, and the first round's last_key = (t_min, 0)
+    // with last_u = INT32_MAX admits exactly the depths beyond t_min
+    if (!surfel_hit<false>(r0, r1, r2, r3, ray, P.alpha_min, P.alpha_max, kh, kl, a, nullptr, key_depth(last_key),
+                           t_hi))
+        return;
     const uint64_t key = depth_key(kh, kl);
-    const bool past_min = kh > P.t_min || (kh == P.t_min && kl > 0.f);
     const int32_t u = __float_as_int(r2.w);
-    const bool after = past_min && (key > last_key || (key == last_key && u > last_u));
+    const bool after = key > last_key || (key == last_key && u > last_u);
     const bool before = kh < P.t_max || (kh == P.t_max && kl < 0.f);
     if (after && before && kb.fits(key, u, S.rec)) {
         if (STATS) ts->inserts++;
@@ -325,8 +327,8 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
     float t_hi = P.t_max;
     int ni = 0;
     // each wide node is fetched at most once per round in a valid tree
-    const int64_t max_visits = S.n + 64;
-    for (int64_t visits = 0;; ++visits) {
+    const int max_visits = S.n + 64 < (int64_t)INT32_MAX ? (int)(S.n + 64) : INT32_MAX;
+    for (int visits = 0;; ++visits) {
         if (visits > max_visits) {
             ok = false;
             break;
@@ -339,7 +341,7 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
         float hi_c = t_hi + tslack(t_hi);
         bool h[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) h[k] = c[k] != kNoChild && tn[k] <= tf[k] && tf[k] >= lo_c && tn[k] <= hi_c;
+        for (int k = 0; k < 4; ++k) h[k] = tn[k] <= tf[k] && tf[k] >= lo_c && tn[k] <= hi_c;   // empty slots: empty box
         {
             // lanes of a warp walk different nodes here: each tests its own
             // needed leaves in one loop, so lanes run their i-th leaf test
@@ -431,8 +433,8 @@ __device__ __forceinline__ bool collect_round_warp(const SceneView& S, const Ray
     int sp = 0;
     bool ok = true;
     int ni = 0;
-    const int64_t max_visits = S.n + 64;
-    for (int64_t visits = 0;; ++visits) {
+    const int max_visits = S.n + 64 < (int64_t)INT32_MAX ? (int)(S.n + 64) : INT32_MAX;
+    for (int visits = 0;; ++visits) {
         if (visits > max_visits) {
             ok = false;
             break;
@@ -446,22 +448,24 @@ __device__ __forceinline__ bool collect_round_warp(const SceneView& S, const Ray
         bool h[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            h[k] = active && c[k] != kNoChild && tn[k] <= tf[k] && tf[k] >= lo_c && tn[k] <= hi_c;
+            h[k] = active && tn[k] <= tf[k] && tf[k] >= lo_c && tn[k] <= hi_c;   // empty slots: empty box
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             if (h[k] && c[k] < 0) leaf_insert<KB, STATS>(S, ray, P, ~c[k], last_key, last_u, kb, t_hi, ts);
         hi_c = t_hi + tslack(t_hi);
         // internal children some lane still needs; order them by the entry
         // depth seen by the first lane that needs each
-        float t[4];
+        float t[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
         int nv = 0;
+        if (max(max(c[0], c[1]), max(c[2], c[3])) >= 0) {   // the node (same for the warp) has internal children
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const unsigned b = __ballot_sync(kFullWarp, h[k] && c[k] >= 0 && tn[k] <= hi_c);
-            const int src = b ? __ffs(b) - 1 : 0;
-            const float tk = __shfl_sync(kFullWarp, tn[k], src);
-            t[k] = b ? tk : INFINITY;
-            nv += b ? 1 : 0;
+            for (int k = 0; k < 4; ++k) {
+                const unsigned b = __ballot_sync(kFullWarp, h[k] && c[k] >= 0 && tn[k] <= hi_c);
+                const int src = b ? __ffs(b) - 1 : 0;
+                const float tk = __shfl_sync(kFullWarp, tn[k], src);
+                t[k] = b ? tk : INFINITY;
+                nv += b ? 1 : 0;
+            }
         }
         if (nv == 0) {
             if (sp == 0) break;
