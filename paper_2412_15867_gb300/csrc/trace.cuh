@@ -317,8 +317,7 @@ template <class KB, bool STATS = false>
 __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray, const TraceParams& P,
                                               uint64_t last_key, int32_t last_u, KB& kb,
                                               TraceStats* ts = nullptr) {
-    int stack_n[kStackSize];
-    float stack_t[kStackSize];
+    int2 stack[kStackSize];   // (node, entry depth bits): one 8-byte word per entry
     int sp = 0;
     bool ok = true;
     kb.clear();
@@ -370,8 +369,9 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
             bool found = false;
             while (sp > 0) {
                 --sp;
-                if (stack_t[sp] <= t_hi + tslack(t_hi)) {
-                    ni = stack_n[sp];
+                const int2 e = stack[sp];
+                if (__int_as_float(e.y) <= hi_c) {
+                    ni = e.x;
                     found = true;
                     break;
                 }
@@ -393,8 +393,7 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     if (k == far) {
-                        stack_n[sp] = c[k];
-                        stack_t[sp] = t[k];
+                        stack[sp] = make_int2(c[k], __float_as_int(t[k]));
                         t[k] = INFINITY;
                     }
                 ++sp;
