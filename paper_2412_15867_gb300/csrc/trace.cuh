@@ -319,6 +319,8 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
                                               TraceStats* ts = nullptr) {
     int2 stack[kStackSize];   // (node, entry depth bits): one 8-byte word per entry
     int sp = 0;
+    int2 top = make_int2(0, 0);
+    bool has_top = false;
     bool ok = true;
     kb.clear();
     const float t_lo = key_depth(last_key);
@@ -367,13 +369,19 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
         }
         if (nv == 0) {
             bool found = false;
-            while (sp > 0) {
+            if (has_top) {   // the most recent entry, kept in registers
+                has_top = false;
+                if (__int_as_float(top.y) <= hi_c) {
+                    ni = top.x;
+                    found = true;
+                }
+            }
+            while (!found && sp > 0) {
                 --sp;
                 const int2 e = stack[sp];
                 if (__int_as_float(e.y) <= hi_c) {
                     ni = e.x;
                     found = true;
-                    break;
                 }
             }
             if (!found) break;
@@ -389,20 +397,19 @@ __device__ __forceinline__ bool collect_round(const SceneView& S, const Ray& ray
                     tfar = t[k];
                     far = k;
                 }
-            if (sp < kStackSize) {
+            int2 ent = make_int2(0, 0);
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k == far) {
-                        stack[sp] = make_int2(c[k], __float_as_int(t[k]));
-                        t[k] = INFINITY;
-                    }
-                ++sp;
-            } else {
-                ok = false;
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k == far) t[k] = INFINITY;
+            for (int k = 0; k < 4; ++k)
+                if (k == far) {
+                    ent = make_int2(c[k], __float_as_int(t[k]));
+                    t[k] = INFINITY;
+                }
+            if (has_top) {
+                if (sp < kStackSize) stack[sp++] = top;
+                else ok = false;
             }
+            top = ent;
+            has_top = true;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k)
