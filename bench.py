@@ -71,11 +71,11 @@ def measured_peaks():
 # Captured on the 10-camera case (6.4M rays; the ~90 MB scene read is ~3% of
 # it, so the per-ray figure slightly overstates a 64M-ray launch).
 TRAFFIC = {
-    # the four round launches of one forward (6.4M-ray capture): read 426.7 + 919.6 + 358.8 + 87.4 MB,
-    # written 756.2 + 560.0 + 124.4 + 11.8 MB
-    "k_trace_round<16,10,*>": {"bytes_per_ray": (1792.5e6 + 1452.4e6) / 6.4e6, "src_hash": "6a245dfa735e"},
-    # the listed backward (same capture): read 1949.7 MB, written 187.0 MB
-    "k_trace_backward<16,10>": {"bytes_per_ray": (1949.7e6 + 187.0e6) / 6.4e6, "src_hash": "412251f765ad"},
+    # the four round launches of one forward (6.4M-ray capture): read 425.7 + 924.0 + 359.6 + 87.4 MB,
+    # written 755.7 + 564.5 + 127.5 + 12.6 MB
+    "k_trace_round<16,10,*>": {"bytes_per_ray": (1796.7e6 + 1460.3e6) / 6.4e6, "src_hash": "2760797ebf9e"},
+    # the listed backward and the replay of long lists (same case): read 1916.4 + 25.6 MB, written 156.8 MB
+    "k_trace_backward<16,10>": {"bytes_per_ray": (1942.0e6 + 156.8e6) / 6.4e6, "src_hash": "3f393a963d0b"},
 }
 
 

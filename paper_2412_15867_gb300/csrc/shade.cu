@@ -66,9 +66,8 @@ __global__ void __launch_bounds__(kShadeThreads) k_shade_backward(
     float* __restrict__ g_albedo, float* __restrict__ g_rough, float* __restrict__ g_env,
     float* __restrict__ acc_rows) {
     static_assert(kShadeThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
-    constexpr int N = GradRow<3>::N;
-    __shared__ float rows_all[kShadeThreads * (N + 1)];
-    float* rows = rows_all + (threadIdx.x & ~31) * (N + 1);
+    __shared__ float4 rows_all[kShadeThreads * GradRow<3>::kStride / 4];
+    float* rows = reinterpret_cast<float*>(rows_all) + (threadIdx.x & ~31) * GradRow<3>::kStride;
     const int lane = threadIdx.x & 31;
     const int64_t p = blockIdx.x * (int64_t)(kShadeThreads / 32) + (threadIdx.x >> 5);
     if (p >= Pn) return;

@@ -251,10 +251,9 @@ __global__ void __launch_bounds__(kWaveThreads) k_wave_backward(SceneView S, Tra
                                                                 const int32_t* __restrict__ ids, int max_ids,
                                                                 const float4* __restrict__ up,
                                                                 float* __restrict__ acc_rows) {
-    constexpr int N = GradRow<3>::N;
     static_assert(kWaveThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
-    __shared__ float rows_all[kWaveThreads * (N + 1)];
-    float* rows = rows_all + (threadIdx.x & ~31) * (N + 1);
+    __shared__ float4 rows_all[kWaveThreads * GradRow<3>::kStride / 4];
+    float* rows = reinterpret_cast<float*>(rows_all) + (threadIdx.x & ~31) * GradRow<3>::kStride;
     const int64_t j = blockIdx.x * (int64_t)kWaveThreads + threadIdx.x;
     const int64_t i = j < rays ? order[j] : 0;
     const float4 d4 = dir[i];

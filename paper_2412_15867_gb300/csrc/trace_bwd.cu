@@ -51,10 +51,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_trace_backward(
     const int32_t* __restrict__ out_nhits, const int32_t* __restrict__ hit_ids, int max_ids,
     const float* __restrict__ g_featv, const float* __restrict__ g_depthv, const float* __restrict__ g_opacv,
     float* __restrict__ acc_rows) {
-    constexpr int N = GradRow<FB>::N;
     static_assert(kBwdThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
-    __shared__ float rows_all[kBwdThreads * (N + 1)];
-    float* rows = rows_all + (threadIdx.x & ~31) * (N + 1);
+    __shared__ float4 rows_all[kBwdThreads * GradRow<FB>::kStride / 4];
+    float* rows = reinterpret_cast<float*>(rows_all) + (threadIdx.x & ~31) * GradRow<FB>::kStride;
     const int64_t r = blockIdx.x * (int64_t)kBwdThreads + threadIdx.x;
     if (S.n == 0) return;
     const int nh_total = r < R ? out_nhits[r] : 0;

@@ -32,6 +32,10 @@ namespace irgs {
 template <int FB>
 struct GradRow {
     static constexpr int N = (10 + FB + 3) / 4 * 4;   // floats per row
+    // row stride of the per-warp shared exchange: rows are written and read
+    // as float4; an odd number of float4 per row keeps the 8 lanes of each
+    // 128-bit shared-memory phase on distinct banks
+    static constexpr int kStride = (N / 4) % 2 ? N : N + 4;
     float v[N];
 };
 
@@ -40,8 +44,9 @@ struct GradRow {
 // first of them adds the row with N/4 float4 atomics.
 template <int FB>
 __device__ __forceinline__ void accumulate_row(const GradRow<FB>& g, int32_t m, float* __restrict__ acc_rows,
-                                               float* rows /* [32][N+1] this warp */) {
+                                               float* rows /* [32][kStride] this warp, 16-byte aligned */) {
     constexpr int N = GradRow<FB>::N;
+    constexpr int S = GradRow<FB>::kStride;
     const unsigned active = __activemask();
     const unsigned peers = __match_any_sync(active, m);
     const int lane = threadIdx.x & 31;
@@ -50,18 +55,24 @@ __device__ __forceinline__ void accumulate_row(const GradRow<FB>& g, int32_t m, 
 #pragma unroll
     for (int k = 0; k < N; ++k) acc[k] = g.v[k];
     if (peers != (1u << lane)) {
-        float* mine = rows + lane * (N + 1);
+        float4* mine = reinterpret_cast<float4*>(rows + lane * S);
 #pragma unroll
-        for (int k = 0; k < N; ++k) mine[k] = g.v[k];
+        for (int q = 0; q < N / 4; ++q) mine[q] = make_float4(g.v[4 * q], g.v[4 * q + 1], g.v[4 * q + 2], g.v[4 * q + 3]);
         __syncwarp(peers);
         if (lane == leader) {
             unsigned rest = peers & ~(1u << lane);
             while (rest) {
                 const int l = __ffs(rest) - 1;
                 rest &= rest - 1;
-                const float* other = rows + l * (N + 1);
+                const float4* other = reinterpret_cast<const float4*>(rows + l * S);
 #pragma unroll
-                for (int k = 0; k < N; ++k) acc[k] += other[k];
+                for (int q = 0; q < N / 4; ++q) {
+                    const float4 o = other[q];
+                    acc[4 * q] += o.x;
+                    acc[4 * q + 1] += o.y;
+                    acc[4 * q + 2] += o.z;
+                    acc[4 * q + 3] += o.w;
+                }
             }
         }
         __syncwarp(peers);
