@@ -40,8 +40,9 @@ struct GradRow {
 };
 
 // Add row g for Morton slot m: lanes of the warp holding the same slot are
-// summed first (match mask + per-lane rows in shared memory), then the
-// first of them adds the row with N/4 float4 atomics.
+// summed first (match mask + per-lane rows in shared memory; each lane of
+// the group sums a share of the row's float4 columns over the group and
+// adds them with one float4 atomic each); a lane alone adds its row directly.
 template <int FB>
 __device__ __forceinline__ void accumulate_row(const GradRow<FB>& g, int32_t m, float* __restrict__ acc_rows,
                                                float* rows /* [32][kStride] this warp, 16-byte aligned */) {
@@ -50,38 +51,36 @@ __device__ __forceinline__ void accumulate_row(const GradRow<FB>& g, int32_t m, 
     const unsigned active = __activemask();
     const unsigned peers = __match_any_sync(active, m);
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(peers) - 1;
-    float acc[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k) acc[k] = g.v[k];
-    if (peers != (1u << lane)) {
-        float4* mine = reinterpret_cast<float4*>(rows + lane * S);
-#pragma unroll
-        for (int q = 0; q < N / 4; ++q) mine[q] = make_float4(g.v[4 * q], g.v[4 * q + 1], g.v[4 * q + 2], g.v[4 * q + 3]);
-        __syncwarp(peers);
-        if (lane == leader) {
-            unsigned rest = peers & ~(1u << lane);
-            while (rest) {
-                const int l = __ffs(rest) - 1;
-                rest &= rest - 1;
-                const float4* other = reinterpret_cast<const float4*>(rows + l * S);
-#pragma unroll
-                for (int q = 0; q < N / 4; ++q) {
-                    const float4 o = other[q];
-                    acc[4 * q] += o.x;
-                    acc[4 * q + 1] += o.y;
-                    acc[4 * q + 2] += o.z;
-                    acc[4 * q + 3] += o.w;
-                }
-            }
-        }
-        __syncwarp(peers);
-    }
-    if (lane != leader) return;
     float4* dst = reinterpret_cast<float4*>(acc_rows + (int64_t)m * N);
+    if (peers == (1u << lane)) {
 #pragma unroll
-    for (int q = 0; q < N / 4; ++q)
-        atomicAdd(dst + q, make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]));
+        for (int q = 0; q < N / 4; ++q)
+            atomicAdd(dst + q, make_float4(g.v[4 * q], g.v[4 * q + 1], g.v[4 * q + 2], g.v[4 * q + 3]));
+        return;
+    }
+    float4* mine = reinterpret_cast<float4*>(rows + lane * S);
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) mine[q] = make_float4(g.v[4 * q], g.v[4 * q + 1], g.v[4 * q + 2], g.v[4 * q + 3]);
+    __syncwarp(peers);
+    // the peers split the row's float4 columns: the lane of rank r sums
+    // columns r, r + p, ... over the group and adds each with one atomic
+    const int p = __popc(peers);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    for (int q = rank; q < N / 4; q += p) {
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+        unsigned rest = peers;
+        while (rest) {
+            const int l = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const float4 o = reinterpret_cast<const float4*>(rows + l * S)[q];
+            sum.x += o.x;
+            sum.y += o.y;
+            sum.z += o.z;
+            sum.w += o.w;
+        }
+        atomicAdd(dst + q, sum);
+    }
+    __syncwarp(peers);
 }
 
 // Add the Morton-ordered rows into the caller's user-order gradients
