@@ -36,6 +36,7 @@ namespace {
 constexpr int kWaveThreads = 128;
 constexpr int64_t kWaveChunkRays = int64_t(1) << 24;
 constexpr int kWaveSavedHits = 64;   // 12% of secondary rays blend more than 32 hits, 0.02% more than 64
+constexpr int kWaveReplayBlocks = 1024;   // grid-stride blocks for the few rays whose hit list did not fit
 
 __device__ __forceinline__ f3 ld3w(const float* p, int64_t i) { return mk3(p[3 * i], p[3 * i + 1], p[3 * i + 2]); }
 
@@ -238,30 +239,16 @@ __global__ void __launch_bounds__(kWaveThreads) k_wave_grad_point(
     }
 }
 
-// Backward of the rays in regrouped order. LISTED: rays whose whole hit list
-// was saved (no traversal); otherwise the rays with longer lists replay the
-// march.
+// Backward of one ray in regrouped order (sorted position j): from its saved
+// hit list (LISTED) or by replaying its march.
 template <int K, bool LISTED>
-__global__ void __launch_bounds__(kWaveThreads) k_wave_backward(SceneView S, TraceParams P,
-                                                                const float* __restrict__ xg, int64_t p0, int St,
-                                                                const float4* __restrict__ dir,
-                                                                const int32_t* __restrict__ order, int64_t rays,
-                                                                const float4* __restrict__ res,
-                                                                const int32_t* __restrict__ nh,
-                                                                const int32_t* __restrict__ ids, int max_ids,
-                                                                const float4* __restrict__ up,
-                                                                float* __restrict__ acc_rows) {
-    static_assert(kWaveThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
-    __shared__ float4 rows_all[kWaveThreads * GradRow<3>::kStride / 4];
-    float* rows = reinterpret_cast<float*>(rows_all) + (threadIdx.x & ~31) * GradRow<3>::kStride;
-    const int64_t j = blockIdx.x * (int64_t)kWaveThreads + threadIdx.x;
-    const int64_t i = j < rays ? order[j] : 0;
+__device__ __forceinline__ void wave_backward_ray(const SceneView& S, const TraceParams& P,
+                                                  const float* __restrict__ xg, int64_t p0, int St,
+                                                  const float4* __restrict__ dir, int64_t i,
+                                                  const float4* __restrict__ res, int n_hits,
+                                                  const int32_t* __restrict__ ids, int max_ids, float4 u4,
+                                                  float* __restrict__ acc_rows, float* rows) {
     const float4 d4 = dir[i];
-    const float4 u4 = up[i];
-    const int n_hits = (j < rays && d4.w != 0.f) ? nh[i] : 0;
-    const bool has_grad = u4.x != 0.f || u4.y != 0.f || u4.z != 0.f || u4.w != 0.f;
-    const bool mine = n_hits > 0 && has_grad && (LISTED == (n_hits <= max_ids));
-    if (!mine) return;
     const int64_t p = p0 + i / St;
     const Ray ray = make_ray(ld3w(xg, p), mk3(d4.x, d4.y, d4.z));
     const float4 t = res[i];
@@ -274,6 +261,62 @@ __global__ void __launch_bounds__(kWaveThreads) k_wave_backward(SceneView S, Tra
         const bool ok = march_backward<K, 3, false>(S, ray, P, true, n_hits, Cf, 0.f, t.w, gC, 0.f, u4.w, acc_rows,
                                                     rows);
         if (!ok) atomicOr(S.status, kErrStackOverflow);
+    }
+}
+
+// Backward from the saved hit lists, one thread per sorted ray; rays whose
+// list did not fit (more than max_ids hits) are appended to replay_list for
+// k_wave_replay.
+template <int K>
+__global__ void __launch_bounds__(kWaveThreads) k_wave_backward(SceneView S, TraceParams P,
+                                                                const float* __restrict__ xg, int64_t p0, int St,
+                                                                const float4* __restrict__ dir,
+                                                                const int32_t* __restrict__ order, int64_t rays,
+                                                                const float4* __restrict__ res,
+                                                                const int32_t* __restrict__ nh,
+                                                                const int32_t* __restrict__ ids, int max_ids,
+                                                                const float4* __restrict__ up,
+                                                                float* __restrict__ acc_rows,
+                                                                int32_t* __restrict__ replay_list,
+                                                                uint32_t* __restrict__ replay_count) {
+    static_assert(kWaveThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
+    __shared__ float4 rows_all[kWaveThreads * GradRow<3>::kStride / 4];
+    float* rows = reinterpret_cast<float*>(rows_all) + (threadIdx.x & ~31) * GradRow<3>::kStride;
+    const int64_t j = blockIdx.x * (int64_t)kWaveThreads + threadIdx.x;
+    if (j >= rays) return;
+    const int64_t i = order[j];
+    const int n_hits = nh[i];   // 0 for samples that drew no ray
+    if (n_hits <= 0) return;
+    const float4 u4 = up[i];
+    if (u4.x == 0.f && u4.y == 0.f && u4.z == 0.f && u4.w == 0.f) return;
+    if (n_hits > max_ids) {
+        replay_list[atomicAdd(replay_count, 1u)] = (int32_t)j;
+        return;
+    }
+    wave_backward_ray<K, true>(S, P, xg, p0, St, dir, i, res, n_hits, ids, max_ids, u4, acc_rows, rows);
+}
+
+// The rays of replay_list replay their march backwards (the list's length is
+// what the listing launch left in replay_count). Consecutive entries go to
+// different blocks, so the few long replays spread over every SM.
+template <int K>
+__global__ void __launch_bounds__(kWaveThreads) k_wave_replay(SceneView S, TraceParams P,
+                                                              const float* __restrict__ xg, int64_t p0, int St,
+                                                              const float4* __restrict__ dir,
+                                                              const int32_t* __restrict__ order,
+                                                              const float4* __restrict__ res,
+                                                              const int32_t* __restrict__ nh,
+                                                              const float4* __restrict__ up,
+                                                              float* __restrict__ acc_rows,
+                                                              const int32_t* __restrict__ replay_list,
+                                                              const uint32_t* __restrict__ replay_count) {
+    static_assert(kWaveThreads == trace_threads<K>(), "k-buffer slots are laid out per block thread");
+    __shared__ float4 rows_all[kWaveThreads * GradRow<3>::kStride / 4];
+    float* rows = reinterpret_cast<float*>(rows_all) + (threadIdx.x & ~31) * GradRow<3>::kStride;
+    const int64_t n = *replay_count;
+    for (int64_t t = threadIdx.x * (int64_t)gridDim.x + blockIdx.x; t < n; t += (int64_t)gridDim.x * kWaveThreads) {
+        const int64_t i = order[replay_list[t]];
+        wave_backward_ray<K, false>(S, P, xg, p0, St, dir, i, res, nh[i], nullptr, 0, up[i], acc_rows, rows);
     }
 }
 
@@ -442,10 +485,12 @@ cudaError_t wave_backward(const SceneView& S, const int32_t* perm, const uint32_
         if (e != cudaSuccess) break;
         k_wave_grad_point<<<grid_for(np, kWaveThreads / 32), kWaveThreads, 0, st>>>(
             n, a, r, wo, p0, np, env, H, W, nd, ns, mode, seed, w.res, g_rgb, g_albedo, g_rough, g_env, w.up);
-        k_wave_backward<K, true><<<g, kWaveThreads, 0, st>>>(S, TP, x, p0, St, w.dir, w.val, rays, w.res, w.nh,
-                                                             w.ids, kWaveSavedHits, w.up, acc_rows);
-        k_wave_backward<K, false><<<g, kWaveThreads, 0, st>>>(S, TP, x, p0, St, w.dir, w.val, rays, w.res, w.nh,
-                                                              w.ids, kWaveSavedHits, w.up, acc_rows);
+        e = cudaMemsetAsync(w.count, 0, sizeof(uint32_t), st);
+        if (e != cudaSuccess) break;
+        k_wave_backward<K><<<g, kWaveThreads, 0, st>>>(S, TP, x, p0, St, w.dir, w.val, rays, w.res, w.nh, w.ids,
+                                                       kWaveSavedHits, w.up, acc_rows, w.list, w.count);
+        k_wave_replay<K><<<kWaveReplayBlocks, kWaveThreads, 0, st>>>(S, TP, x, p0, St, w.dir, w.val, w.res, w.nh,
+                                                                     w.up, acc_rows, w.list, w.count);
         count_launches(4);
         e = cudaGetLastError();
     }

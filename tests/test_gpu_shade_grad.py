@@ -181,3 +181,52 @@ def test_uniform_mode_rejects_specular_samples():
         irgs.shade_mc(S, dev(x), dev(n), dev(a), dev(r), dev(wo), dev(env), 4, 4, 0, p, mode="uniform")
     with pytest.raises(irgs.IrgsError):
         irgs.trace_forward(S, dev(x), dev(n), p.with_(flags=irgs.FLAG_UNIFORM))
+
+
+def _faint_layers(layers=40, per=60, seed=221):
+    """Horizontal layers of faint surfels above z = 0 (normal +z): secondary
+    rays leaving the floor cross them all and blend ~100 hits each."""
+    rng = np.random.default_rng(seed)
+    n = layers * per
+    means = np.column_stack([rng.uniform(-1, 1, n), rng.uniform(-1, 1, n),
+                             0.05 + 0.02 * np.repeat(np.arange(layers), per) + rng.uniform(0, 0.005, n)])
+    quats = np.tile([1.0, 0.0, 0.0, 0.0], (n, 1))
+    scales = np.exp(rng.normal(np.log(0.1), 0.2, size=(n, 2)))
+    opacity = rng.uniform(0.02, 0.08, n)
+    feats = rng.uniform(0, 1, (n, 3))
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float32)
+    return synth.Surfels(f(means), f(quats), f(scales), f(opacity), f(feats))
+
+
+def test_wavefront_gradient_replays_rays_beyond_saved_lists():
+    """The wavefront gradient saves 64 hit ids per secondary ray; rays that
+    blend more replay their march from a list the listing launch builds.
+    Here most rays do; the gradient must equal the fused per-thread kernel's
+    (which replays every ray) up to the reordering of the float atomics."""
+    sc = _faint_layers()
+    P, nd, ns = 24, 16, 16
+    rng = np.random.default_rng(222)
+    x = np.column_stack([rng.uniform(-0.5, 0.5, P), rng.uniform(-0.5, 0.5, P), np.zeros(P)]).astype(np.float32)
+    n = np.tile(np.float32([0, 0, 1]), (P, 1))
+    a = rng.uniform(0.1, 0.9, (P, 3)).astype(np.float32)
+    r = rng.uniform(0.2, 1.0, P).astype(np.float32)
+    wo = n.copy()
+    env = synth.env_map(seed=223, height=32, width=64)
+    S = make_scene(irgs, sc)
+    p = irgs.TraceParams(k=16, feat_count=3, t_min=1e-3)
+    # the sampled rays really exceed the saved list length
+    d, v = irgs.shade_sample_rays(dev(n), dev(r), dev(wo), nd, ns, 31)
+    vm = v.bool()
+    o = dev(x).repeat_interleave(nd + ns, 0)[vm].contiguous()
+    nh = irgs.trace_forward(S, o, d[vm].contiguous(), p)["n_hits"].cpu().numpy()
+    assert (nh > 64).sum() >= 50, np.sort(nh)[-10:]
+    g = torch.from_numpy(rng.normal(size=(P, 3)).astype(np.float32)).cuda()
+    args = (dev(x), dev(n), dev(a), dev(r), dev(wo), dev(env), nd, ns, 31)
+    g1 = irgs.shade_mc_backward(S, *args, p, g)
+    g2 = irgs.shade_mc_backward(S, *args, p.with_(flags=irgs.FLAG_PER_THREAD), g)
+    torch.cuda.synchronize()
+    assert S.status() == 0
+    for k in g1:
+        scale = max(float(g1[k].abs().max()), 1e-30)
+        assert float((g1[k] - g2[k]).abs().max()) <= 1e-5 * scale, k
+    assert float(g1["opacity"].abs().sum()) > 0
