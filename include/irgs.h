@@ -419,7 +419,7 @@ irgs_status irgs_envmap_export(irgs_envmap envmap, float* irr, float* pref, floa
  * indirect term over all samples) may be NULL. By default the samples of
  * all points are regrouped by direction and origin and traced with one
  * stack per ray (scratch from the stream-ordered allocator, ~64 bytes per
- * sample in chunks of at most 2^24); IRGS_FLAG_PER_THREAD selects the fused
+ * sample in chunks of at most 2^26); IRGS_FLAG_PER_THREAD selects the fused
  * kernel (a warp per point tracing its own samples). Both give the same
  * traces.
  */

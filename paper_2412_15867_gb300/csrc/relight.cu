@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(kRelightThreads) k_relight_shade(EnvMaps M, co
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t > 0 ? (n + t - 1) / t : 1); }
 
-constexpr int64_t kRelightChunkRays = int64_t(1) << 24;
+constexpr int64_t kRelightChunkRays = int64_t(1) << 26;
 
 template <int K>
 cudaError_t relight_wave(const SceneView& S, const uint32_t* bounds, const EnvMaps& M, const float* x,

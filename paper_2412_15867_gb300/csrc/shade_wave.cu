@@ -21,7 +21,10 @@
 // order from their hit lists (rays with longer lists replay the march).
 //
 // Rays are processed in chunks of whole points, at most kWaveChunkRays rays
-// each, so the scratch (~390 bytes per ray with the gradient) stays bounded.
+// each, so the scratch (~390 bytes per ray with the gradient) stays bounded;
+// a chunk is sorted as a whole, and the denser its points the more a warp's
+// regrouped rays share their paths (one chunk of 41M rays traces 6-7%
+// faster than three of at most 2^24).
 #include <cuda_runtime.h>
 
 #include "scene.h"
@@ -34,7 +37,7 @@ namespace irgs {
 namespace {
 
 constexpr int kWaveThreads = 128;
-constexpr int64_t kWaveChunkRays = int64_t(1) << 24;
+constexpr int64_t kWaveChunkRays = int64_t(1) << 26;
 constexpr int kWaveSavedHits = 64;   // 12% of secondary rays blend more than 32 hits, 0.02% more than 64
 constexpr int kWaveReplayBlocks = 1024;   // grid-stride blocks for the few rays whose hit list did not fit
 

@@ -122,9 +122,10 @@ def test_point_result_independent_of_other_points():
 @pytest.mark.slow
 def test_mc_config_full_size_sampled():
     """1M-surfel scene, 640k G-buffer points x (32 cosine + 32 GGX) samples
-    = 41M secondary rays against a 512x256 environment; 32 random points and
-    the points at the wavefront's chunk boundaries re-shaded by the oracle
-    (same point indices, so the same random numbers)."""
+    = 41M secondary rays (one wavefront chunk) against a 512x256
+    environment; 32 random points and the first and last point re-shaded by
+    the oracle (same point indices, so the same random numbers). Chunk
+    boundaries: test_gpu_fullsize.py."""
     sc = synth.object_scene(n=1_000_000, seed=1002)
     gb = synth.gbuffer_points(640_000, seed=1002)
     env = synth.env_map(seed=1003)
@@ -137,11 +138,8 @@ def test_mc_config_full_size_sampled():
     assert np.all(np.isfinite(rgb)) and np.all(rgb >= 0)
     # the point's position in the call keys its random stream: the oracle
     # shades the sampled points with those positions as keys
-    # 32 random points plus the points on both sides of the wavefront's
-    # chunk boundaries (whole points, 2^24 rays = 262,144 points of 64
-    # samples per chunk) and the first and last point
-    pc = (1 << 24) // 64
-    edges = [0, pc - 1, pc, 2 * pc - 1, 2 * pc, 640_000 - 1]
+    # 32 random points plus the first and last point
+    edges = [0, 640_000 - 1]
     idx = np.unique(np.concatenate([np.random.default_rng(5).choice(640_000, 32, replace=False), edges]))
     sub_gb = [arr[idx] for arr in gb]
     ref = oracle.shade(sc, *sub_gb, env, 32, 32, 2024, opar(p), point_ids=idx)
