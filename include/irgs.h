@@ -18,6 +18,10 @@
  *  - The return status covers argument validation and launch errors. Errors
  *    that kernels detect (traversal stack overflow) are recorded in the
  *    scene's status word and reported by irgs_scene_status().
+ *  - Per-call scratch is stream-ordered: taken from the library's own
+ *    memory pool on the current device and freed on the call's stream. The
+ *    pool keeps up to 32 GiB of freed scratch for later calls instead of
+ *    returning it to the driver; it is released when the process ends.
  *  - No entry point exits or aborts the process. Build/destroy of one scene
  *    must not race with other calls on that scene; concurrent traces of one
  *    scene are safe (they only read it).
@@ -231,7 +235,7 @@ irgs_status irgs_scene_export_wide(irgs_scene scene, float* nodes, int64_t cap, 
  * k = 16 and at least 2^20 rays, rays still marching after each of the
  * first three k-buffer rounds are regrouped into full warps; that takes
  * 56 to 104 bytes per ray of scratch (72 at 4..10 channels), allocated and
- * freed stream-ordered (cudaMallocAsync) on `stream`; if that allocation
+ * freed stream-ordered (the library's scratch pool) on `stream`; if that allocation
  * fails the rays are marched without regrouping. Results are the same
  * either way.
  */

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 
 #include "../../include/irgs.h"
 #include "scene.h"
@@ -13,6 +14,39 @@
 namespace irgs {
 static std::atomic<uint64_t> g_launches{0};
 void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// One scratch pool per device, created on first use.
+static std::mutex g_pool_mutex;
+static cudaMemPool_t g_pools[256] = {};
+
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st) {
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return e;
+    if (device < 0 || device >= 256) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mutex);
+        if (g_pools[device] == nullptr) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = device;
+            cudaMemPool_t created;
+            e = cudaMemPoolCreate(&created, &props);
+            if (e != cudaSuccess) return e;
+            uint64_t keep = kScratchKeepBytes;
+            e = cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) {
+                cudaMemPoolDestroy(created);
+                return e;
+            }
+            g_pools[device] = created;
+        }
+        pool = g_pools[device];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
 }  // namespace irgs
 
 namespace {

@@ -115,6 +115,13 @@ __device__ __forceinline__ float u01_from_bits(uint64_t z) {
 // Process-wide count of kernel launches (capi.cu owns the counter).
 void count_launches(uint64_t k);
 
+// Stream-ordered scratch of the current device from the library's own pool
+// (capi.cu): freed blocks stay in the pool up to kScratchKeepBytes, so the
+// large per-call scratch is not mapped again on every call. Free with
+// cudaFreeAsync.
+constexpr uint64_t kScratchKeepBytes = uint64_t(32) << 30;
+cudaError_t scratch_alloc(void** p, size_t bytes, cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // Device view of a scene (plain pointers, passed by value to kernels).
 struct SceneView {

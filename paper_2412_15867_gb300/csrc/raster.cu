@@ -261,7 +261,7 @@ irgs_status launch_rasterize(const SceneView& S, const float* leaf_box, const ir
     const size_t b_z = 4 * nn, b_rect = 16 * nn, b_cnt = 4 * nn, b_off = 4 * nn, b_rng = 8 * n_tiles, b_tot = 16;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t total_bytes = al(b_z) + al(b_rect) + al(b_cnt) + al(b_off) + al(b_rng) + al(b_tot);
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), total_bytes, st);
+    cudaError_t e = scratch_alloc(reinterpret_cast<void**>(&base), total_bytes, st);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? IRGS_ERR_OOM : IRGS_ERR_CUDA;
     size_t off = 0;
     auto take = [&](size_t b) { unsigned char* q = base + off; off += al(b); return q; };
@@ -289,7 +289,7 @@ irgs_status launch_rasterize(const SceneView& S, const float* leaf_box, const ir
         const int64_t hw = sort_hist_words(T);
         const size_t b4 = 4 * (size_t)T;
         const size_t pb = al(b4) * 7 + al(4 * (size_t)hw);
-        e = cudaMallocAsync(reinterpret_cast<void**>(&pairs), pb, st);
+        e = scratch_alloc(reinterpret_cast<void**>(&pairs), pb, st);
         if (e == cudaSuccess) {
             size_t o2 = 0;
             auto take2 = [&](size_t b) { unsigned char* q = pairs + o2; o2 += al(b); return q; };

@@ -522,7 +522,7 @@ cudaError_t relight_wave(const SceneView& S, const uint32_t* bounds, const EnvMa
     const size_t bytes = al(16 * cap) + 4 * al(4 * cap) + al(4 * hw) + al(32 * cap) + al(4 * (cap + 1)) +
                          al(4 * cap) + al(4 * (1 + sums)) + al(16 * kRelightStateF4 * cap);
     unsigned char* base = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, st);
+    cudaError_t e = scratch_alloc(reinterpret_cast<void**>(&base), bytes, st);
     if (e != cudaSuccess) return e;
     size_t off = 0;
     auto take = [&](size_t b) { unsigned char* q = base + off; off += al(b); return q; };

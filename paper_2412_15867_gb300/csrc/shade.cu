@@ -174,7 +174,7 @@ irgs_status launch_shade_mc_backward(const SceneView& S, const int32_t* perm, co
     constexpr int N = GradRow<3>::N;
     const size_t bytes = sizeof(float) * N * (size_t)(S.n > 0 ? S.n : 1);
     float* acc_rows = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&acc_rows), bytes, st);
+    cudaError_t e = scratch_alloc(reinterpret_cast<void**>(&acc_rows), bytes, st);
     if (e == cudaErrorMemoryAllocation) return IRGS_ERR_OOM;
     if (e != cudaSuccess) return IRGS_ERR_CUDA;
     e = cudaMemsetAsync(acc_rows, 0, bytes, st);

@@ -363,7 +363,7 @@ struct WaveScratch {
             o_ids = take(sizeof(int32_t) * kWaveSavedHits * rays);
             o_up = take(sizeof(float4) * rays);
         }
-        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), off, st);
+        cudaError_t e = scratch_alloc(reinterpret_cast<void**>(&base), off, st);
         if (e != cudaSuccess) return e;
         dir = reinterpret_cast<float4*>(base + o_dir);
         key = reinterpret_cast<uint32_t*>(base + o_key);
@@ -471,7 +471,7 @@ cudaError_t wave_backward(const SceneView& S, const int32_t* perm, const uint32_
     const int64_t pc = chunk_points(St);
     const size_t row_bytes = sizeof(float) * N * (size_t)(S.n > 0 ? S.n : 1);
     float* acc_rows = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&acc_rows), row_bytes, st);
+    cudaError_t e = scratch_alloc(reinterpret_cast<void**>(&acc_rows), row_bytes, st);
     if (e != cudaSuccess) return e;
     WaveScratch w;
     e = cudaMemsetAsync(acc_rows, 0, row_bytes, st);

@@ -95,7 +95,7 @@ cudaError_t launch(const SceneView& S, const TraceParams& P, const BwdArgs& a, c
     constexpr int N = GradRow<FB>::N;
     const size_t bytes = sizeof(float) * N * (size_t)(S.n > 0 ? S.n : 1);
     float* acc_rows = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&acc_rows), bytes, st);
+    cudaError_t e = scratch_alloc(reinterpret_cast<void**>(&acc_rows), bytes, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(acc_rows, 0, bytes, st);
     if (e == cudaSuccess) {

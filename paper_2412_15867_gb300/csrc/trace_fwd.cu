@@ -144,7 +144,7 @@ cudaError_t launch_rounds(const SceneView& S, const float* ro, const float* rd, 
     const size_t state_off = (size_t)((words * 4 + 255) / 256 * 256);
     const size_t bytes = state_off + sizeof(float4) * SW * (size_t)R;
     unsigned char* base = nullptr;
-    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&base), bytes, st);
+    cudaError_t e = scratch_alloc(reinterpret_cast<void**>(&base), bytes, st);
     if (e != cudaSuccess) return e;
     uint32_t* flags = reinterpret_cast<uint32_t*>(base);
     int32_t* list = reinterpret_cast<int32_t*>(flags + R + 1);
